@@ -1,0 +1,71 @@
+"""Pins for oracle.bfv: Dec(Enc(m)) = m, homomorphic plaintext product against
+the schoolbook product over Z_t, re-masking Dec(W Enc(r) - s) + s = W r, and
+the noise check flagging a corrupted ciphertext."""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import bfv
+from oracle.params import BfvParams
+from oracle.ring import negacyclic_schoolbook
+
+
+@pytest.fixture(scope="module", params=[(6, 2, 54), (7, 3, 60)])
+def params(request):
+    log_n, L, bits = request.param
+    return BfvParams(log_n=log_n, num_primes=L, prime_bits=bits)
+
+
+def test_roundtrip(params):
+    p = params
+    sk = bfv.keygen(p, 1)
+    r = random.Random(2)
+    for idx in range(3):
+        m = [r.randrange(p.t) for _ in range(p.n)]
+        ct = bfv.encrypt(p, sk, m, seed=9, ct_index=idx)
+        assert bfv.decrypt(p, sk, ct) == m
+        assert bfv.noise_budget_ok(p, sk, ct)
+
+
+def test_encrypt_is_randomised_by_index(params):
+    p = params
+    sk = bfv.keygen(p, 1)
+    m = [0] * p.n
+    a = bfv.encrypt(p, sk, m, seed=9, ct_index=0)
+    b = bfv.encrypt(p, sk, m, seed=9, ct_index=1)
+    assert not (a == b).all()
+
+
+def test_plain_product_and_mask(params):
+    p = params
+    sk = bfv.keygen(p, 3)
+    r = random.Random(4)
+    x = [r.randrange(p.t) for _ in range(p.n)]
+    w = [r.randrange(-(1 << 15), 1 << 15) for _ in range(p.n)]
+    s = [r.randrange(p.t) for _ in range(p.n)]
+    ct = bfv.encrypt(p, sk, x, seed=5, ct_index=0)
+    out = bfv.sub_plain(p, bfv.mul_plain(p, ct, bfv.encode_plain(p, [v % p.t for v in w])), s)
+    dec = bfv.decrypt(p, sk, out)
+    want = negacyclic_schoolbook(x, [v % p.t for v in w], p.t)
+    assert [(d + si) % p.t for d, si in zip(dec, s)] == want
+
+
+def test_add_plain(params):
+    p = params
+    sk = bfv.keygen(p, 3)
+    r = random.Random(6)
+    x1 = [r.randrange(p.t) for _ in range(p.n)]
+    x0 = [r.randrange(p.t) for _ in range(p.n)]
+    ct = bfv.add_plain(p, bfv.encrypt(p, sk, x1, seed=5, ct_index=2), x0)
+    assert bfv.decrypt(p, sk, ct) == [(a + b) % p.t for a, b in zip(x0, x1)]
+
+
+def test_noise_check_flags_corruption():
+    p = BfvParams(log_n=6, num_primes=2, prime_bits=54)
+    sk = bfv.keygen(p, 1)
+    ct = bfv.encrypt(p, sk, [1] * p.n, seed=1, ct_index=0)
+    bad = ct.copy()
+    bad[0, 0, 3] = (bad[0, 0, 3] + p.primes[0] // 3) % p.primes[0]
+    assert bfv.noise_budget_ok(p, sk, ct)
+    assert not bfv.noise_budget_ok(p, sk, bad)

@@ -1,0 +1,104 @@
+"""Pins for oracle.protocol: Alg. 1 reconstructs W o X + b, the grad_X role
+reconstructs the input gradient, Alg. 2 reconstructs grad_W -- each against
+the direct ring operators -- and decoded shares do not depend on the partition."""
+import numpy as np
+import pytest
+
+from oracle import bfv, protocol
+from oracle.packing import Partition
+from oracle.params import BfvParams
+from oracle.protocol import DGRAD, FWD, WGRAD, Layer
+from paper_2403_11166_gb300 import inputs
+
+P_SMALL = BfvParams(log_n=7, num_primes=2, prime_bits=54)     # weights small: q ~ 2^108 suffices
+P_BIG = BfvParams(log_n=7, num_primes=3, prime_bits=60)       # uniform shares as multipliers
+
+
+def _mask(x, t_bits=41):
+    return np.asarray(x).astype(np.uint64) & np.uint64((1 << t_bits) - 1)
+
+
+def _add(a, b):
+    with np.errstate(over="ignore"):
+        return _mask(np.asarray(a, dtype=np.uint64) + np.asarray(b, dtype=np.uint64))
+
+
+FC = Layer("fc", B=3, Ci=10, Co=5)
+CONV = Layer("conv", B=2, Ci=3, Co=2, h=5, w=4, s=3, pad=1)
+
+
+@pytest.mark.parametrize("layer,part", [
+    (FC, Partition(2, 4, 3, 1, 1, 1, 1)),
+    (CONV, Partition(1, 2, 1, 3, 2, 3, 3)),
+])
+def test_forward_reconstructs(layer, part):
+    p = P_SMALL
+    g = inputs.rng(0)
+    sk = bfv.keygen(p, 1)
+    W = inputs.gaussian_fixed(g, layer.w_shape())
+    x = inputs.gaussian_fixed(g, layer.x_shape())
+    b = inputs.gaussian_fixed(g, (layer.Co,), frac_bits=24)
+    x0, x1 = inputs.split_shares(g, x)
+    y0, y1, *_ = protocol.he_linear(p, sk, layer, FWD, part, W, x1, x0, 11, 12, bias=b)
+    want = _add(protocol.ring_op(layer, FWD, W, x, 41).reshape(layer.y_shape()),
+                np.asarray(b).astype(np.int64).view(np.uint64).reshape((1, -1) + (1,) * (len(layer.y_shape()) - 2)))
+    assert (_add(y0, y1) == want).all()
+
+
+@pytest.mark.parametrize("layer,part", [
+    (FC, Partition(3, 2, 4, 1, 1, 1, 1)),
+    (CONV, Partition(1, 1, 2, 2, 3, 3, 3)),
+])
+def test_dgrad_reconstructs(layer, part):
+    p = P_SMALL
+    g = inputs.rng(1)
+    sk = bfv.keygen(p, 2)
+    W = inputs.gaussian_fixed(g, layer.w_shape())
+    gy = inputs.gaussian_fixed(g, layer.y_shape())
+    gy0, gy1 = inputs.split_shares(g, gy)
+    gx0, gx1, *_ = protocol.he_linear(p, sk, layer, DGRAD, part, W, gy1, gy0, 21, 22)
+    want = protocol.ring_op(layer, DGRAD, W, gy, 41).reshape(layer.x_shape())
+    assert (_add(gx0, gx1) == want).all()
+
+
+@pytest.mark.parametrize("layer,part", [
+    (FC, Partition(4, 2, 3, 1, 1, 1, 1)),
+    (CONV, Partition(1, 1, 1, 3, 3, 2, 2)),
+])
+def test_wgrad_reconstructs(layer, part):
+    p = P_BIG
+    g = inputs.rng(2)
+    sk = bfv.keygen(p, 3)
+    x = inputs.gaussian_fixed(g, layer.x_shape())
+    gy = inputs.gaussian_fixed(g, layer.y_shape())
+    x0, x1 = inputs.split_shares(g, x)
+    gy0, gy1 = inputs.split_shares(g, gy)
+    gw, tilde, s = protocol.he_wgrad(p, sk, layer, part, gy0, gy1, x0, x1, 31, 32, 33)
+    want = protocol.ring_op(layer, WGRAD, gy, x, 41).reshape(layer.w_shape())
+    assert (gw == want).all()
+
+
+def test_partition_independence():
+    p = P_SMALL
+    g = inputs.rng(3)
+    sk = bfv.keygen(p, 4)
+    layer = CONV
+    W = inputs.gaussian_fixed(g, layer.w_shape())
+    x = inputs.gaussian_fixed(g, layer.x_shape())
+    x0, x1 = inputs.split_shares(g, x)
+    a = protocol.he_linear(p, sk, layer, FWD, Partition(1, 3, 2, 3, 2, 3, 3), W, x1, x0, 1, 2)
+    b = protocol.he_linear(p, sk, layer, FWD, Partition(2, 1, 1, 2, 2, 3, 3), W, x1, x0, 5, 2)
+    assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+
+
+def test_simulator_view_zero_input_gives_minus_mask():
+    """MO's view with Enc(0) in place of Enc(<X>_1) (and <X>_0 = 0): the protocol
+    still runs and the DO decrypts exactly -s."""
+    p = P_SMALL
+    g = inputs.rng(4)
+    sk = bfv.keygen(p, 5)
+    layer = FC
+    W = inputs.gaussian_fixed(g, layer.w_shape())
+    zero = np.zeros(layer.x_shape(), dtype=np.uint64)
+    y0, y1, *_ = protocol.he_linear(p, sk, layer, FWD, Partition(1, 5, 5, 1, 1, 1, 1), W, zero, zero, 7, 8)
+    assert (_add(y0, y1) == 0).all()
