@@ -1,0 +1,231 @@
+/*
+ * pencil_he.h -- C ABI of the GB300 (sm_103a) homomorphic linear-layer hot path
+ * of Pencil (NDSS 2024): BFV with RNS limbs, negacyclic NTT, coefficient
+ * packings of Appendix A, Algorithm 1 (forward / input gradient) and
+ * Algorithm 2 (weight-gradient cross terms) between a data owner (DO) and a
+ * model owner (MO).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Return value: PENCIL_OK (0) or a negative PENCIL_E_* code.  Arguments are
+ *   validated on the host before anything is enqueued; on error nothing has
+ *   been launched.  Work is asynchronous on `stream` (a cudaStream_t passed as
+ *   void*; NULL = legacy default stream).  Device-detected conditions (noise
+ *   check) are OR-ed into a per-context status word read by pencil_sync_status.
+ * - Every `uint64_t*` / `int64_t*` / `void* ws` argument is DEVICE memory owned
+ *   by the caller, on the context's device.  The library never frees caller
+ *   memory.  Handles (PencilCtx, PencilSecretKey, PencilPlan) are owned by the
+ *   library and released with the matching *_destroy call.
+ * - Ring layouts.  N = 2^log_n slots, L RNS limbs.
+ *     ciphertext  uint64[2][L][N]  (c0, c1), NTT (evaluation) form, canonical in [0, q_i)
+ *     plaintext   uint64[L][N]     NTT form, canonical
+ *   Arrays of ciphertexts / plaintexts are contiguous: [count][2][L][N] / [count][L][N].
+ *   NTT slot i of limb j holds a(psi_j^(2 brv(i) + 1)) mod q_j, brv = bit reversal.
+ * - Shares and masks are Z_t values (t = 2^t_bits) stored in uint64, row-major in
+ *   the user's layout: FC input [B][n_i], output [B][n_o]; conv input
+ *   [B][C_in][H][W], output [B][C_out][H_out][W_out]; weights int64 (signed,
+ *   any value is read mod t) [n_o][n_i] or [C_out][C_in][s][s].
+ * - `ws` is scratch device memory of at least the size reported for that call
+ *   by pencil_plan_sizes; its contents on entry are ignored.
+ */
+#ifndef PENCIL_HE_H
+#define PENCIL_HE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define PENCIL_OK 0
+#define PENCIL_E_ARG (-1)      /* null pointer, bad enum, bad seed use        */
+#define PENCIL_E_SHAPE (-2)    /* layer shape invalid or inconsistent         */
+#define PENCIL_E_PARAMS (-3)   /* unsupported N / limb count / prime size / t */
+#define PENCIL_E_CAPACITY (-4) /* partition exceeds N or workspace too small  */
+#define PENCIL_E_NOISE (-5)    /* decryption noise above q/(4t) (status word) */
+#define PENCIL_E_TIMEOUT (-6)  /* a bounded device wait gave up (status word) */
+#define PENCIL_E_CUDA (-7)     /* a CUDA runtime call failed                  */
+#define PENCIL_E_UNIMPL (-8)   /* combination not implemented                 */
+
+typedef struct PencilCtx PencilCtx;
+typedef struct PencilSecretKey PencilSecretKey;
+typedef struct PencilPlan PencilPlan;
+
+/* BFV instance {N, t, q} (Sec. 2.2) with q the product of `num_primes` RNS
+ * limbs (Sec. 5 "RNS Decomposition"): the largest primes below 2^prime_bits
+ * that are 1 mod 2N, in descending order.  Supported: log_n in {12, 13, 14},
+ * num_primes in [1, 4], prime_bits in [30, 60], t_bits in [8, 60].  The
+ * encryption error is a discrete Gaussian with sigma = 3.2 on [-19, 19]. */
+typedef struct {
+  int32_t log_n;
+  int32_t num_primes;
+  int32_t prime_bits;
+  int32_t t_bits;
+} PencilParams;
+
+/* Creates a context on CUDA device `device`: primes, NTT tables (psi_i = the
+ * smallest primitive 2N-th root of unity mod q_i), RNS constants.
+ * Allocates a few MB of device memory (freed by pencil_ctx_destroy). */
+int pencil_ctx_create(const PencilParams* params, int device, PencilCtx** out);
+int pencil_ctx_destroy(PencilCtx* ctx);
+/* Copies the L primes and roots (host arrays of length num_primes). */
+int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
+/* Reads and clears the device status word (synchronises the device):
+ * *status = 0, or a PENCIL_E_* code recorded by a kernel. */
+int pencil_sync_status(PencilCtx* ctx, int32_t* status);
+
+/* DO side: ternary secret key s_i = (w_i mod 3) - 1, w = Philox4x64-10 word
+ * (key = (seed, 1), counter = (i/4, 0, 0, 0), word i%4), kept as NTT(s) per
+ * limb on the device (owned by the handle). */
+int pencil_keygen(PencilCtx* ctx, uint64_t seed, PencilSecretKey** out, void* stream);
+int pencil_sk_destroy(PencilSecretKey* sk);
+
+/* ---------------------------------------------------------------- plans */
+enum { PENCIL_FC = 0, PENCIL_CONV = 1 };
+/* Role of a plan: the forward product (Alg. 1), the input gradient
+ * grad_X = W (.)_x grad_Y (Sec. 3.2.2, Alg.-1-like) or the weight gradient
+ * cross terms (Alg. 2). */
+enum { PENCIL_ROLE_FWD = 0, PENCIL_ROLE_DGRAD = 1, PENCIL_ROLE_WGRAD = 2 };
+/* Operand positions of a plan: ciphertext-input positions ct_in[m*K+k]
+ * (packing pi_v) or kernel positions pt[k*NC+n] (packing pi_W). */
+enum { PENCIL_OPERAND_INPUT = 0, PENCIL_OPERAND_KERNEL = 1 };
+
+/* Layer: FC (c_in = n_i, c_out = n_o, height = width = kernel = 1, pad = 0) or
+ * stride-1 2-D convolution with zero padding `pad` on an height x width input. */
+typedef struct {
+  int32_t kind;
+  int32_t batch;
+  int32_t c_in;
+  int32_t c_out;
+  int32_t height;
+  int32_t width;
+  int32_t kernel;
+  int32_t pad;
+} PencilLayerDesc;
+
+/* Block partition of the correlation (Appendix A: "larger inputs or weights
+ * could be partitioned"): bb batch items, cib input channels and cob output
+ * channels per polynomial; th x tw output tile; kth x ktw kernel tile.
+ * Valid iff bb*cob*cib*(th+kth-1)*(tw+ktw-1) <= N. */
+typedef struct {
+  int32_t bb, cib, cob, th, tw, kth, ktw;
+} PencilPartition;
+
+typedef struct {
+  PencilPartition part;
+  int64_t ct_in;         /* ciphertexts at input positions  (M*K)      */
+  int64_t pt;            /* plaintexts at kernel positions  (K*NC)     */
+  int64_t ct_out;        /* output ciphertexts              (M*NC)     */
+  int64_t products;      /* ct x pt products per call       (M*K*NC)   */
+  int64_t ct_words;      /* uint64 words per ciphertext = 2*L*N        */
+  int64_t pt_words;      /* uint64 words per plaintext  = L*N          */
+  int64_t out_elems;     /* elements of the user's output tensor       */
+  int64_t ws_encrypt;    /* bytes of ws for encrypt_share (either operand) */
+  int64_t ws_forward;    /* bytes of ws for he_linear_forward          */
+  int64_t ws_backward;   /* bytes of ws for he_linear_backward (this plan's role) */
+  int64_t ws_decrypt;    /* bytes of ws for decrypt_to_share           */
+} PencilPlanSizes;
+
+/* Plans `role` of `layer`.  `part` = NULL lets the planner choose the
+ * partition with its cost model (bytes moved and NTT / multiply counts);
+ * otherwise `part` is used as given (PENCIL_E_CAPACITY if it does not fit).
+ * Builds the packing index tables on the device (owned by the plan). */
+int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role,
+                       const PencilPartition* part, PencilPlan** out);
+int pencil_plan_destroy(PencilPlan* plan);
+int pencil_plan_sizes(const PencilPlan* plan, PencilPlanSizes* sizes);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* MO: plaintext encoding (Appendix A pi_W / pi_v).  `values` are read mod t and
+ * lifted through their centred representative in [-t/2, t/2) to every limb,
+ * then transformed.  operand = KERNEL: writes pt[K*NC][L][N] from the role's
+ * kernel tensor (fwd/dgrad: the weights W; wgrad: the MO share <gY>_0).
+ * operand = INPUT: writes [M*K][L][N] from the role's input tensor (wgrad: the
+ * MO share <X>_0).  `values` is int64 for W and uint64 Z_t shares otherwise
+ * (same bits). */
+int encode_weights(PencilCtx* ctx, const PencilPlan* plan, int32_t operand,
+                   const int64_t* values, uint64_t* pt, void* stream);
+
+/* DO: symmetric BFV encryption of a packed share (Sec. 2.2, Alg. 1 step 1,
+ * Alg. 2 step 1).  For ciphertext index c (0-based within this call):
+ *   c1 = a,  a[i] = (w0 * 2^64 + w1) mod q_j from Philox (key (seed, 2),
+ *             counter (i/2, c, j, 0), words 2(i%2), 2(i%2)+1) -- NTT form;
+ *   c0 = NTT(Delta * m + e) - a * NTT(s),  Delta = floor(q / t),
+ *   e[i] from the CDT on Philox (key (seed, 3), counter (i/4, c, 0, 0), word i%4).
+ * operand INPUT packs `share` with pi_v into ct[M*K]; operand KERNEL packs it
+ * with pi_W into ct[K*NC] (Alg. 2's Enc(<gY>_1)).  ws >= ws_encrypt bytes. */
+int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* plan,
+                  int32_t operand, const uint64_t* share, uint64_t seed, uint64_t* ct,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* MO: Algorithm 1 steps 2-3 for a FWD or DGRAD plan.
+ *   ct_out[m,n] = sum_k (ct_in[m,k] + Delta*pi_v(x0)[m,k]) * pt[k,n] - Delta * s
+ * with s one Z_t value per output element from Philox (key (mask_seed, 4),
+ * counter (flat/4, 0, 0, 0), word flat%4; flat = row-major index in the output)
+ * and, at coefficients carrying no output, (key (mask_seed, 5), counter
+ * (i/4, ct_out index, 0, 0)).  Writes the MO share y0[flat] = s + bias[o]
+ * (bias: nullable, Z_t values [n_o] / [C_out], FWD only).  ct_in is not
+ * modified.  ws >= ws_forward bytes. */
+int he_linear_forward(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* ct_in,
+                      const uint64_t* pt, const uint64_t* x0, const uint64_t* bias,
+                      uint64_t mask_seed, uint64_t* ct_out, uint64_t* y0,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* MO: backward pass of one layer (Sec. 3.2.2).
+ * Input gradient (plan_dgrad, nullable to skip): Algorithm 1 on the DGRAD plan,
+ *   ct_gx = sum_k (ct_gy1_d + Delta pi_v(gy0)) * pt_wt - Delta s_x, gx0 = s_x
+ *   (pt_wt = encode_weights(plan_dgrad, KERNEL, W)).
+ * Weight gradient (plan_wgrad, nullable to skip): Algorithm 2 steps 2-3,
+ *   ct_gw[m,n] = sum_k Enc(<X>_1)[m,k] * NTT(pi_W(<gY>_0))[k,n]
+ *              + Enc(<gY>_1)[k,n] * NTT(pi_v(<X>_0))[m,k]  - Delta s_w,
+ *   gw_mask = s_w (the MO keeps it; grad_W = decrypted + s_w + local terms).
+ *   ct_x1_w = encrypt_share(plan_wgrad, INPUT, <X>_1), ct_gy1_w =
+ *   encrypt_share(plan_wgrad, KERNEL, <gY>_1); gy0 / x0 are the MO's shares.
+ * ws >= ws_backward of plan_dgrad + ws_backward of plan_wgrad. */
+int he_linear_backward(PencilCtx* ctx, const PencilPlan* plan_dgrad, const PencilPlan* plan_wgrad,
+                       const uint64_t* ct_gy1_d, const uint64_t* pt_wt,
+                       const uint64_t* ct_x1_w, const uint64_t* ct_gy1_w,
+                       const uint64_t* gy0, const uint64_t* x0,
+                       uint64_t mask_seed_x, uint64_t mask_seed_w,
+                       uint64_t* ct_gx, uint64_t* gx0, uint64_t* ct_gw, uint64_t* gw_mask,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* DO: decryption and unpacking (Alg. 1 step 4): x = INTT(c0 + c1 * NTT(s)) per
+ * limb, m = round(t x / q) mod t computed from the RNS residues (no big
+ * integers), scattered with pi_y^{-1} into y1 (user output layout).  With
+ * check_noise != 0, coefficients whose t x / q lies 1/4 or more away from an
+ * integer set PENCIL_E_NOISE in the status word.  ws >= ws_decrypt bytes. */
+int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* plan,
+                     const uint64_t* ct_out, uint64_t* y1, int32_t check_noise,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* In-place batched negacyclic NTT (inverse = 0) or INTT (inverse = 1) of
+ * `count` polynomials laid out [count][L][N], canonical in and out (Sec. 5 "NTT"). */
+int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream);
+
+/* ---------------------------------------------------------------- profiling
+ * Per-kernel timing with CUDA events recorded on the launch stream around every
+ * kernel the context launches (not available inside CUDA-graph capture).
+ * pencil_profile(ctx, 1) clears and starts recording, (ctx, 0) stops.
+ * pencil_profile_read synchronises the recorded events and returns one entry
+ * per kernel kind that launched: launches and summed milliseconds. */
+enum {
+  PENCIL_K_NTT_RAW = 0, PENCIL_K_INTT_RAW, PENCIL_K_NTT_ENCRYPT, PENCIL_K_NTT_ADDPLAIN, PENCIL_K_NTT_ENCODE,
+  PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
+  PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_COUNT
+};
+typedef struct {
+  int32_t kernel;   /* PENCIL_K_* */
+  int32_t launches;
+  double ms;
+} PencilProfEntry;
+int pencil_profile(PencilCtx* ctx, int32_t enable);
+int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t max_entries, int32_t* n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PENCIL_HE_H */

@@ -1,0 +1,986 @@
+// C ABI of the Pencil HE hot path (declared in include/pencil_he.h).
+//
+// Host side: BFV/RNS parameter generation (Sec. 2.2, Sec. 5), the planner
+// that partitions a layer into polynomial blocks (Appendix A), the packing
+// index tables, argument validation, and the launch sequences of Alg. 1 and
+// Alg. 2.  Every launch goes to the caller's stream; nothing here allocates
+// on the hot path (contexts, keys and plans own their device tables).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pencil_he.h"
+#include "kernels.h"
+
+using namespace pencil;
+typedef unsigned __int128 u128;
+
+// ================================================================== number theory (host)
+static u64 mulmod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+
+static u64 powmod(u64 a, u64 e, u64 m) {
+  u64 r = 1 % m;
+  a %= m;
+  while (e) {
+    if (e & 1) r = mulmod(r, a, m);
+    a = mulmod(a, a, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Deterministic Miller-Rabin for 64-bit n (bases = first 12 primes).
+static bool is_prime64(u64 n) {
+  static const u64 bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (u64 p : bases) {
+    if (n % p == 0) return n == p;
+  }
+  u64 d = n - 1;
+  int r = 0;
+  while ((d & 1) == 0) {
+    d >>= 1;
+    ++r;
+  }
+  for (u64 a : bases) {
+    u64 x = powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < r; ++i) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+// Largest `count` primes q < 2^bits with q = 1 mod two_n, descending.
+static bool find_primes(int bits, int count, u64 two_n, std::vector<u64>& out) {
+  u64 top = (bits == 64) ? ~0ull : ((1ull << bits) - 1);
+  u64 q = top / two_n * two_n + 1;
+  if (q > top) q -= two_n;
+  while ((int)out.size() < count) {
+    if (q <= two_n) return false;
+    if (is_prime64(q)) out.push_back(q);
+    q -= two_n;
+  }
+  return true;
+}
+
+// Numerically smallest element of multiplicative order exactly two_n mod q.
+static u64 min_root_2n(u64 q, u64 two_n) {
+  const u64 half = two_n / 2, ex = (q - 1) / two_n;
+  u64 psi0 = 0;
+  for (u64 g = 2;; ++g) {
+    psi0 = powmod(g, ex, q);
+    if (powmod(psi0, half, q) == q - 1) break;
+  }
+  const u64 sq = mulmod(psi0, psi0, q);
+  u64 cur = psi0, best = psi0;
+  for (u64 k = 1; k < half; ++k) {
+    cur = mulmod(cur, sq, q);
+    if (cur < best) best = cur;
+  }
+  return best;
+}
+
+static u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+static unsigned brv(unsigned x, int bits) {
+  unsigned r = 0;
+  for (int i = 0; i < bits; ++i) {
+    r = (r << 1) | (x & 1);
+    x >>= 1;
+  }
+  return r;
+}
+
+// floor(2^e / q) as a 128-bit value (requires the result < 2^128).
+static u128 floor_pow2_div(int e, u64 q) {
+  u128 quo = 0;
+  u128 rem = 0;
+  for (int bit = e; bit >= 0; --bit) {
+    rem = (rem << 1) | (bit == e ? 1 : 0);
+    quo <<= 1;
+    if (rem >= q) {
+      rem -= q;
+      quo |= 1;
+    }
+  }
+  return quo;
+}
+
+// floor(prod(q) / 2^t_bits) mod p, prod(q) held as little-endian 64-bit words.
+static u64 delta_mod(const std::vector<u64>& qs, int t_bits, u64 p) {
+  std::vector<u64> w(qs.size() + 1, 0);
+  w[0] = 1;
+  for (u64 q : qs) {
+    u128 carry = 0;
+    for (size_t i = 0; i < w.size(); ++i) {
+      u128 v = (u128)w[i] * q + carry;
+      w[i] = (u64)v;
+      carry = v >> 64;
+    }
+  }
+  // shift right by t_bits (< 64)
+  for (size_t i = 0; i < w.size(); ++i) {
+    u64 hi = (i + 1 < w.size()) ? w[i + 1] : 0;
+    w[i] = (t_bits == 0) ? w[i] : ((w[i] >> t_bits) | (hi << (64 - t_bits)));
+  }
+  u64 r = 0;
+  for (size_t i = w.size(); i-- > 0;) r = (u64)((((u128)r << 64) | w[i]) % p);
+  return r;
+}
+
+// ================================================================== handles
+struct ProfRec {
+  int kernel;
+  cudaEvent_t a, b;
+};
+
+struct PencilCtx {
+  bool prof_on = false;
+  std::vector<ProfRec> prof;      // recorded launches
+  std::vector<cudaEvent_t> pool;  // spare events
+  PencilParams params;
+  int device;
+  int n;
+  std::vector<u64> primes, psis;
+  DevCtx dev;
+  ulonglong2* tw_fwd = nullptr;
+  ulonglong2* tw_inv = nullptr;
+  int* status = nullptr;
+};
+
+struct PencilSecretKey {
+  PencilCtx* ctx;
+  ulonglong2* sk = nullptr;
+};
+
+struct Geom {
+  int B, Ci, Co, H, W, KH, KW;
+  int Ho() const { return H - KH + 1; }
+  int Wo() const { return W - KW + 1; }
+};
+
+struct Counts {
+  int MB, MTH, MTW, KC, KTH, KTW, NC;
+  long long M() const { return (long long)MB * MTH * MTW; }
+  long long K() const { return (long long)KC * KTH * KTW; }
+};
+
+struct PencilPlan {
+  PencilCtx* ctx;
+  PencilLayerDesc layer;
+  int role;
+  Geom g;
+  PencilPartition part;
+  Counts c;
+  long long ct_in, pt, ct_out, products, out_elems;
+  Accessor acc_v, acc_w, acc_y;  // ptr filled per call
+  long long hw;                  // output spatial size (bias broadcast)
+  int co_out;                    // output channel count seen by the bias
+  u64* d_tab = nullptr;          // [3][N]: v, w, y tables
+  int4* d_org = nullptr;         // origins: v [ct_in], w [pt], y [ct_out]
+  Packing pk_v, pk_w, pk_y;
+  long long ws_encrypt, ws_forward, ws_backward, ws_decrypt;
+};
+
+static int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static cudaEvent_t prof_event(PencilCtx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records CUDA events around the launches made while it lives (when enabled).
+struct ProfScope {
+  PencilCtx* c;
+  int k;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(PencilCtx* ctx, int kernel, cudaStream_t st) : c(ctx), k(kernel), s(st) {
+    if (c->prof_on) {
+      a = prof_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, s);
+      c->prof.push_back(ProfRec{k, a, b});
+    }
+  }
+};
+#define PROF(ctx, kernel, stream) ProfScope _prof_##kernel(ctx, kernel, stream)
+
+#define CUDA_TRY(x)                               \
+  do {                                            \
+    cudaError_t _e = (x);                         \
+    if (_e != cudaSuccess) {                      \
+      fprintf(stderr, "pencil: %s -> %s\n", #x, cudaGetErrorString(_e)); \
+      return PENCIL_E_CUDA;                       \
+    }                                             \
+  } while (0)
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// ================================================================== context
+extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilCtx** out) {
+  if (!params || !out) return PENCIL_E_ARG;
+  *out = nullptr;
+  const PencilParams& p = *params;
+  if (p.log_n < 12 || p.log_n > 14) return PENCIL_E_PARAMS;
+  if (p.num_primes < 1 || p.num_primes > PENCIL_MAX_LIMBS) return PENCIL_E_PARAMS;
+  if (p.prime_bits < 30 || p.prime_bits > 60) return PENCIL_E_PARAMS;
+  if (p.t_bits < 8 || p.t_bits > 60) return PENCIL_E_PARAMS;
+  const int n = 1 << p.log_n;
+  std::vector<u64> qs;
+  if (!find_primes(p.prime_bits, p.num_primes, 2ull * n, qs)) return PENCIL_E_PARAMS;
+  // q must leave room for t: Delta >= 1 and t < every q_i
+  for (u64 q : qs)
+    if (p.t_bits >= 63 || q <= (1ull << p.t_bits)) return PENCIL_E_PARAMS;
+
+  PencilCtx* ctx = new (std::nothrow) PencilCtx();
+  if (!ctx) return PENCIL_E_CUDA;
+  ctx->params = p;
+  ctx->device = device;
+  ctx->n = n;
+  ctx->primes = qs;
+  DeviceGuard guard(device);
+
+  DevCtx& d = ctx->dev;
+  memset(&d, 0, sizeof(d));
+  d.log_n = p.log_n;
+  d.n = n;
+  d.L = p.num_primes;
+  d.t_bits = p.t_bits;
+  d.t_mask = (1ull << p.t_bits) - 1;
+  std::vector<ulonglong2> tf((size_t)d.L * n), ti((size_t)d.L * n);
+  for (int j = 0; j < d.L; ++j) {
+    const u64 q = qs[j];
+    const u64 psi = min_root_2n(q, 2ull * n);
+    ctx->psis.push_back(psi);
+    const u64 psi_inv = powmod(psi, q - 2, q);
+    for (int k = 0; k < n; ++k) {
+      const unsigned r = brv((unsigned)k, p.log_n);
+      const u64 w = powmod(psi, r, q), wi = powmod(psi_inv, r, q);
+      tf[(size_t)j * n + k] = make_ulonglong2(w, shoup(w, q));
+      ti[(size_t)j * n + k] = make_ulonglong2(wi, shoup(wi, q));
+    }
+    LimbConst& lc = d.limb[j];
+    lc.q = q;
+    lc.mu = (u64)((((u128)1) << 64) / q);
+    lc.r64 = (u64)((((u128)1) << 64) % q);
+    lc.r64s = shoup(lc.r64, q);
+    lc.ninv = powmod((u64)n, q - 2, q);
+    lc.ninvs = shoup(lc.ninv, q);
+    lc.delta = delta_mod(qs, p.t_bits, q);
+    lc.deltas = shoup(lc.delta, q);
+    u64 qt = 1;
+    for (int i = 0; i < d.L; ++i)
+      if (i != j) qt = mulmod(qt, qs[i] % q, q);
+    lc.qtil = powmod(qt, q - 2, q);
+    lc.qtils = shoup(lc.qtil, q);
+    const u128 th = floor_pow2_div(128 + p.t_bits, q);
+    lc.th_hi = (u64)(th >> 64);
+    lc.th_lo = (u64)th;
+  }
+  cudaError_t e1 = cudaMalloc(&ctx->tw_fwd, tf.size() * sizeof(ulonglong2));
+  cudaError_t e2 = cudaMalloc(&ctx->tw_inv, ti.size() * sizeof(ulonglong2));
+  cudaError_t e3 = cudaMalloc(&ctx->status, sizeof(int));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    pencil_ctx_destroy(ctx);
+    return PENCIL_E_CUDA;
+  }
+  if (cudaMemcpy(ctx->tw_fwd, tf.data(), tf.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->tw_inv, ti.data(), ti.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess || upload_cdt() != cudaSuccess) {
+    pencil_ctx_destroy(ctx);
+    return PENCIL_E_CUDA;
+  }
+  d.tw_fwd = ctx->tw_fwd;
+  d.tw_inv = ctx->tw_inv;
+  d.status = ctx->status;
+  *out = ctx;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_ctx_destroy(PencilCtx* ctx) {
+  if (!ctx) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  for (ProfRec& r : ctx->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  cudaFree(ctx->tw_fwd);
+  cudaFree(ctx->tw_inv);
+  cudaFree(ctx->status);
+  delete ctx;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis) {
+  if (!ctx || !primes || !psis) return PENCIL_E_ARG;
+  for (size_t j = 0; j < ctx->primes.size(); ++j) {
+    primes[j] = ctx->primes[j];
+    psis[j] = ctx->psis[j];
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_sync_status(PencilCtx* ctx, int32_t* status) {
+  if (!ctx || !status) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  int v = 0;
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(int)));
+  *status = (v & 1) ? PENCIL_E_NOISE : (v & 2) ? PENCIL_E_TIMEOUT : PENCIL_OK;
+  return PENCIL_OK;
+}
+
+// ================================================================== keys
+extern "C" int pencil_keygen(PencilCtx* ctx, uint64_t seed, PencilSecretKey** out, void* stream) {
+  if (!ctx || !out) return PENCIL_E_ARG;
+  *out = nullptr;
+  DeviceGuard guard(ctx->device);
+  PencilSecretKey* sk = new (std::nothrow) PencilSecretKey();
+  if (!sk) return PENCIL_E_CUDA;
+  sk->ctx = ctx;
+  if (cudaMalloc(&sk->sk, (size_t)ctx->dev.L * ctx->n * sizeof(ulonglong2)) != cudaSuccess) {
+    delete sk;
+    return PENCIL_E_CUDA;
+  }
+  ModeKeygen::Params P;
+  P.seed = seed;
+  P.sk = sk->sk;
+  if (ntt<ModeKeygen, false>(ctx->dev, P, 1, (cudaStream_t)stream) != cudaSuccess) {
+    pencil_sk_destroy(sk);
+    return PENCIL_E_CUDA;
+  }
+  *out = sk;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_sk_destroy(PencilSecretKey* sk) {
+  if (!sk) return PENCIL_E_ARG;
+  DeviceGuard guard(sk->ctx->device);
+  cudaFree(sk->sk);
+  delete sk;
+  return PENCIL_OK;
+}
+
+// ================================================================== plans
+static Accessor make_acc(i64 s0, i64 s1, i64 s2, i64 s3, int pr, int ps, int hr, int wr, i64 base = 0) {
+  Accessor a;
+  a.ptr = nullptr;
+  a.base = base;
+  a.s0 = s0;
+  a.s1 = s1;
+  a.s2 = s2;
+  a.s3 = s3;
+  a.pr = pr;
+  a.ps = ps;
+  a.hr = hr;
+  a.wr = wr;
+  return a;
+}
+
+// Maps the user's tensors of `role` onto one correlation
+//   y[a, o, i, j] = sum_{c, u, v} Wt[o, c, u, v] * V[a, c, i + u, j + v].
+static int role_setup(const PencilLayerDesc& L, int role, PencilPlan& P) {
+  const bool fc = L.kind == PENCIL_FC;
+  const i64 B = L.batch, ni = L.c_in, no = L.c_out;
+  if (fc) {
+    P.hw = 1;
+    if (role == PENCIL_ROLE_FWD) {
+      P.g = Geom{(int)B, (int)ni, (int)no, 1, 1, 1, 1};
+      P.acc_v = make_acc(ni, 1, 0, 0, 0, 0, 1, 1);
+      P.acc_w = make_acc(ni, 1, 0, 0, 0, 0, 1, 1);
+      P.acc_y = make_acc(no, 1, 0, 0, 0, 0, 1, 1);
+      P.co_out = (int)no;
+    } else if (role == PENCIL_ROLE_DGRAD) {
+      P.g = Geom{(int)B, (int)no, (int)ni, 1, 1, 1, 1};
+      P.acc_v = make_acc(no, 1, 0, 0, 0, 0, 1, 1);   // gY [B][n_o]
+      P.acc_w = make_acc(1, ni, 0, 0, 0, 0, 1, 1);   // Wt[i, o] = W[o, i]
+      P.acc_y = make_acc(ni, 1, 0, 0, 0, 0, 1, 1);   // gX [B][n_i]
+      P.co_out = (int)ni;
+    } else {
+      P.g = Geom{(int)ni, (int)B, (int)no, 1, 1, 1, 1};
+      P.acc_v = make_acc(1, ni, 0, 0, 0, 0, 1, 1);   // V[i, b] = X[b, i]
+      P.acc_w = make_acc(1, no, 0, 0, 0, 0, 1, 1);   // Wt[o, b] = gY[b, o]
+      P.acc_y = make_acc(1, ni, 0, 0, 0, 0, 1, 1);   // y[i, o] = gW[o, i]
+      P.co_out = (int)no;
+    }
+    return PENCIL_OK;
+  }
+  const i64 h = L.height, w = L.width, s = L.kernel, p = L.pad;
+  const i64 ho = h + 2 * p - s + 1, wo = w + 2 * p - s + 1;
+  const i64 Ci = ni, Co = no;
+  if (role == PENCIL_ROLE_FWD) {
+    P.g = Geom{(int)B, (int)Ci, (int)Co, (int)(h + 2 * p), (int)(w + 2 * p), (int)s, (int)s};
+    P.acc_v = make_acc(Ci * h * w, h * w, w, 1, (int)p, (int)p, (int)h, (int)w);
+    P.acc_w = make_acc(Ci * s * s, s * s, s, 1, 0, 0, (int)s, (int)s);
+    P.acc_y = make_acc(Co * ho * wo, ho * wo, wo, 1, 0, 0, (int)ho, (int)wo);
+    P.hw = ho * wo;
+    P.co_out = (int)Co;
+  } else if (role == PENCIL_ROLE_DGRAD) {
+    const i64 e = s - 1 - p;
+    P.g = Geom{(int)B, (int)Co, (int)Ci, (int)(ho + 2 * e), (int)(wo + 2 * e), (int)s, (int)s};
+    P.acc_v = make_acc(Co * ho * wo, ho * wo, wo, 1, (int)e, (int)e, (int)ho, (int)wo);
+    // Wt[c, o, u, v] = W[o, c, s-1-u, s-1-v]
+    P.acc_w = make_acc(s * s, Ci * s * s, -s, -1, 0, 0, (int)s, (int)s, (s - 1) * s + (s - 1));
+    P.acc_y = make_acc(Ci * h * w, h * w, w, 1, 0, 0, (int)h, (int)w);
+    P.hw = h * w;
+    P.co_out = (int)Ci;
+  } else {
+    P.g = Geom{(int)Ci, (int)B, (int)Co, (int)(h + 2 * p), (int)(w + 2 * p), (int)ho, (int)wo};
+    P.acc_v = make_acc(h * w, Ci * h * w, w, 1, (int)p, (int)p, (int)h, (int)w);   // V[c, b] = X[b, c]
+    P.acc_w = make_acc(ho * wo, Co * ho * wo, wo, 1, 0, 0, (int)ho, (int)wo);      // Wt[o, b] = gY[b, o]
+    P.acc_y = make_acc(s * s, Ci * s * s, s, 1, 0, 0, (int)s, (int)s);             // y[c, o] = gW[o, c]
+    P.hw = s * s;
+    P.co_out = (int)Co;
+  }
+  return PENCIL_OK;
+}
+
+static Counts counts_of(const Geom& g, const PencilPartition& p) {
+  return Counts{cdiv(g.B, p.bb), cdiv(g.Ho(), p.th), cdiv(g.Wo(), p.tw), cdiv(g.Ci, p.cib),
+                cdiv(g.KH, p.kth), cdiv(g.KW, p.ktw), cdiv(g.Co, p.cob)};
+}
+
+static bool part_valid(const Geom& g, const PencilPartition& p, int n) {
+  if (p.bb < 1 || p.cib < 1 || p.cob < 1 || p.th < 1 || p.tw < 1 || p.kth < 1 || p.ktw < 1) return false;
+  if (p.bb > g.B || p.cib > g.Ci || p.cob > g.Co || p.th > g.Ho() || p.tw > g.Wo() || p.kth > g.KH ||
+      p.ktw > g.KW)
+    return false;
+  const long long hw = (long long)(p.th + p.kth - 1) * (p.tw + p.ktw - 1);
+  return (long long)p.bb * p.cob * p.cib * hw <= n;
+}
+
+// Distinct values of ceil(x / d), d = 1..x (descending).
+static std::vector<int> ceil_divs(int x) {
+  std::vector<int> v;
+  for (int d = 1; d <= x; ++d) {
+    const int c = cdiv(x, d);
+    if (v.empty() || v.back() != c) v.push_back(c);
+  }
+  return v;
+}
+
+// Cost model of one call sequence of the role, in 32-bit multiply units:
+// limb-NTTs at 10 * (N/2) log2 N, ct x pt slot products at 8 per 64x64->128
+// multiply-add, bytes at 3 per byte (the multiply/HBM balance of the GPU).
+static double plan_cost(const Geom& g, const PencilPartition& p, int role, int n, int log_n, int L) {
+  const Counts c = counts_of(g, p);
+  const double M = (double)c.M(), K = (double)c.K(), NC = c.NC;
+  const double ntt_u = 10.0 * (n / 2) * log_n;
+  const double ln = (double)L * n;
+  double ntts, prods, bytes;
+  if (role == PENCIL_ROLE_WGRAD) {
+    ntts = L * (2 * M * K + 2 * K * NC + 2 * M * NC);
+    prods = 2 * M * K * NC;
+    bytes = 8 * ln * (2 * M * K * 2 + 2 * K * NC * 2 + K * NC * 2 + M * K * 2 + 2 * M * NC * 3);
+  } else {
+    ntts = L * (2 * M * K + K * NC + 2 * M * NC);
+    prods = M * K * NC;
+    bytes = 8 * ln * (2 * M * K * 2 + M * K * 2 + K * NC * 2 + 2 * M * NC * 3);
+  }
+  return ntts * ntt_u + prods * 2 * ln * 8 + bytes * 3;
+}
+
+static PencilPartition choose_partition(const Geom& g, int role, int n, int log_n, int L) {
+  PencilPartition best{1, 1, 1, 1, 1, 1, 1};
+  double best_cost = 1e300;
+  const std::vector<int> ths = ceil_divs(g.Ho()), tws = ceil_divs(g.Wo());
+  const std::vector<int> khs = ceil_divs(g.KH), kws = ceil_divs(g.KW);
+  const std::vector<int> cis = ceil_divs(g.Ci), cos_ = ceil_divs(g.Co), bs = ceil_divs(g.B);
+  for (int th : ths)
+    for (int tw : tws)
+      for (int kth : khs)
+        for (int ktw : kws) {
+          const long long hw = (long long)(th + kth - 1) * (tw + ktw - 1);
+          if (hw > n) continue;
+          const long long cap = n / hw;
+          for (int ci : cis) {
+            if (ci > cap) continue;
+            for (int co : cos_) {
+              if ((long long)ci * co > cap) continue;
+              const long long bmax = cap / ((long long)ci * co);
+              // the largest batch block that fits, as one of the distinct ceil values
+              int bb = 1;
+              for (int b : bs)
+                if (b <= bmax) {
+                  bb = b;
+                  break;
+                }
+              PencilPartition p{bb, ci, co, th, tw, kth, ktw};
+              if (!part_valid(g, p, n)) continue;
+              const double cost = plan_cost(g, p, role, n, log_n, L);
+              if (cost < best_cost) {
+                best_cost = cost;
+                best = p;
+              }
+            }
+          }
+        }
+  return best;
+}
+
+static inline u64 pack4(int a, int b, int c, int d) {
+  return (u64)(uint16_t)a | ((u64)(uint16_t)b << 16) | ((u64)(uint16_t)c << 32) | ((u64)(uint16_t)d << 48);
+}
+
+extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role,
+                                  const PencilPartition* part, PencilPlan** out) {
+  if (!ctx || !layer || !out) return PENCIL_E_ARG;
+  *out = nullptr;
+  if (role < PENCIL_ROLE_FWD || role > PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  const PencilLayerDesc& L = *layer;
+  if (L.kind != PENCIL_FC && L.kind != PENCIL_CONV) return PENCIL_E_ARG;
+  if (L.batch < 1 || L.c_in < 1 || L.c_out < 1) return PENCIL_E_SHAPE;
+  if (L.kind == PENCIL_FC && (L.height != 1 || L.width != 1 || L.kernel != 1 || L.pad != 0)) return PENCIL_E_SHAPE;
+  if (L.kind == PENCIL_CONV) {
+    if (L.height < 1 || L.width < 1 || L.kernel < 1 || L.pad < 0 || L.pad > L.kernel - 1) return PENCIL_E_SHAPE;
+    if (L.height + 2 * L.pad < L.kernel || L.width + 2 * L.pad < L.kernel) return PENCIL_E_SHAPE;
+  }
+  const int n = ctx->n;
+  if (L.batch > 65535 || L.c_in > 65535 || L.c_out > 65535 || L.height + 2 * L.pad > 65535 ||
+      L.width + 2 * L.pad > 65535)
+    return PENCIL_E_SHAPE;
+
+  PencilPlan* P = new (std::nothrow) PencilPlan();
+  if (!P) return PENCIL_E_CUDA;
+  P->ctx = ctx;
+  P->layer = L;
+  P->role = role;
+  role_setup(L, role, *P);
+  const Geom& g = P->g;
+  if (part) {
+    if (!part_valid(g, *part, n)) {
+      delete P;
+      return PENCIL_E_CAPACITY;
+    }
+    P->part = *part;
+  } else {
+    P->part = choose_partition(g, role, n, ctx->params.log_n, ctx->dev.L);
+    if (!part_valid(g, P->part, n)) {
+      delete P;
+      return PENCIL_E_CAPACITY;
+    }
+  }
+  const PencilPartition& p = P->part;
+  P->c = counts_of(g, p);
+  const Counts& c = P->c;
+  P->ct_in = c.M() * c.K();
+  P->pt = c.K() * c.NC;
+  P->ct_out = c.M() * c.NC;
+  P->products = c.M() * c.K() * c.NC;
+  if (P->ct_in > (1 << 30) || P->pt > (1 << 30) || P->ct_out > (1 << 30)) {
+    delete P;
+    return PENCIL_E_CAPACITY;
+  }
+  if (role == PENCIL_ROLE_WGRAD)
+    P->out_elems = (long long)L.c_out * L.c_in * L.kernel * L.kernel;
+  else if (role == PENCIL_ROLE_DGRAD)
+    P->out_elems = (long long)L.batch * L.c_in * L.height * L.width;
+  else
+    P->out_elems = (long long)g.B * g.Co * g.Ho() * g.Wo();
+
+  // --- packing tables (Appendix A index maps)
+  const int h = p.th + p.kth - 1, w = p.tw + p.ktw - 1;
+  const long long O = (long long)(p.cib - 1) * h * w + (long long)(p.kth - 1) * w + p.ktw - 1;
+  const long long blk = (long long)p.cob * p.cib * h * w;
+  std::vector<u64> tab(3 * (size_t)n, PENCIL_TAB_NONE);
+  for (int b = 0; b < p.bb; ++b)
+    for (int ch = 0; ch < p.cib; ++ch)
+      for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) tab[b * blk + (long long)ch * h * w + (long long)i * w + j] = pack4(b, ch, i, j);
+  for (int co = 0; co < p.cob; ++co)
+    for (int ch = 0; ch < p.cib; ++ch)
+      for (int u = 0; u < p.kth; ++u)
+        for (int v = 0; v < p.ktw; ++v)
+          tab[n + O + (long long)co * p.cib * h * w - (long long)ch * h * w - (long long)u * w - v] =
+              pack4(co, ch, u, v);
+  for (int b = 0; b < p.bb; ++b)
+    for (int co = 0; co < p.cob; ++co)
+      for (int i = 0; i < p.th; ++i)
+        for (int j = 0; j < p.tw; ++j)
+          tab[2 * (size_t)n + b * blk + O + (long long)co * p.cib * h * w + (long long)i * w + j] =
+              pack4(b, co, i, j);
+  std::vector<int4> org((size_t)(P->ct_in + P->pt + P->ct_out));
+  size_t o = 0;
+  for (long long m = 0; m < c.M(); ++m) {
+    const int mw = (int)(m % c.MTW), mh = (int)((m / c.MTW) % c.MTH), mb = (int)(m / ((long long)c.MTW * c.MTH));
+    for (long long k = 0; k < c.K(); ++k) {
+      const int kw = (int)(k % c.KTW), kh = (int)((k / c.KTW) % c.KTH), kc = (int)(k / ((long long)c.KTW * c.KTH));
+      org[o++] = make_int4(mb * p.bb, kc * p.cib, mh * p.th + kh * p.kth, mw * p.tw + kw * p.ktw);
+    }
+  }
+  for (long long k = 0; k < c.K(); ++k) {
+    const int kw = (int)(k % c.KTW), kh = (int)((k / c.KTW) % c.KTH), kc = (int)(k / ((long long)c.KTW * c.KTH));
+    for (int nn = 0; nn < c.NC; ++nn) org[o++] = make_int4(nn * p.cob, kc * p.cib, kh * p.kth, kw * p.ktw);
+  }
+  for (long long m = 0; m < c.M(); ++m) {
+    const int mw = (int)(m % c.MTW), mh = (int)((m / c.MTW) % c.MTH), mb = (int)(m / ((long long)c.MTW * c.MTH));
+    for (int nn = 0; nn < c.NC; ++nn) org[o++] = make_int4(mb * p.bb, nn * p.cob, mh * p.th, mw * p.tw);
+  }
+  DeviceGuard guard(ctx->device);
+  if (cudaMalloc(&P->d_tab, tab.size() * sizeof(u64)) != cudaSuccess ||
+      cudaMalloc(&P->d_org, org.size() * sizeof(int4)) != cudaSuccess ||
+      cudaMemcpy(P->d_tab, tab.data(), tab.size() * sizeof(u64), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(P->d_org, org.data(), org.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
+    pencil_plan_destroy(P);
+    return PENCIL_E_CUDA;
+  }
+  P->pk_v = Packing{P->d_tab, P->d_org, make_int4(g.B, g.Ci, g.H, g.W)};
+  P->pk_w = Packing{P->d_tab + n, P->d_org + P->ct_in, make_int4(g.Co, g.Ci, g.KH, g.KW)};
+  P->pk_y = Packing{P->d_tab + 2 * (size_t)n, P->d_org + P->ct_in + P->pt, make_int4(g.B, g.Co, g.Ho(), g.Wo())};
+
+  // --- workspace sizes (bytes, each region 256-byte aligned)
+  auto al = [](long long b) { return (b + 255) / 256 * 256; };
+  const long long lnb = (long long)ctx->dev.L * n * 8;
+  P->ws_encrypt = al(std::max(P->ct_in, P->pt) * (long long)n);
+  P->ws_forward = al(P->ct_in * lnb) + al(P->ct_out * (long long)n * 8);
+  if (role == PENCIL_ROLE_WGRAD)
+    P->ws_backward = al(P->pt * lnb) + al(P->ct_in * lnb) + al(P->ct_out * (long long)n * 8);
+  else
+    P->ws_backward = P->ws_forward;
+  P->ws_decrypt = al(P->ct_out * lnb);
+  *out = P;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_plan_destroy(PencilPlan* P) {
+  if (!P) return PENCIL_E_ARG;
+  DeviceGuard guard(P->ctx->device);
+  cudaFree(P->d_tab);
+  cudaFree(P->d_org);
+  delete P;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_plan_sizes(const PencilPlan* P, PencilPlanSizes* s) {
+  if (!P || !s) return PENCIL_E_ARG;
+  s->part = P->part;
+  s->ct_in = P->ct_in;
+  s->pt = P->pt;
+  s->ct_out = P->ct_out;
+  s->products = P->products;
+  s->ct_words = 2ll * P->ctx->dev.L * P->ctx->n;
+  s->pt_words = (long long)P->ctx->dev.L * P->ctx->n;
+  s->out_elems = P->out_elems;
+  s->ws_encrypt = P->ws_encrypt;
+  s->ws_forward = P->ws_forward;
+  s->ws_backward = P->ws_backward;
+  s->ws_decrypt = P->ws_decrypt;
+  return PENCIL_OK;
+}
+
+// ================================================================== hot path
+extern "C" int encode_weights(PencilCtx* ctx, const PencilPlan* P, int32_t operand, const int64_t* values,
+                              uint64_t* pt, void* stream) {
+  if (!ctx || !P || !values || !pt || P->ctx != ctx) return PENCIL_E_ARG;
+  if (operand != PENCIL_OPERAND_INPUT && operand != PENCIL_OPERAND_KERNEL) return PENCIL_E_ARG;
+  if (!aligned16(pt)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  ModeEncode::Params M;
+  M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
+  M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
+  M.ac.ptr = reinterpret_cast<const u64*>(values);
+  M.pt = pt;
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
+  {
+    PROF(ctx, PENCIL_K_NTT_ENCODE, (cudaStream_t)stream);
+    CUDA_TRY((ntt<ModeEncode, false>(ctx->dev, M, (int)count, (cudaStream_t)stream)));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* P, int32_t operand,
+                             const uint64_t* share, uint64_t seed, uint64_t* ct, void* ws, size_t ws_bytes,
+                             void* stream) {
+  if (!ctx || !sk || !P || !share || !ct || !ws || P->ctx != ctx || sk->ctx != ctx) return PENCIL_E_ARG;
+  if (operand != PENCIL_OPERAND_INPUT && operand != PENCIL_OPERAND_KERNEL) return PENCIL_E_ARG;
+  if (!aligned16(ct) || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_encrypt) return PENCIL_E_CAPACITY;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
+  int8_t* err = reinterpret_cast<int8_t*>(ws);
+  {
+    PROF(ctx, PENCIL_K_SAMPLE_ERR, s);
+    CUDA_TRY(launch_sample_err(seed, (int)count, ctx->n, err, s));
+  }
+  ModeEncrypt::Params M;
+  M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
+  M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
+  M.ac.ptr = share;
+  M.err = err;
+  M.sk = sk->sk;
+  M.ct = ct;
+  M.seed = seed;
+  {
+    PROF(ctx, PENCIL_K_NTT_ENCRYPT, s);
+    CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+  }
+  return PENCIL_OK;
+}
+
+// Alg. 1 steps 2-3 for a FWD or DGRAD plan (shared by forward and backward).
+static int alg1(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, const u64* pt, const u64* x0, const u64* bias,
+                u64 mask_seed, u64* ct_out, u64* y0, char* ws, cudaStream_t s) {
+  const long long lnw = (long long)ctx->dev.L * ctx->n;
+  u64* c0p = reinterpret_cast<u64*>(ws);
+  u64* mpoly = reinterpret_cast<u64*>(ws + (P->ct_in * lnw * 8 + 255) / 256 * 256);
+  ModeAddPlain::Params A;
+  A.pk = P->pk_v;
+  A.ac = P->acc_v;
+  A.ac.ptr = x0;
+  A.ct_in = ct_in;
+  A.out_c0 = c0p;
+  {
+    PROF(ctx, PENCIL_K_NTT_ADDPLAIN, s);
+    CUDA_TRY((ntt<ModeAddPlain, false>(ctx->dev, A, (int)P->ct_in, s)));
+  }
+  MacParams M;
+  memset(&M, 0, sizeof(M));
+  M.a0 = c0p;
+  M.a0_stride = lnw;
+  M.a1 = ct_in + lnw;
+  M.a1_stride = 2 * lnw;
+  M.b = pt;
+  M.b_stride = lnw;
+  M.out = ct_out;
+  M.M = (int)P->c.M();
+  M.K = (int)P->c.K();
+  M.NC = P->c.NC;
+  M.lanes = (int)lnw;
+  {
+    PROF(ctx, PENCIL_K_MAC, s);
+    CUDA_TRY(launch_mac(ctx->dev, M, false, s));
+  }
+  Accessor ay = P->acc_y;
+  {
+    PROF(ctx, PENCIL_K_MASK_POLY, s);
+    CUDA_TRY(launch_mask_poly(ctx->dev, P->pk_y, ay, mask_seed, (int)P->ct_out, mpoly, s));
+  }
+  ModeMask::Params K;
+  K.mpoly = mpoly;
+  K.ct = ct_out;
+  {
+    PROF(ctx, PENCIL_K_NTT_MASK, s);
+    CUDA_TRY((ntt<ModeMask, false>(ctx->dev, K, (int)P->ct_out, s)));
+  }
+  {
+    PROF(ctx, PENCIL_K_MO_SHARE, s);
+    CUDA_TRY(launch_mo_share(mask_seed, P->out_elems, ctx->dev.t_mask, bias, P->hw, P->co_out, y0, s));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int he_linear_forward(PencilCtx* ctx, const PencilPlan* P, const uint64_t* ct_in, const uint64_t* pt,
+                                 const uint64_t* x0, const uint64_t* bias, uint64_t mask_seed, uint64_t* ct_out,
+                                 uint64_t* y0, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !P || !ct_in || !pt || !x0 || !ct_out || !y0 || !ws || P->ctx != ctx) return PENCIL_E_ARG;
+  if (P->role == PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  if (bias && P->role != PENCIL_ROLE_FWD) return PENCIL_E_ARG;
+  if (!aligned16(ct_in) || !aligned16(pt) || !aligned16(ct_out) || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_forward) return PENCIL_E_CAPACITY;
+  DeviceGuard guard(ctx->device);
+  return alg1(ctx, P, ct_in, pt, x0, bias, mask_seed, ct_out, y0, reinterpret_cast<char*>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const PencilPlan* Pw,
+                                  const uint64_t* ct_gy1_d, const uint64_t* pt_wt, const uint64_t* ct_x1_w,
+                                  const uint64_t* ct_gy1_w, const uint64_t* gy0, const uint64_t* x0,
+                                  uint64_t mask_seed_x, uint64_t mask_seed_w, uint64_t* ct_gx, uint64_t* gx0,
+                                  uint64_t* ct_gw, uint64_t* gw_mask, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || (!Pd && !Pw) || !ws || !aligned16(ws)) return PENCIL_E_ARG;
+  if (Pd && (Pd->ctx != ctx || Pd->role != PENCIL_ROLE_DGRAD || !ct_gy1_d || !pt_wt || !gy0 || !ct_gx || !gx0 ||
+             !aligned16(ct_gy1_d) || !aligned16(pt_wt) || !aligned16(ct_gx)))
+    return PENCIL_E_ARG;
+  if (Pw && (Pw->ctx != ctx || Pw->role != PENCIL_ROLE_WGRAD || !ct_x1_w || !ct_gy1_w || !gy0 || !x0 || !ct_gw ||
+             !gw_mask || !aligned16(ct_x1_w) || !aligned16(ct_gy1_w) || !aligned16(ct_gw)))
+    return PENCIL_E_ARG;
+  if (Pd && Pw) {
+    const PencilLayerDesc &a = Pd->layer, &b = Pw->layer;
+    if (memcmp(&a, &b, sizeof(a)) != 0) return PENCIL_E_SHAPE;
+  }
+  const long long need = (Pd ? Pd->ws_backward : 0) + (Pw ? Pw->ws_backward : 0);
+  if ((long long)ws_bytes < need) return PENCIL_E_CAPACITY;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  char* w = reinterpret_cast<char*>(ws);
+  if (Pd) {
+    int rc = alg1(ctx, Pd, ct_gy1_d, pt_wt, gy0, nullptr, mask_seed_x, ct_gx, gx0, w, s);
+    if (rc != PENCIL_OK) return rc;
+    w += Pd->ws_backward;
+  }
+  if (Pw) {
+    const long long lnw = (long long)ctx->dev.L * ctx->n;
+    auto al = [](long long b) { return (b + 255) / 256 * 256; };
+    u64* pt_gy0 = reinterpret_cast<u64*>(w);
+    u64* pt_x0 = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8));
+    u64* mpoly = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8) + al(Pw->ct_in * lnw * 8));
+    ModeEncode::Params E1;
+    E1.pk = Pw->pk_w;
+    E1.ac = Pw->acc_w;
+    E1.ac.ptr = gy0;
+    E1.pt = pt_gy0;
+    {
+      PROF(ctx, PENCIL_K_NTT_ENCODE, s);
+      CUDA_TRY((ntt<ModeEncode, false>(ctx->dev, E1, (int)Pw->pt, s)));
+    }
+    ModeEncode::Params E2;
+    E2.pk = Pw->pk_v;
+    E2.ac = Pw->acc_v;
+    E2.ac.ptr = x0;
+    E2.pt = pt_x0;
+    {
+      PROF(ctx, PENCIL_K_NTT_ENCODE, s);
+      CUDA_TRY((ntt<ModeEncode, false>(ctx->dev, E2, (int)Pw->ct_in, s)));
+    }
+    MacParams M;
+    memset(&M, 0, sizeof(M));
+    M.a0 = ct_x1_w;
+    M.a0_stride = 2 * lnw;
+    M.a1 = ct_x1_w + lnw;
+    M.a1_stride = 2 * lnw;
+    M.b = pt_gy0;
+    M.b_stride = lnw;
+    M.pa = pt_x0;
+    M.pa_stride = lnw;
+    M.cb0 = ct_gy1_w;
+    M.cb1 = ct_gy1_w + lnw;
+    M.cb_stride = 2 * lnw;
+    M.out = ct_gw;
+    M.M = (int)Pw->c.M();
+    M.K = (int)Pw->c.K();
+    M.NC = Pw->c.NC;
+    M.lanes = (int)lnw;
+    {
+      PROF(ctx, PENCIL_K_MAC_DUAL, s);
+      CUDA_TRY(launch_mac(ctx->dev, M, true, s));
+    }
+    {
+      PROF(ctx, PENCIL_K_MASK_POLY, s);
+      CUDA_TRY(launch_mask_poly(ctx->dev, Pw->pk_y, Pw->acc_y, mask_seed_w, (int)Pw->ct_out, mpoly, s));
+    }
+    ModeMask::Params K;
+    K.mpoly = mpoly;
+    K.ct = ct_gw;
+    {
+      PROF(ctx, PENCIL_K_NTT_MASK, s);
+      CUDA_TRY((ntt<ModeMask, false>(ctx->dev, K, (int)Pw->ct_out, s)));
+    }
+    {
+      PROF(ctx, PENCIL_K_MO_SHARE, s);
+      CUDA_TRY(launch_mo_share(mask_seed_w, Pw->out_elems, ctx->dev.t_mask, nullptr, 1, 1, gw_mask, s));
+    }
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* P,
+                                const uint64_t* ct_out, uint64_t* y1, int32_t check_noise, void* ws, size_t ws_bytes,
+                                void* stream) {
+  if (!ctx || !sk || !P || !ct_out || !y1 || !ws || P->ctx != ctx || sk->ctx != ctx) return PENCIL_E_ARG;
+  if (!aligned16(ct_out) || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_decrypt) return PENCIL_E_CAPACITY;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  ModeDecrypt::Params D;
+  D.ct = ct_out;
+  D.sk = sk->sk;
+  D.out = reinterpret_cast<u64*>(ws);
+  {
+    PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
+    CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->ct_out, s)));
+  }
+  {
+    PROF(ctx, PENCIL_K_DECRYPT_COMBINE, s);
+    CUDA_TRY(launch_decrypt_combine(ctx->dev, P->pk_y, P->acc_y, D.out, (int)P->ct_out, check_noise ? 1 : 0, y1, s));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream) {
+  if (!ctx || !polys || count < 0 || count > (1ll << 31) - 1) return PENCIL_E_ARG;
+  if (!aligned16(polys)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  ModeRaw::Params R;
+  R.polys = polys;
+  if (inverse) {
+    PROF(ctx, PENCIL_K_INTT_RAW, (cudaStream_t)stream);
+    CUDA_TRY((ntt<ModeRaw, true>(ctx->dev, R, (int)count, (cudaStream_t)stream)));
+  } else {
+    PROF(ctx, PENCIL_K_NTT_RAW, (cudaStream_t)stream);
+    CUDA_TRY((ntt<ModeRaw, false>(ctx->dev, R, (int)count, (cudaStream_t)stream)));
+  }
+  return PENCIL_OK;
+}
+
+// ================================================================== profiling
+extern "C" int pencil_profile(PencilCtx* ctx, int32_t enable) {
+  if (!ctx) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  if (enable) {
+    for (ProfRec& r : ctx->prof) {
+      ctx->pool.push_back(r.a);
+      ctx->pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+  }
+  ctx->prof_on = enable != 0;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t max_entries, int32_t* n_entries) {
+  if (!ctx || !n_entries || (max_entries > 0 && !out)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  double ms[PENCIL_K_COUNT] = {0};
+  int launches[PENCIL_K_COUNT] = {0};
+  for (ProfRec& r : ctx->prof) {
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.kernel] += t;
+    launches[r.kernel] += 1;
+  }
+  int n = 0;
+  for (int k = 0; k < PENCIL_K_COUNT; ++k) {
+    if (!launches[k]) continue;
+    if (n < max_entries) out[n] = PencilProfEntry{k, launches[k], ms[k]};
+    ++n;
+  }
+  *n_entries = n;
+  return PENCIL_OK;
+}

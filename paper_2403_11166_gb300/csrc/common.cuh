@@ -1,0 +1,191 @@
+// Device-side building blocks of the Pencil HE hot path on sm_103a:
+// 64-bit modular arithmetic (Shoup, Barrett, Harvey lazy butterflies),
+// Philox4x64-10, and the parameter structs every kernel receives by value.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef uint32_t u32;
+
+#define PENCIL_MAX_LIMBS 4
+
+// ------------------------------------------------------------------ structs
+// Per-limb constants for q_j (all computed on the host at context creation).
+struct LimbConst {
+  u64 q;
+  u64 mu;            // floor(2^64 / q)                           (Barrett)
+  u64 r64, r64s;     // 2^64 mod q and its Shoup companion
+  u64 ninv, ninvs;   // N^{-1} mod q                              (INTT scaling)
+  u64 delta, deltas; // floor(q_total / t) mod q                  (BFV Delta)
+  u64 qtil, qtils;   // (q_total / q_j)^{-1} mod q_j              (CRT)
+  u64 th_hi, th_lo;  // floor(2^(128 + t_bits) / q_j), 128 bits   (t / q_j in 0.128 fixed point)
+};
+
+struct DevCtx {
+  int log_n;
+  int n;
+  int L;
+  int t_bits;
+  u64 t_mask;
+  LimbConst limb[PENCIL_MAX_LIMBS];
+  const ulonglong2* tw_fwd;  // [L][N] (psi^brv(k), Shoup companion)
+  const ulonglong2* tw_inv;  // [L][N] (psi^-brv(k), Shoup companion)
+  int* status;               // device status word (atomicOr of error bits)
+};
+
+// A strided view of a user tensor seen as (a, b, r, s) with spatial zero
+// padding: element = ptr[base + a*s0 + b*s1 + (r-pr)*s2 + (s-ps)*s3] when
+// 0 <= r-pr < hr and 0 <= s-ps < wr, else 0.
+struct Accessor {
+  const u64* ptr;
+  i64 base;
+  i64 s0, s1, s2, s3;
+  int pr, ps, hr, wr;
+};
+
+// Packing of one operand position class (inputs, kernels or outputs):
+// tab[e] = local (a, b, r, s) of coefficient e packed as 4 x 16 bits, or
+// all-ones when coefficient e carries nothing; org[idx] = the block origin of
+// polynomial idx; bound = the geometry extent of (a, b, r, s).
+struct Packing {
+  const u64* tab;
+  const int4* org;
+  int4 bound;
+};
+
+#define PENCIL_TAB_NONE 0xFFFFFFFFFFFFFFFFull
+
+// ------------------------------------------------------------------ 64-bit modular arithmetic
+__device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
+
+// a * w mod q in [0, 2q), w < q, ws = floor(w 2^64 / q), any a < 2^64 (Shoup).
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
+  u64 qt = mulhi64(a, ws);
+  return a * w - qt * q;
+}
+
+__device__ __forceinline__ u64 csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+__device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 ws, u64 q) {
+  return csub(mul_shoup_lazy(a, w, ws, q), q);
+}
+
+// x mod q for any x < 2^64 with mu = floor(2^64 / q) (Barrett, one correction).
+__device__ __forceinline__ u64 reduce64(u64 x, const LimbConst& c) {
+  u64 qt = mulhi64(x, c.mu);
+  return csub(x - qt * c.q, c.q);
+}
+
+// (hi * 2^64 + lo) mod q, canonical.
+__device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const LimbConst& c) {
+  u64 rh = reduce64(hi, c);
+  u64 t = mul_shoup_lazy(rh, c.r64, c.r64s, c.q);  // [0, 2q)
+  u64 rl = reduce64(lo, c);
+  u64 s = t + rl;                                   // [0, 3q)
+  s = csub(s, 2 * c.q);
+  return csub(s, c.q);
+}
+
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// 128-bit accumulate: (hi, lo) += a * b.
+__device__ __forceinline__ void mac128(u64& lo, u64& hi, u64 a, u64 b) {
+  u64 plo = a * b;
+  u64 phi = mulhi64(a, b);
+  lo += plo;
+  hi += phi + (lo < plo ? 1ull : 0ull);
+}
+
+// Harvey Cooley-Tukey butterfly: x, y in [0, 4q) -> x + w y, x - w y in [0, 4q).
+__device__ __forceinline__ void ct_butterfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
+  u64 a = x >= q2 ? x - q2 : x;
+  u64 t = mul_shoup_lazy(y, w, ws, q);
+  x = a + t;
+  y = a - t + q2;
+}
+
+// Harvey Gentleman-Sande butterfly: x, y in [0, 2q) -> x + y, (x - y) w in [0, 2q).
+__device__ __forceinline__ void gs_butterfly(u64& x, u64& y, u64 w, u64 ws, u64 q, u64 q2) {
+  u64 s = x + y;
+  s = s >= q2 ? s - q2 : s;
+  u64 d = x - y + q2;
+  x = s;
+  y = mul_shoup_lazy(d, w, ws, q);
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 canon4(u64 x, u64 q, u64 q2) {
+  x = x >= q2 ? x - q2 : x;
+  return x >= q ? x - q : x;
+}
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Salmon et al., SC'11: two 64x64->128 products per round on counter words 0
+// and 2, high halves mixed with words 1, 3 and the round key; Weyl key schedule.
+struct Philox4 {
+  u64 v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1) {
+  const u64 M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const u64 W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+    u64 lo0 = M0 * c0, hi0 = mulhi64(M0, c0);
+    u64 lo1 = M1 * c2, hi1 = mulhi64(M1, c2);
+    u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  Philox4 o;
+  o.v[0] = c0;
+  o.v[1] = c1;
+  o.v[2] = c2;
+  o.v[3] = c3;
+  return o;
+}
+
+// Stream domains (the second key word).
+#define PENCIL_DOM_SECRET 1ull
+#define PENCIL_DOM_A 2ull
+#define PENCIL_DOM_E 3ull
+#define PENCIL_DOM_MASK 4ull
+#define PENCIL_DOM_MASK_PAD 5ull
+
+// ------------------------------------------------------------------ packing gathers
+__device__ __forceinline__ u64 gather(const Packing& pk, const Accessor& ac, int idx, int e) {
+  u64 ent = __ldg(pk.tab + e);
+  if (ent == PENCIL_TAB_NONE) return 0;
+  int4 o = __ldg(pk.org + idx);
+  int a = o.x + (int)(ent & 0xffff);
+  int b = o.y + (int)((ent >> 16) & 0xffff);
+  int r = o.z + (int)((ent >> 32) & 0xffff);
+  int s = o.w + (int)(ent >> 48);
+  if (a >= pk.bound.x || b >= pk.bound.y || r >= pk.bound.z || s >= pk.bound.w) return 0;
+  r -= ac.pr;
+  s -= ac.ps;
+  if ((unsigned)r >= (unsigned)ac.hr || (unsigned)s >= (unsigned)ac.wr) return 0;
+  return __ldg(ac.ptr + ac.base + a * ac.s0 + b * ac.s1 + r * ac.s2 + s * ac.s3);
+}
+
+// Output flat index of coefficient e of output polynomial idx, or -1.
+__device__ __forceinline__ i64 out_index(const Packing& pk, const Accessor& ac, int idx, int e) {
+  u64 ent = __ldg(pk.tab + e);
+  if (ent == PENCIL_TAB_NONE) return -1;
+  int4 o = __ldg(pk.org + idx);
+  int a = o.x + (int)(ent & 0xffff);
+  int b = o.y + (int)((ent >> 16) & 0xffff);
+  int r = o.z + (int)((ent >> 32) & 0xffff);
+  int s = o.w + (int)(ent >> 48);
+  if (a >= pk.bound.x || b >= pk.bound.y || r >= pk.bound.z || s >= pk.bound.w) return -1;
+  return ac.base + a * ac.s0 + b * ac.s1 + r * ac.s2 + s * ac.s3;
+}

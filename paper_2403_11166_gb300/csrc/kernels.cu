@@ -1,0 +1,230 @@
+// Element-wise kernels of the hot path: the NTT-domain ct x pt
+// multiply-accumulate (Alg. 1 step 2 / Alg. 2 step 2), the samplers for the
+// encryption error and the re-mask (Alg. 1 step 3), the MO's output share,
+// and the RNS scale-and-round of decryption (Alg. 1 step 4).
+#include "cdt_table.h"
+#include "kernels.h"
+
+namespace pencil {
+
+__constant__ u64 c_cdt[PENCIL_CDT_LEN];
+
+cudaError_t upload_cdt() {
+  return cudaMemcpyToSymbol(c_cdt, kPencilCdt, sizeof(kPencilCdt));
+}
+
+// ------------------------------------------------------------------ MAC
+// acc[m, n] = sum_k A[m, k] * B[k, n] (+ A'[m, k] * B'[k, n] for Alg. 2),
+// slot-wise mod q_j, 128-bit lazy accumulation, one reduction per output.
+// Thread = one slot (limb, coefficient) of NT consecutive output columns n.
+template <int NT, bool DUAL>
+__global__ void __launch_bounds__(256) k_mac(DevCtx ctx, MacParams P) {
+  const int lane = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lane >= P.lanes) return;
+  const int n0 = blockIdx.y * NT;
+  const int m = blockIdx.z + P.m_base;
+  const int nn = min(NT, P.NC - n0);
+  const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
+  u64 lo0[NT], hi0[NT], lo1[NT], hi1[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) lo0[j] = hi0[j] = lo1[j] = hi1[j] = 0;
+  const int fold = DUAL ? 64 : 128;   // products per accumulator stay below 2^128
+  for (int k = 0; k < P.K; ++k) {
+    const size_t mk = (size_t)m * P.K + k;
+    const u64 a0 = __ldg(P.a0 + mk * P.a0_stride + lane);
+    const u64 a1 = __ldg(P.a1 + mk * P.a1_stride + lane);
+    u64 pa = 0;
+    if constexpr (DUAL) pa = __ldg(P.pa + mk * P.pa_stride + lane);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      if (j < nn) {
+        const size_t kn = (size_t)k * P.NC + n0 + j;
+        const u64 b = __ldg(P.b + kn * P.b_stride + lane);
+        mac128(lo0[j], hi0[j], a0, b);
+        mac128(lo1[j], hi1[j], a1, b);
+        if constexpr (DUAL) {
+          const u64 c0 = __ldg(P.cb0 + kn * P.cb_stride + lane);
+          const u64 c1 = __ldg(P.cb1 + kn * P.cb_stride + lane);
+          mac128(lo0[j], hi0[j], c0, pa);
+          mac128(lo1[j], hi1[j], c1, pa);
+        }
+      }
+    }
+    if ((k % fold) == fold - 1) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        lo0[j] = reduce128(hi0[j], lo0[j], lc);
+        lo1[j] = reduce128(hi1[j], lo1[j], lc);
+        hi0[j] = hi1[j] = 0;
+      }
+    }
+  }
+  const size_t ln = (size_t)P.lanes;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (j < nn) {
+      const size_t o = ((size_t)m * P.NC + n0 + j) * 2 * ln + lane;
+      P.out[o] = reduce128(hi0[j], lo0[j], lc);
+      P.out[o + ln] = reduce128(hi1[j], lo1[j], lc);
+    }
+  }
+}
+
+cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  constexpr int NT = 8;
+  const int threads = 256;
+  MacParams P = P0;
+  const unsigned gx = (unsigned)((P.lanes + threads - 1) / threads);
+  const unsigned gy = (unsigned)((P.NC + NT - 1) / NT);
+  for (int base = 0; base < P0.M; base += 65535) {
+    P.m_base = base;
+    dim3 grid(gx, gy, (unsigned)min(65535, P0.M - base));
+    if (dual)
+      k_mac<NT, true><<<grid, threads, 0, s>>>(ctx, P);
+    else
+      k_mac<NT, false><<<grid, threads, 0, s>>>(ctx, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ samplers
+// Encryption error: |e| = #{j : T[j] <= w mod 2^63}, sign = top bit of w,
+// w = Philox(key (seed, 3), counter (i/4, ct, 0, 0)) word i%4.
+__global__ void k_sample_err(u64 seed, int count, int n, int8_t* out) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = n >> 2;
+  if (id >= (long long)count * per) return;
+  const int ct = (int)(id / per);
+  const int blk = (int)(id % per);
+  const Philox4 w = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_E);
+  char4 r;
+  int8_t v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const u64 u = w.v[i] & 0x7FFFFFFFFFFFFFFFull;
+    int mag = 0;
+#pragma unroll
+    for (int j = 0; j < PENCIL_CDT_LEN; ++j) mag += (u >= c_cdt[j]) ? 1 : 0;
+    v[i] = (int8_t)((w.v[i] >> 63) ? -mag : mag);
+  }
+  r.x = v[0];
+  r.y = v[1];
+  r.z = v[2];
+  r.w = v[3];
+  reinterpret_cast<char4*>(out + (size_t)ct * n)[blk] = r;
+}
+
+cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStream_t s) {
+  const long long total = (long long)count * (n >> 2);
+  if (total == 0) return cudaSuccess;
+  k_sample_err<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, count, n, out);
+  return cudaGetLastError();
+}
+
+// Mask polynomial of each output ciphertext: at coefficients carrying output
+// element `flat`, Philox(key (seed, 4), counter (flat/4, 0, 0, 0)) word flat%4;
+// elsewhere Philox(key (seed, 5), counter (i/4, ct, 0, 0)) word i%4; mod t.
+__global__ void k_mask_poly(DevCtx ctx, Packing pk, Accessor ac, u64 seed, int count, u64* out) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  const int per = n >> 2;
+  if (id >= (long long)count * per) return;
+  const int ct = (int)(id / per);
+  const int blk = (int)(id % per);
+  const Philox4 pad = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_MASK_PAD);
+  u64 r[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const i64 flat = out_index(pk, ac, ct, 4 * blk + i);
+    u64 w = pad.v[i];
+    if (flat >= 0) {
+      const Philox4 el = philox4x64((u64)(flat >> 2), 0ull, 0ull, 0ull, seed, PENCIL_DOM_MASK);
+      w = el.v[flat & 3];
+    }
+    r[i] = w & ctx.t_mask;
+  }
+  ulonglong2* o = reinterpret_cast<ulonglong2*>(out + (size_t)ct * n + 4 * blk);
+  o[0] = make_ulonglong2(r[0], r[1]);
+  o[1] = make_ulonglong2(r[2], r[3]);
+}
+
+cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed, int count, u64* out,
+                             cudaStream_t s) {
+  const long long total = (long long)count * (ctx.n >> 2);
+  if (total == 0) return cudaSuccess;
+  k_mask_poly<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, seed, count, out);
+  return cudaGetLastError();
+}
+
+// MO share: y0[flat] = s[flat] (+ bias[(flat / hw) % co]) mod t.
+__global__ void k_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0) {
+  const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk * 4 >= count) return;
+  const Philox4 w = philox4x64((u64)blk, 0ull, 0ull, 0ull, seed, PENCIL_DOM_MASK);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long flat = blk * 4 + i;
+    if (flat < count) {
+      u64 v = w.v[i] & t_mask;
+      if (bias) v = (v + __ldg(bias + (flat / hw) % co)) & t_mask;
+      y0[flat] = v;
+    }
+  }
+}
+
+cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,
+                            cudaStream_t s) {
+  const long long blocks = (count + 3) / 4;
+  if (blocks == 0) return cudaSuccess;
+  k_mo_share<<<(unsigned)((blocks + 255) / 256), 256, 0, s>>>(seed, count, t_mask, bias, hw, co, y0);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ decryption, second half
+// y_j = x_j * (q/q_j)^{-1} mod q_j (first half); then
+//   t x / q = sum_j y_j t / q_j - v t  (v integer),
+// so round(t x / q) mod t = round(sum_j y_j th_j / 2^128) mod t with
+// th_j = floor(2^(128 + t_bits) / q_j).  The sum is kept as a 128-bit window
+// (64 integer bits, 64 fraction bits); truncation error < L * 2^-63.
+__global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int count, int check,
+                                  u64* y1) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  if (id >= (long long)count * n) return;
+  const int ct = (int)(id / n);
+  const int e = (int)(id % n);
+  const i64 flat = out_index(pk, ac, ct, e);
+  if (flat < 0) return;
+  u64 s_lo = 0, s_hi = 0;
+  for (int j = 0; j < ctx.L; ++j) {
+    const LimbConst& lc = ctx.limb[j];
+    const u64 y = __ldg(yres + ((size_t)ct * ctx.L + j) * n + e);
+    const u64 a_hi = __umul64hi(y, lc.th_lo);
+    const u64 b_lo = y * lc.th_hi;
+    const u64 b_hi = __umul64hi(y, lc.th_hi);
+    const u64 w_lo = b_lo + a_hi;
+    const u64 w_hi = b_hi + (w_lo < b_lo ? 1ull : 0ull);
+    s_lo += w_lo;
+    s_hi += w_hi + (s_lo < w_lo ? 1ull : 0ull);
+  }
+  if (check) {
+    const i64 frac = (i64)s_lo;   // signed distance to the nearest integer, units of 2^-64
+    const u64 mag = frac < 0 ? (u64)(-frac) : (u64)frac;
+    if (mag >= (1ull << 62)) atomicOr(ctx.status, 1);
+  }
+  const u64 r_lo = s_lo + (1ull << 63);
+  const u64 r_hi = s_hi + (r_lo < s_lo ? 1ull : 0ull);
+  y1[flat] = r_hi & ctx.t_mask;
+}
+
+cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
+                                   int count, int check, u64* y1, cudaStream_t s) {
+  const long long total = (long long)count * ctx.n;
+  if (total == 0) return cudaSuccess;
+  k_decrypt_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, yres, count, check, y1);
+  return cudaGetLastError();
+}
+
+}  // namespace pencil

@@ -1,0 +1,58 @@
+// Host-side launchers of the hot-path kernels (implemented in kernels.cu and
+// ntt12.cu / ntt13.cu / ntt14.cu).
+#pragma once
+#include "ntt.cuh"
+
+namespace pencil {
+
+// Operands of the NTT-domain multiply-accumulate.  All arrays are indexed
+// [poly][...][lanes]; `*_stride` is the distance in words between consecutive
+// polynomials of that operand, lanes = L * N.
+struct MacParams {
+  const u64* a0;     // A[m, k] first component  (ciphertext c0, or c0 + Delta x0)
+  i64 a0_stride;
+  const u64* a1;     // A[m, k] second component (ciphertext c1)
+  i64 a1_stride;
+  const u64* b;      // B[k, n] plaintext
+  i64 b_stride;
+  const u64* pa;     // Alg. 2: A'[m, k] plaintext
+  i64 pa_stride;
+  const u64* cb0;    // Alg. 2: B'[k, n] ciphertext c0
+  const u64* cb1;    //                      and c1
+  i64 cb_stride;
+  u64* out;          // [M * NC][2][lanes]
+  int M, K, NC;
+  int lanes;
+  int m_base;
+};
+
+cudaError_t upload_cdt();
+cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P, bool dual, cudaStream_t s);
+cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStream_t s);
+cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed, int count, u64* out,
+                             cudaStream_t s);
+cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,
+                            cudaStream_t s);
+cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
+                                   int count, int check, u64* y1, cudaStream_t s);
+
+PENCIL_NTT_INSTANTIATE(extern, 12)
+PENCIL_NTT_INSTANTIATE(extern, 13)
+PENCIL_NTT_INSTANTIATE(extern, 14)
+
+// Dispatch on log2(N) at run time.
+template <class Mode, bool INV>
+cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
+  switch (ctx.log_n) {
+    case 12:
+      return launch_ntt<12, Mode, INV>(ctx, P, count, s);
+    case 13:
+      return launch_ntt<13, Mode, INV>(ctx, P, count, s);
+    case 14:
+      return launch_ntt<14, Mode, INV>(ctx, P, count, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pencil

@@ -1,0 +1,404 @@
+// Batched negacyclic NTT / INTT for one (polynomial, limb) per CTA.
+//
+// Sec. 5 ("NTT"): ring products in Z_q[X]/(X^N+1) become slot-wise after the
+// transform.  Forward = Cooley-Tukey with twiddles psi^brv(m+i) (natural order
+// in, bit-reversed evaluation order out); inverse = Gentleman-Sande with
+// psi^-brv(m+i), then N^{-1}.  Harvey's lazy butterflies keep forward values
+// in [0, 4q) and inverse values in [0, 2q); q < 2^62 keeps 4q < 2^64.
+//
+// GB300 mapping: T = N / E threads each hold E = 2^LOGE coefficients in
+// registers and run LOGE radix-2 stages between two shared-memory exchanges
+// (a radix-2^LOGE round).  The first forward round reads its coefficients
+// straight from the fused prologue (coalesced: thread t holds t + l*T); the
+// result goes through shared memory once more so the fused epilogue sees pairs
+// of consecutive slots (16-byte coalesced stores, one Philox block per pair).
+#pragma once
+#include <utility>
+
+#include "common.cuh"
+
+namespace pencil {
+
+// Shared-memory slot of coefficient x: XOR swizzle at 16-element granularity so
+// that strided round accesses spread over the 32 banks.
+template <int LOGN>
+__device__ __forceinline__ int sidx(int x) {
+  return x ^ ((x >> 4) & 15);
+}
+
+template <int LOGN, int LOGE, int S0>
+struct Round {
+  static constexpr int K = (LOGN - S0) < LOGE ? (LOGN - S0) : LOGE;
+  static constexpr int G = 1 << (LOGE - K);
+  static constexpr int LOGD = LOGN - S0 - K;
+  static constexpr int T = (1 << LOGN) >> LOGE;
+  static constexpr int E = 1 << LOGE;
+
+  static __device__ __forceinline__ int pos(int tau, int gg, int l) {
+    int g = gg * T + tau;
+    int B = g >> LOGD;
+    int p = g & ((1 << LOGD) - 1);
+    return (B << (LOGD + K)) + p + (l << LOGD);
+  }
+  static __device__ __forceinline__ void load(u64 (&v)[E], const u64* sm, int tau) {
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg)
+#pragma unroll
+      for (int l = 0; l < (1 << K); ++l) v[gg * (1 << K) + l] = sm[sidx<LOGN>(pos(tau, gg, l))];
+  }
+  static __device__ __forceinline__ void store(const u64 (&v)[E], u64* sm, int tau) {
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg)
+#pragma unroll
+      for (int l = 0; l < (1 << K); ++l) sm[sidx<LOGN>(pos(tau, gg, l))] = v[gg * (1 << K) + l];
+  }
+  // One radix-2 stage J of this round on every group the thread holds.
+  template <int J, bool FWD>
+  static __device__ __forceinline__ void stage(u64 (&v)[E], const ulonglong2* __restrict__ tw, int tau, u64 q,
+                                               u64 q2) {
+    constexpr int half = 1 << (K - 1 - J);
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      const int B = (gg * T + tau) >> LOGD;
+#pragma unroll
+      for (int i = 0; i < (1 << J); ++i) {
+        const ulonglong2 w = __ldg(tw + (1 << (S0 + J)) + (B << J) + i);
+#pragma unroll
+        for (int r = 0; r < half; ++r) {
+          const int l = gg * (1 << K) + i * 2 * half + r;
+          if constexpr (FWD)
+            ct_butterfly(v[l], v[l + half], w.x, w.y, q, q2);
+          else
+            gs_butterfly(v[l], v[l + half], w.x, w.y, q, q2);
+        }
+      }
+    }
+  }
+  template <int... J>
+  static __device__ __forceinline__ void fwd_seq(std::integer_sequence<int, J...>, u64 (&v)[E],
+                                                 const ulonglong2* tw, int tau, u64 q, u64 q2) {
+    (stage<J, true>(v, tw, tau, q, q2), ...);
+  }
+  template <int... J>
+  static __device__ __forceinline__ void inv_seq(std::integer_sequence<int, J...>, u64 (&v)[E],
+                                                 const ulonglong2* tw, int tau, u64 q, u64 q2) {
+    (stage<K - 1 - J, false>(v, tw, tau, q, q2), ...);
+  }
+  static __device__ __forceinline__ void fwd(u64 (&v)[E], const ulonglong2* __restrict__ tw, int tau, u64 q, u64 q2) {
+    fwd_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, q, q2);
+  }
+  static __device__ __forceinline__ void inv(u64 (&v)[E], const ulonglong2* __restrict__ tw, int tau, u64 q, u64 q2) {
+    inv_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, q, q2);
+  }
+};
+
+// Forward rounds S0, S0 + LOGE, ...; on return the last round's values are in smem.
+template <int LOGN, int LOGE, int S0>
+struct FwdRounds {
+  static __device__ __forceinline__ void run(u64 (&v)[1 << LOGE], u64* sm, const ulonglong2* tw, int tau, u64 q,
+                                             u64 q2) {
+    using R = Round<LOGN, LOGE, S0>;
+    R::fwd(v, tw, tau, q, q2);
+    if constexpr (S0 > 0) __syncthreads();  // previous round's readers are done
+    R::store(v, sm, tau);
+    __syncthreads();
+    if constexpr (S0 + LOGE < LOGN) {
+      Round<LOGN, LOGE, S0 + LOGE>::load(v, sm, tau);
+      FwdRounds<LOGN, LOGE, S0 + LOGE>::run(v, sm, tw, tau, q, q2);
+    }
+  }
+};
+
+// Inverse rounds from S0 down to 0; on entry the values are in smem (synced);
+// on return v holds the coefficients tau + l*T.
+template <int LOGN, int LOGE, int S0>
+struct InvRounds {
+  static __device__ __forceinline__ void run(u64 (&v)[1 << LOGE], u64* sm, const ulonglong2* tw, int tau, u64 q,
+                                             u64 q2) {
+    using R = Round<LOGN, LOGE, S0>;
+    R::load(v, sm, tau);
+    R::inv(v, tw, tau, q, q2);
+    if constexpr (S0 > 0) {
+      __syncthreads();
+      R::store(v, sm, tau);
+      __syncthreads();
+      InvRounds<LOGN, LOGE, S0 - LOGE>::run(v, sm, tw, tau, q, q2);
+    }
+  }
+};
+
+template <int LOGN>
+struct NttCfg {
+  static constexpr int LOGE = LOGN <= 12 ? 4 : 5;
+  static constexpr int N = 1 << LOGN;
+  static constexpr int E = 1 << LOGE;
+  static constexpr int T = N >> LOGE;
+  static constexpr int LAST_S0 = ((LOGN - 1) / LOGE) * LOGE;
+  static constexpr size_t SMEM = (size_t)N * sizeof(u64);
+  static constexpr int MIN_BLOCKS = LOGN >= 14 ? 1 : 2;   // 128 KB of smem: one CTA per SM
+};
+
+// Forward transform with a fused prologue (Mode::load, canonical coefficient
+// e) and epilogue (Mode::store2, canonical slots e and e + 1).
+template <int LOGN, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN>::T, NttCfg<LOGN>::MIN_BLOCKS) k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
+  using C = NttCfg<LOGN>;
+  extern __shared__ u64 sm[];
+  const int tau = threadIdx.x;
+  const int poly = blockIdx.x;
+  const int limb = blockIdx.y;
+  const LimbConst& lc = ctx.limb[limb];
+  const u64 q = lc.q, q2 = 2 * q;
+  const ulonglong2* tw = ctx.tw_fwd + (size_t)limb * C::N;
+  u64 v[C::E];
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
+  FwdRounds<LOGN, C::LOGE, 0>::run(v, sm, tw, tau, q, q2);
+#pragma unroll
+  for (int l = 0; l < C::E / 2; ++l) {
+    const int e = 2 * (tau + l * C::T);
+    const u64 x0 = canon4(sm[sidx<LOGN>(e)], q, q2);
+    const u64 x1 = canon4(sm[sidx<LOGN>(e + 1)], q, q2);
+    Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x0, x1);
+  }
+}
+
+// Inverse transform with a fused prologue (Mode::load, value in [0, 2q)) and
+// epilogue (Mode::store, canonical coefficient e).
+template <int LOGN, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN>::T, NttCfg<LOGN>::MIN_BLOCKS) k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
+  using C = NttCfg<LOGN>;
+  extern __shared__ u64 sm[];
+  const int tau = threadIdx.x;
+  const int poly = blockIdx.x;
+  const int limb = blockIdx.y;
+  const LimbConst& lc = ctx.limb[limb];
+  const u64 q = lc.q, q2 = 2 * q;
+  const ulonglong2* tw = ctx.tw_inv + (size_t)limb * C::N;
+  u64 v[C::E];
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) {
+    const int e = tau + l * C::T;
+    sm[sidx<LOGN>(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+  }
+  __syncthreads();
+  InvRounds<LOGN, C::LOGE, C::LAST_S0>::run(v, sm, tw, tau, q, q2);
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) {
+    const u64 x = mul_shoup(v[l], lc.ninv, lc.ninvs, q);
+    Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, x);
+  }
+}
+
+// ------------------------------------------------------------------ fused modes
+__device__ __forceinline__ size_t limb_off(int poly, int limb, int L, int n) {
+  return ((size_t)poly * L + limb) * n;
+}
+__device__ __forceinline__ size_t ct_off(int poly, int comp, int limb, int L, int n) {
+  return (((size_t)poly * 2 + comp) * L + limb) * n;
+}
+
+// In-place transform of [count][L][N] polynomials.
+struct ModeRaw {
+  struct Params {
+    u64* polys;
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst&, int poly, int limb,
+                                             int e) {
+    return P.polys[limb_off(poly, limb, c.L, N) + e];
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    *reinterpret_cast<ulonglong2*>(P.polys + limb_off(poly, limb, c.L, N) + e) = make_ulonglong2(x0, x1);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+                                               int limb, int e, u64 x) {
+    P.polys[limb_off(poly, limb, c.L, N) + e] = x;
+  }
+};
+
+// DO encryption: prologue Delta*m + e (m gathered by the packing), epilogue
+// c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain.
+struct ModeEncrypt {
+  struct Params {
+    Packing pk;
+    Accessor ac;
+    const int8_t* err;        // [count][N]
+    const ulonglong2* sk;     // [L][N] (s_hat, companion)
+    u64* ct;                  // [count][2][L][N]
+    u64 seed;
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    const u64 m = gather(P.pk, P.ac, poly, e) & c.t_mask;
+    const u64 r = mul_shoup(m, lc.delta, lc.deltas, lc.q);
+    const int ee = P.err[(size_t)poly * N + e];
+    return ee >= 0 ? add_mod(r, (u64)ee, lc.q) : sub_mod(r, (u64)(-ee), lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    const Philox4 w = philox4x64((u64)(e >> 1), (u64)poly, (u64)limb, 0ull, P.seed, PENCIL_DOM_A);
+    const u64 a0 = reduce128(w.v[0], w.v[1], lc);
+    const u64 a1 = reduce128(w.v[2], w.v[3], lc);
+    const ulonglong2 s0 = __ldg(P.sk + (size_t)limb * N + e);
+    const ulonglong2 s1 = __ldg(P.sk + (size_t)limb * N + e + 1);
+    const u64 c00 = sub_mod(x0, mul_shoup(a0, s0.x, s0.y, lc.q), lc.q);
+    const u64 c01 = sub_mod(x1, mul_shoup(a1, s1.x, s1.y, lc.q), lc.q);
+    *reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 0, limb, c.L, N) + e) = make_ulonglong2(c00, c01);
+    *reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 1, limb, c.L, N) + e) = make_ulonglong2(a0, a1);
+  }
+};
+
+// MO add_plain (Alg. 1 step 2): out_c0 = ct_in.c0 + NTT(Delta * pi_v(x0)).
+struct ModeAddPlain {
+  struct Params {
+    Packing pk;
+    Accessor ac;
+    const u64* ct_in;   // [count][2][L][N]
+    u64* out_c0;        // [count][L][N]
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    const u64 m = gather(P.pk, P.ac, poly, e) & c.t_mask;
+    return mul_shoup(m, lc.delta, lc.deltas, lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    const ulonglong2 c0 = __ldg(reinterpret_cast<const ulonglong2*>(P.ct_in + ct_off(poly, 0, limb, c.L, N) + e));
+    *reinterpret_cast<ulonglong2*>(P.out_c0 + limb_off(poly, limb, c.L, N) + e) =
+        make_ulonglong2(add_mod(c0.x, x0, lc.q), add_mod(c0.y, x1, lc.q));
+  }
+};
+
+// MO plaintext encoding: centred lift of Z_t values, NTT.
+struct ModeEncode {
+  struct Params {
+    Packing pk;
+    Accessor ac;
+    u64* pt;   // [count][L][N]
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    const u64 v = gather(P.pk, P.ac, poly, e) & c.t_mask;
+    const u64 half = (c.t_mask >> 1) + 1;
+    return v >= half ? lc.q - ((c.t_mask + 1) - v) : v;
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    *reinterpret_cast<ulonglong2*>(P.pt + limb_off(poly, limb, c.L, N) + e) = make_ulonglong2(x0, x1);
+  }
+};
+
+// MO re-mask (Alg. 1 step 3): ct_out.c0 -= NTT(Delta * s).
+struct ModeMask {
+  struct Params {
+    const u64* mpoly;   // [count][N] Z_t mask coefficients
+    u64* ct;            // [count][2][L][N]
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    return mul_shoup(P.mpoly[(size_t)poly * N + e], lc.delta, lc.deltas, lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
+    const ulonglong2 c0 = *p;
+    *p = make_ulonglong2(sub_mod(c0.x, x0, lc.q), sub_mod(c0.y, x1, lc.q));
+  }
+};
+
+__device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
+  return (u64)((((unsigned __int128)w) << 64) / q);
+}
+
+// DO key generation: ternary s, NTT, stored with Shoup companions.
+struct ModeKeygen {
+  struct Params {
+    u64 seed;
+    ulonglong2* sk;   // [L][N]
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int, int, int e) {
+    const Philox4 w = philox4x64((u64)(e >> 2), 0ull, 0ull, 0ull, P.seed, PENCIL_DOM_SECRET);
+    const u64 r = w.v[e & 3] % 3ull;
+    return r == 0 ? lc.q - 1 : r - 1;
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx&, const Params& P, const LimbConst& lc, int, int limb,
+                                                int e, u64 x0, u64 x1) {
+    P.sk[(size_t)limb * N + e] = make_ulonglong2(x0, shoup_companion(x0, lc.q));
+    P.sk[(size_t)limb * N + e + 1] = make_ulonglong2(x1, shoup_companion(x1, lc.q));
+  }
+};
+
+// DO decryption, first half: x = INTT(c0 + c1 * s_hat); stores y = x * qtilde mod q_j.
+struct ModeDecrypt {
+  struct Params {
+    const u64* ct;          // [count][2][L][N]
+    const ulonglong2* sk;   // [L][N]
+    u64* out;               // [count][L][N]
+  };
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                             int limb, int e) {
+    const u64 c0 = __ldg(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
+    const u64 c1 = __ldg(P.ct + ct_off(poly, 1, limb, c.L, N) + e);
+    const ulonglong2 s = __ldg(P.sk + (size_t)limb * N + e);
+    return add_mod(c0, mul_shoup(c1, s.x, s.y, lc.q), lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                               int limb, int e, u64 x) {
+    P.out[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.qtil, lc.qtils, lc.q);
+  }
+};
+
+// Host-side launcher; explicitly instantiated per LOGN in ntt12.cu / ntt13.cu / ntt14.cu.
+template <int LOGN, class Mode, bool INV>
+cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
+  using C = NttCfg<LOGN>;
+  if (count <= 0) return cudaSuccess;
+  cudaError_t err;
+  dim3 grid((unsigned)count, (unsigned)ctx.L);
+  if constexpr (INV) {
+    err = cudaFuncSetAttribute(k_ntt_inv<LOGN, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (err != cudaSuccess) return err;
+    k_ntt_inv<LOGN, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+  } else {
+    err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (err != cudaSuccess) return err;
+    k_ntt_fwd<LOGN, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+  }
+  return cudaGetLastError();
+}
+
+#define PENCIL_NTT_INSTANTIATE(SPEC, LOGN)                                                                 \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeRaw, false>(const DevCtx&, const ModeRaw::Params&, int,         \
+                                                             cudaStream_t);                                \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeRaw, true>(const DevCtx&, const ModeRaw::Params&, int,          \
+                                                            cudaStream_t);                                 \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeEncrypt, false>(const DevCtx&, const ModeEncrypt::Params&, int, \
+                                                                 cudaStream_t);                            \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeAddPlain, false>(const DevCtx&, const ModeAddPlain::Params&,    \
+                                                                  int, cudaStream_t);                      \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeEncode, false>(const DevCtx&, const ModeEncode::Params&, int,   \
+                                                                cudaStream_t);                             \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeMask, false>(const DevCtx&, const ModeMask::Params&, int,       \
+                                                              cudaStream_t);                               \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeKeygen, false>(const DevCtx&, const ModeKeygen::Params&, int,   \
+                                                                cudaStream_t);                             \
+  SPEC template cudaError_t launch_ntt<LOGN, ModeDecrypt, true>(const DevCtx&, const ModeDecrypt::Params&, int,  \
+                                                                cudaStream_t);
+
+}  // namespace pencil

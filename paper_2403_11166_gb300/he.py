@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libpencil_he.so (include/pencil_he.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory and streams.
+Shares, ciphertexts and plaintexts travel as torch.int64 tensors holding the
+uint64 bit patterns.  Importing this module raises if the library has not been
+built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpencil_he.so")
+
+PENCIL_OK = 0
+ERRORS = {-1: "PENCIL_E_ARG", -2: "PENCIL_E_SHAPE", -3: "PENCIL_E_PARAMS", -4: "PENCIL_E_CAPACITY",
+          -5: "PENCIL_E_NOISE", -6: "PENCIL_E_TIMEOUT", -7: "PENCIL_E_CUDA", -8: "PENCIL_E_UNIMPL"}
+FC, CONV = 0, 1
+ROLE_FWD, ROLE_DGRAD, ROLE_WGRAD = 0, 1, 2
+OPERAND_INPUT, OPERAND_KERNEL = 0, 1
+
+# Every entry point declared in include/pencil_he.h.
+EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "pencil_sync_status",
+           "pencil_keygen", "pencil_sk_destroy", "pencil_plan_linear", "pencil_plan_destroy",
+           "pencil_plan_sizes", "encode_weights", "encrypt_share", "he_linear_forward",
+           "he_linear_backward", "decrypt_to_share", "pencil_ntt_batch", "pencil_profile",
+           "pencil_profile_read")
+KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
+                "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine")
+
+
+class PencilError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where} failed: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_int32), ("num_primes", ctypes.c_int32),
+                ("prime_bits", ctypes.c_int32), ("t_bits", ctypes.c_int32)]
+
+
+class LayerDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("batch", ctypes.c_int32), ("c_in", ctypes.c_int32),
+                ("c_out", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Partition(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("bb", "cib", "cob", "th", "tw", "kth", "ktw")]
+
+    def astuple(self):
+        return tuple(getattr(self, k) for k, _ in self._fields_)
+
+
+class PlanSizes(ctypes.Structure):
+    _fields_ = [("part", Partition)] + [(k, ctypes.c_int64) for k in (
+        "ct_in", "pt", "ct_out", "products", "ct_words", "pt_words", "out_elems",
+        "ws_encrypt", "ws_forward", "ws_backward", "ws_decrypt")]
+
+
+class ProfEntry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("launches", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2403_11166_gb300.build` "
+                          "(the HE hot path has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    sig = {
+        "pencil_ctx_create": [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(P)],
+        "pencil_ctx_destroy": [P],
+        "pencil_ctx_primes": [P, P, P],
+        "pencil_sync_status": [P, ctypes.POINTER(I32)],
+        "pencil_keygen": [P, U64, ctypes.POINTER(P), P],
+        "pencil_sk_destroy": [P],
+        "pencil_plan_linear": [P, ctypes.POINTER(LayerDesc), I32, ctypes.POINTER(Partition), ctypes.POINTER(P)],
+        "pencil_plan_destroy": [P],
+        "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
+        "encode_weights": [P, P, I32, P, P, P],
+        "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
+        "he_linear_forward": [P, P, P, P, P, P, U64, P, P, P, SZ, P],
+        "he_linear_backward": [P, P, P, P, P, P, P, P, P, U64, U64, P, P, P, P, P, SZ, P],
+        "decrypt_to_share": [P, P, P, P, P, I32, P, SZ, P],
+        "pencil_ntt_batch": [P, P, I64, I32, P],
+        "pencil_profile": [P, I32],
+        "pencil_profile_read": [P, ctypes.POINTER(ProfEntry), I32, ctypes.POINTER(I32)],
+    }
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        fn.argtypes = sig[name]
+        fn.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(code: int, where: str):
+    if code != PENCIL_OK:
+        raise PencilError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda or not t.is_contiguous() or t.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("tensors must be contiguous CUDA int64/uint64")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """BFV context (pencil_ctx_create)."""
+
+    def __init__(self, log_n: int, num_primes: int, prime_bits: int, t_bits: int = 41, device: int = 0):
+        self.params = Params(log_n, num_primes, prime_bits, t_bits)
+        self.device = device
+        self.n = 1 << log_n
+        self.L = num_primes
+        self.t_bits = t_bits
+        h = ctypes.c_void_p()
+        _check(lib.pencil_ctx_create(ctypes.byref(self.params), device, ctypes.byref(h)), "pencil_ctx_create")
+        self.h = h
+
+    def primes(self):
+        q = (ctypes.c_uint64 * self.L)()
+        r = (ctypes.c_uint64 * self.L)()
+        _check(lib.pencil_ctx_primes(self.h, q, r), "pencil_ctx_primes")
+        return list(q), list(r)
+
+    def sync_status(self) -> int:
+        s = ctypes.c_int32()
+        _check(lib.pencil_sync_status(self.h, ctypes.byref(s)), "pencil_sync_status")
+        return s.value
+
+    def profile(self, enable: bool):
+        _check(lib.pencil_profile(self.h, int(enable)), "pencil_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} for the launches recorded since profile(True)."""
+        buf = (ProfEntry * 32)()
+        n = ctypes.c_int32()
+        _check(lib.pencil_profile_read(self.h, buf, 32, ctypes.byref(n)), "pencil_profile_read")
+        return {KERNEL_NAMES[buf[i].kernel]: (buf[i].launches, buf[i].ms) for i in range(n.value)}
+
+    def keygen(self, seed: int, stream=None) -> "SecretKey":
+        return SecretKey(self, seed, stream)
+
+    def close(self):
+        if self.h:
+            lib.pencil_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SecretKey:
+    def __init__(self, ctx: Context, seed: int, stream=None):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib.pencil_keygen(ctx.h, seed, ctypes.byref(h), _stream(stream)), "pencil_keygen")
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.pencil_sk_destroy(self.h)
+        except Exception:
+            pass
+
+
+@dataclass
+class Layer:
+    kind: int
+    batch: int
+    c_in: int
+    c_out: int
+    height: int = 1
+    width: int = 1
+    kernel: int = 1
+    pad: int = 0
+
+    def desc(self) -> LayerDesc:
+        return LayerDesc(self.kind, self.batch, self.c_in, self.c_out, self.height, self.width,
+                         self.kernel, self.pad)
+
+
+class Plan:
+    """pencil_plan_linear for one role; `part` = None lets the planner choose."""
+
+    def __init__(self, ctx: Context, layer: Layer, role: int, part=None):
+        self.ctx = ctx
+        self.layer = layer
+        self.role = role
+        d = layer.desc()
+        pp = ctypes.byref(Partition(*part)) if part is not None else None
+        h = ctypes.c_void_p()
+        _check(lib.pencil_plan_linear(ctx.h, ctypes.byref(d), role, pp, ctypes.byref(h)), "pencil_plan_linear")
+        self.h = h
+        s = PlanSizes()
+        _check(lib.pencil_plan_sizes(h, ctypes.byref(s)), "pencil_plan_sizes")
+        self.sizes = s
+        self.part = s.part.astuple()
+
+    def new_ct(self, count: int) -> torch.Tensor:
+        return torch.empty((count, 2, self.ctx.L, self.ctx.n), dtype=torch.int64, device=f"cuda:{self.ctx.device}")
+
+    def new_pt(self, count: int) -> torch.Tensor:
+        return torch.empty((count, self.ctx.L, self.ctx.n), dtype=torch.int64, device=f"cuda:{self.ctx.device}")
+
+    def new_ws(self, nbytes: int) -> torch.Tensor:
+        words = max(2, (int(nbytes) + 7) // 8)
+        return torch.empty(words, dtype=torch.int64, device=f"cuda:{self.ctx.device}")
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.pencil_plan_destroy(self.h)
+        except Exception:
+            pass
+
+
+def _ws(ws):
+    return _ptr(ws), ctypes.c_size_t(ws.numel() * 8)
+
+
+def encode_weights(ctx: Context, plan: Plan, operand: int, values: torch.Tensor, pt: torch.Tensor, stream=None):
+    _check(lib.encode_weights(ctx.h, plan.h, operand, _ptr(values), _ptr(pt), _stream(stream)), "encode_weights")
+
+
+def encrypt_share(ctx: Context, sk: SecretKey, plan: Plan, operand: int, share: torch.Tensor, seed: int,
+                  ct: torch.Tensor, ws: torch.Tensor, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.encrypt_share(ctx.h, sk.h, plan.h, operand, _ptr(share), seed, _ptr(ct), w, nb, _stream(stream)),
+           "encrypt_share")
+
+
+def he_linear_forward(ctx: Context, plan: Plan, ct_in, pt, x0, bias, mask_seed: int, ct_out, y0, ws, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.he_linear_forward(ctx.h, plan.h, _ptr(ct_in), _ptr(pt), _ptr(x0), _ptr(bias), mask_seed,
+                                 _ptr(ct_out), _ptr(y0), w, nb, _stream(stream)), "he_linear_forward")
+
+
+def he_linear_backward(ctx: Context, plan_dgrad, plan_wgrad, ct_gy1_d, pt_wt, ct_x1_w, ct_gy1_w, gy0, x0,
+                       mask_seed_x: int, mask_seed_w: int, ct_gx, gx0, ct_gw, gw_mask, ws, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.he_linear_backward(
+        ctx.h, plan_dgrad.h if plan_dgrad is not None else None, plan_wgrad.h if plan_wgrad is not None else None,
+        _ptr(ct_gy1_d), _ptr(pt_wt), _ptr(ct_x1_w), _ptr(ct_gy1_w), _ptr(gy0), _ptr(x0), mask_seed_x, mask_seed_w,
+        _ptr(ct_gx), _ptr(gx0), _ptr(ct_gw), _ptr(gw_mask), w, nb, _stream(stream)), "he_linear_backward")
+
+
+def decrypt_to_share(ctx: Context, sk: SecretKey, plan: Plan, ct_out, y1, check_noise: bool, ws, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.decrypt_to_share(ctx.h, sk.h, plan.h, _ptr(ct_out), _ptr(y1), int(check_noise), w, nb,
+                                _stream(stream)), "decrypt_to_share")
+
+
+def pencil_ntt_batch(ctx: Context, polys: torch.Tensor, inverse: bool, stream=None):
+    count = polys.numel() // (ctx.L * ctx.n)
+    _check(lib.pencil_ntt_batch(ctx.h, _ptr(polys), count, int(inverse), _stream(stream)), "pencil_ntt_batch")

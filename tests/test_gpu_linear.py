@@ -1,0 +1,248 @@
+"""GPU parity of the HE linear layer (through the C ABI) against the oracle:
+raw ciphertexts / plaintexts bit-exact on the same seeds and partition, shares
+bit-exact, and reconstruction = the direct ring operator.  Covers the FC and
+conv workloads at full size (FC 784->100 B=32 N=4096; conv 3x3 16->16 32x32
+B=64 N=8192) plus small ragged cases of the grad_X and grad_W roles."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bfv, protocol
+from oracle.packing import Partition
+from oracle.params import BfvParams
+from oracle.protocol import DGRAD, FWD, WGRAD, Layer
+from paper_2403_11166_gb300 import inputs
+from tests.gpu_util import as_u64, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+T_BITS = 41
+TMASK = np.uint64((1 << T_BITS) - 1)
+
+
+@pytest.fixture(scope="module")
+def he():
+    from paper_2403_11166_gb300 import he
+    return he
+
+
+def _he_layer(he, L):
+    kind = he.FC if L.kind == "fc" else he.CONV
+    return he.Layer(kind, L.B, L.Ci, L.Co, L.h, L.w, L.s, L.pad)
+
+
+def _add(a, b):
+    with np.errstate(over="ignore"):
+        return (np.asarray(a, dtype=np.uint64) + np.asarray(b, dtype=np.uint64)) & TMASK
+
+
+def gpu_forward(he, ctx, sk, L, role, part, kernel, x1, x0, bias, enc_seed, mask_seed):
+    plan = he.Plan(ctx, _he_layer(he, L), role, part)
+    S = plan.sizes
+    pt = plan.new_pt(S.pt)
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, to_dev(kernel), pt)
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+    ct_in = plan.new_ct(S.ct_in)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), enc_seed, ct_in, ws)
+    ct_out = plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    y1 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    if role == he.ROLE_FWD:
+        he.he_linear_forward(ctx, plan, ct_in, pt, to_dev(x0), None if bias is None else to_dev(bias), mask_seed,
+                             ct_out, y0, ws)
+    else:
+        he.he_linear_backward(ctx, plan, None, ct_in, pt, None, None, to_dev(x0), None, mask_seed, 0,
+                              ct_out, y0, None, None, ws)
+    he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    return plan, to_np(pt), to_np(ct_in), to_np(ct_out), to_np(y0), to_np(y1)
+
+
+def check_forward(he, cfg, L, role, part, seed, sample_in, sample_pt, sample_out, with_bias):
+    ctx = he.Context(*cfg)
+    p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
+    sk = ctx.keygen(seed + 1)
+    osk = bfv.keygen(p, seed + 1)
+    g = inputs.rng(seed)
+    W = inputs.gaussian_fixed(g, L.w_shape())
+    if role == FWD:
+        x = inputs.gaussian_fixed(g, L.x_shape())
+        bias = inputs.gaussian_fixed(g, (L.Co,), frac_bits=24) if with_bias else None
+    else:
+        x = inputs.gaussian_fixed(g, L.y_shape())
+        bias = None
+    x0, x1 = inputs.split_shares(g, x)
+    enc_seed, mask_seed = 1000 + seed, 2000 + seed
+    he_role = he.ROLE_FWD if role == FWD else he.ROLE_DGRAD
+    plan, pt, ct_in, ct_out, y0, y1 = gpu_forward(he, ctx, sk, L, he_role, part, W, x1, x0, bias,
+                                                  enc_seed, mask_seed)
+    opart = Partition(*plan.part)
+    if part is not None:
+        assert plan.part == tuple(part)
+    from oracle.packing import counts
+    c = counts(protocol.geometry(L, role), opart)
+    K, NC = c.K, c.NC
+    assert (plan.sizes.ct_in, plan.sizes.pt, plan.sizes.ct_out) == (c.ct_in, c.pt, c.ct_out)
+    # raw ciphertexts and plaintexts
+    ins = sorted(set([0, c.ct_in - 1] + list(sample_in)))
+    want_in = protocol.encrypt_inputs(p, osk, L, role, opart, x1, enc_seed, indices=ins)
+    for i in ins:
+        assert (ct_in[i] == as_u64(want_in[i])).all(), ("ct_in", i)
+    pts_idx = sorted(set([0, c.pt - 1] + list(sample_pt)))
+    want_pt = protocol.encode_kernel(p, L, role, opart, W, indices=pts_idx)
+    for i in pts_idx:
+        assert (pt[i] == as_u64(want_pt[i])).all(), ("pt", i)
+    for o in sorted(set([c.ct_out - 1] + list(sample_out))):
+        m, nn = divmod(o, NC)
+        need_in = [m * K + k for k in range(K)]
+        need_pt = [k * NC + nn for k in range(K)]
+        cts = protocol.encrypt_inputs(p, osk, L, role, opart, x1, enc_seed, indices=need_in)
+        pts = protocol.encode_kernel(p, L, role, opart, W, indices=need_pt)
+        want = protocol.mo_forward_ct(p, L, role, opart, cts, pts, x0, mask_seed, o)
+        assert (ct_out[o] == as_u64(want)).all(), ("ct_out", o)
+        # decryption of that ciphertext by the oracle lands in y1
+        dec = protocol.decrypt_outputs(p, osk, L, role, opart, {o: want})
+        from oracle.packing import decode_positions
+        for e, (b, oc, i, j) in decode_positions(protocol.geometry(L, role), opart, m, nn):
+            flat = protocol.output_flat(L, role, b, oc, i, j)
+            assert y1[flat] == dec[flat]
+    # shares: MO share exactly the oracle's, reconstruction = direct operator (+ bias)
+    want_y0 = protocol.mo_share(p, L, role, mask_seed, bias).reshape(-1)
+    assert (y0 == want_y0).all()
+    if role == FWD:
+        ref = protocol.ring_op(L, FWD, W, x, T_BITS)
+        if bias is not None:
+            ref = _add(ref, np.asarray(bias).astype(np.int64).view(np.uint64).reshape((1, -1) + (1,) * (ref.ndim - 2)))
+    else:
+        ref = protocol.ring_op(L, DGRAD, W, x, T_BITS)
+    assert (_add(y0, y1) == ref.reshape(-1)).all()
+    return plan
+
+
+def test_fc_784_100_b32_n4096(he):
+    L = Layer("fc", B=32, Ci=784, Co=100)
+    check_forward(he, (12, 2, 54), L, FWD, (1, 128, 32, 1, 1, 1, 1), 1,
+                  sample_in=[6, 13, 100], sample_pt=[3, 27], sample_out=[0, 5], with_bias=True)
+
+
+def test_fc_784_100_planner(he):
+    """Planner-chosen partition: shares and reconstruction still exact."""
+    L = Layer("fc", B=32, Ci=784, Co=100)
+    check_forward(he, (12, 2, 54), L, FWD, None, 2, sample_in=[], sample_pt=[], sample_out=[0], with_bias=True)
+
+
+def test_conv_16_16_32x32_b64_n8192(he):
+    L = Layer("conv", B=64, Ci=16, Co=16, h=32, w=32, s=3, pad=1)
+    check_forward(he, (13, 3, 60), L, FWD, (1, 2, 3, 32, 32, 3, 3), 3,
+                  sample_in=[9], sample_pt=[5], sample_out=[7], with_bias=False)
+
+
+@pytest.mark.parametrize("L,part,cfg", [
+    (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (1, 2, 2, 4, 3, 3, 3), (12, 2, 54)),
+    (Layer("conv", B=3, Ci=2, Co=3, h=5, w=5, s=3, pad=0), (2, 1, 2, 2, 3, 3, 3), (13, 3, 60)),
+    (Layer("fc", B=5, Ci=20, Co=7), (2, 3, 8, 1, 1, 1, 1), (12, 2, 54)),
+])
+def test_dgrad_small(he, L, part, cfg):
+    # grad_X role: the shares are grad_Y's, the kernel operand is the layer's weights
+    assert Partition(*part).fits(1 << cfg[0])
+    check_forward(he, cfg, L, DGRAD, part, 11, sample_in=[1], sample_pt=[1], sample_out=[0, 1], with_bias=False)
+
+
+@pytest.mark.parametrize("L,part", [
+    (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (2, 1, 3, 3, 3, 3, 2)),
+    (Layer("fc", B=5, Ci=20, Co=7), (3, 2, 4, 1, 1, 1, 1)),
+])
+def test_wgrad_small(he, L, part):
+    cfg = (12, 3, 60)
+    ctx = he.Context(*cfg)
+    p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
+    sk = ctx.keygen(5)
+    osk = bfv.keygen(p, 5)
+    g = inputs.rng(21)
+    x = inputs.gaussian_fixed(g, L.x_shape())
+    gy = inputs.gaussian_fixed(g, L.y_shape())
+    x0, x1 = inputs.split_shares(g, x)
+    gy0, gy1 = inputs.split_shares(g, gy)
+    plan = he.Plan(ctx, _he_layer(he, L), he.ROLE_WGRAD, part)
+    S = plan.sizes
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_backward, S.ws_decrypt))
+    ct_x1 = plan.new_ct(S.ct_in)
+    ct_gy1 = plan.new_ct(S.pt)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), 31, ct_x1, ws)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_KERNEL, to_dev(gy1), 32, ct_gy1, ws)
+    ct_gw = plan.new_ct(S.ct_out)
+    gw_mask = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    tilde = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    he.he_linear_backward(ctx, None, plan, None, None, ct_x1, ct_gy1, to_dev(gy0), to_dev(x0), 0, 33,
+                          None, None, ct_gw, gw_mask, ws)
+    he.decrypt_to_share(ctx, sk, plan, ct_gw, tilde, True, ws)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    opart = Partition(*part)
+    gw, want_tilde, want_s = protocol.he_wgrad(p, osk, L, opart, gy0, gy1, x0, x1, 31, 32, 33)
+    # raw operands
+    want_x1 = protocol.encrypt_inputs(p, osk, L, WGRAD, opart, x1, 31)
+    for i, ct in want_x1.items():
+        assert (to_np(ct_x1)[i] == as_u64(ct)).all()
+    want_gy1 = protocol.encrypt_kernel_operand(p, osk, L, WGRAD, opart, gy1, 32)
+    for i, ct in want_gy1.items():
+        assert (to_np(ct_gy1)[i] == as_u64(ct)).all()
+    assert (to_np(gw_mask) == want_s.reshape(-1)).all()
+    assert (to_np(tilde) == want_tilde.reshape(-1)).all()
+    # Alg. 2 reconstruction with the two local terms gives grad_W exactly
+    local = _add(protocol.ring_op(L, WGRAD, gy1, x1, T_BITS), protocol.ring_op(L, WGRAD, gy0, x0, T_BITS))
+    assert (_add(_add(to_np(tilde), to_np(gw_mask)), local.reshape(-1)) == gw.reshape(-1)).all()
+    assert (gw == protocol.ring_op(L, WGRAD, gy, x, T_BITS)).all()
+
+
+def test_noise_check_flags_corrupted_ciphertext(he):
+    cfg = (12, 2, 54)
+    ctx = he.Context(*cfg)
+    sk = ctx.keygen(3)
+    L = Layer("fc", B=4, Ci=16, Co=8)
+    plan = he.Plan(ctx, _he_layer(he, L), he.ROLE_FWD, (1, 16, 8, 1, 1, 1, 1))
+    S = plan.sizes
+    g = inputs.rng(4)
+    W = inputs.gaussian_fixed(g, L.w_shape())
+    x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L.x_shape()))
+    pt = plan.new_pt(S.pt)
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, to_dev(W), pt)
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+    ct_in = plan.new_ct(S.ct_in)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), 1, ct_in, ws)
+    ct_out = plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    y1 = torch.empty_like(y0)
+    he.he_linear_forward(ctx, plan, ct_in, pt, to_dev(x0), None, 2, ct_out, y0, ws)
+    he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws)
+    assert ctx.sync_status() == 0
+    q0 = ctx.primes()[0][0]
+    bad = to_np(ct_out).copy()
+    bad[1, 0, 0, 5] = (bad[1, 0, 0, 5] + np.uint64(q0 // 3)) % np.uint64(q0)
+    he.decrypt_to_share(ctx, sk, plan, to_dev(bad), y1, True, ws)
+    assert ctx.sync_status() == -5
+    assert ctx.sync_status() == 0
+
+
+def test_host_validation(he):
+    ctx = he.Context(12, 2, 54)
+    L = he.Layer(he.FC, 4, 16, 8)
+    with pytest.raises(he.PencilError) as e:
+        he.Plan(ctx, L, he.ROLE_FWD, (1, 16, 8, 2, 1, 1, 1))   # th > Ho
+    assert e.value.code == -4
+    with pytest.raises(he.PencilError) as e:
+        he.Plan(ctx, he.Layer(he.FC, 4, 64, 64), he.ROLE_FWD, (2, 64, 64, 1, 1, 1, 1))   # > N
+    assert e.value.code == -4
+    plan = he.Plan(ctx, L, he.ROLE_FWD, (1, 16, 8, 1, 1, 1, 1))
+    sk = ctx.keygen(1)
+    small = plan.new_ws(8)
+    with pytest.raises(he.PencilError) as e:
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, torch.zeros(64, dtype=torch.int64, device="cuda"), 1,
+                         plan.new_ct(plan.sizes.ct_in), small)
+    assert e.value.code == -4
+    wplan = he.Plan(ctx, L, he.ROLE_WGRAD, None)
+    with pytest.raises(he.PencilError) as e:
+        he.he_linear_forward(ctx, wplan, plan.new_ct(1), plan.new_pt(1), torch.zeros(64, dtype=torch.int64,
+                             device="cuda"), None, 1, plan.new_ct(1), torch.zeros(64, dtype=torch.int64,
+                             device="cuda"), plan.new_ws(1 << 20))
+    assert e.value.code == -1

@@ -1,0 +1,88 @@
+"""GPU parity: parameters, batched NTT / INTT (pencil_ntt_batch) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.ntt import intt_radix2, ntt_radix2
+from oracle.params import BfvParams
+from tests.gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+CFGS = [(12, 2, 54), (13, 3, 60), (14, 4, 60), (13, 1, 50), (12, 4, 60)]
+
+
+@pytest.fixture(scope="module")
+def he():
+    from paper_2403_11166_gb300 import he
+    return he
+
+
+@pytest.mark.parametrize("cfg", CFGS)
+def test_primes_and_roots(he, cfg):
+    ctx = he.Context(*cfg)
+    p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
+    q, psi = ctx.primes()
+    assert q == p.primes and psi == p.psis
+
+
+def _random_polys(p, count, seed):
+    g = np.random.default_rng(seed)
+    a = np.zeros((count, p.num_primes, p.n), dtype=np.uint64)
+    for j, q in enumerate(p.primes):
+        a[:, j] = g.integers(0, q, size=(count, p.n), dtype=np.uint64)
+    # adversarial rows: all zero, all q-1, a single spike
+    if count >= 3:
+        a[0] = 0
+        for j, q in enumerate(p.primes):
+            a[1, j] = q - 1
+        a[2] = 0
+        a[2, :, 7] = 1
+    return a
+
+
+@pytest.mark.parametrize("cfg", CFGS)
+def test_ntt_matches_oracle(he, cfg):
+    ctx = he.Context(*cfg)
+    p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
+    a = _random_polys(p, 5, cfg[0])
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=False)
+    got = to_np(d)
+    for i in range(a.shape[0]):
+        for j, (q, psi) in enumerate(zip(p.primes, p.psis)):
+            want = ntt_radix2([int(x) for x in a[i, j]], q, psi)
+            assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all(), (i, j)
+    he.pencil_ntt_batch(ctx, d, inverse=True)
+    assert (to_np(d) == a).all()
+
+
+@pytest.mark.parametrize("cfg", CFGS[:3])
+def test_intt_matches_oracle(he, cfg):
+    ctx = he.Context(*cfg)
+    p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
+    a = _random_polys(p, 2, 100 + cfg[0])
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=True)
+    got = to_np(d)
+    for i in range(a.shape[0]):
+        for j, (q, psi) in enumerate(zip(p.primes, p.psis)):
+            want = intt_radix2([int(x) for x in a[i, j]], q, psi)
+            assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all()
+
+
+def test_large_batch_roundtrip(he):
+    """Full-size sweep shape (N = 8192, 3 limbs) on a batch that spans many waves:
+    INTT(NTT(a)) = a everywhere, NTT spot-checked against the oracle."""
+    ctx = he.Context(13, 3, 60)
+    p = BfvParams(log_n=13, num_primes=3, prime_bits=60)
+    a = _random_polys(p, 1000, 7)
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=False)
+    got = to_np(d)
+    for i in (0, 517, 999):
+        j = i % 3
+        want = ntt_radix2([int(x) for x in a[i, j]], p.primes[j], p.psis[j])
+        assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all()
+    he.pencil_ntt_batch(ctx, d, inverse=True)
+    assert torch.equal(d, to_dev(a))
