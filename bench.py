@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the HE linear-layer hot path (one JSON line on stdout).
+
+Workload: the forward homomorphic product of a conv 3x3, 16 -> 16 channels,
+32 x 32 input, pad 1, batch 64 (BFV N = 8192, three 60-bit primes, t = 2^41),
+seeded synthetic Gaussian fixed-point data (12 fractional bits).  One step =
+the whole forward path of Algorithm 1: encode_weights (pi_W + NTT),
+encrypt_share (DO: pi_v + BFV encryption), he_linear_forward (MO: add <X>_0,
+ct x pt multiply-accumulate, re-mask) and decrypt_to_share (DO).  Metric:
+ct x pt products per second (whole job), plus the per-kernel roofline of the
+dominant kernel, an end-to-end number with host buffers, and the oracle timed
+on the host cores.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HE linear-layer ct x pt products/s (conv3x3 16->16, 32x32, B=64, N=8192, fwd)"
+UNIT = "products/s"
+LOG_N, L, PRIME_BITS, T_BITS = 13, 3, 60, 41
+LAYER = dict(batch=64, c_in=16, c_out=16, h=32, w=32, s=3, pad=1)
+WORKLOAD = "conv3x3_16to16_32x32_b64_fwd_N8192_L3x60_t41"
+SMS = 152                    # GB300 SM count (two dies x 76)
+IMAD_PER_CLK_SM = 64         # 32-bit integer multiply-add results per clock per SM
+MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        if self.uuid:
+            mine = [r for r in rows if r and self.uuid in r[0]]
+            rows = mine or rows
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) > 8 for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline accounting
+def limb_ntt_mults(n: int) -> float:
+    """Accounting: one limb-NTT = (N/2) log2 N Shoup modmuls x 10 32-bit multiplies."""
+    return 10.0 * (n // 2) * (n.bit_length() - 1)
+
+
+def kernel_work(name: str, S, n: int, L_: int):
+    """(32-bit multiply ops, algorithmic HBM bytes) of ONE launch of kernel `name`
+    in this workload's step."""
+    ln = L_ * n
+    if name == "ntt_encrypt":
+        return S.ct_in * L_ * limb_ntt_mults(n), S.ct_in * (16 * ln + n)            # write ct, read errors
+    if name == "ntt_addplain":
+        return S.ct_in * L_ * limb_ntt_mults(n), S.ct_in * 16 * ln                  # read c0, write c0'
+    if name == "ntt_encode":
+        return S.pt * L_ * limb_ntt_mults(n), S.pt * 8 * ln                         # write pt
+    if name == "ntt_mask":
+        return S.ct_out * L_ * limb_ntt_mults(n), S.ct_out * (8 * n + 16 * ln)      # read mask, rw c0
+    if name == "intt_decrypt":
+        return S.ct_out * L_ * limb_ntt_mults(n), S.ct_out * (16 * ln + 8 * ln)     # read ct, write residues
+    if name == "mac":
+        return S.products * 2 * ln * 4.0, (S.ct_in * 16 * ln + S.pt * 8 * ln + S.ct_out * 16 * ln)
+    return 0.0, 0.0
+
+
+def roofline(prof: dict, S, n: int, L_: int, steps: int, peaks: dict, clocks: dict):
+    """Dominant kernel (largest time share): achieved rate vs the multiply-pipe peak."""
+    shares = {k: v[1] for k, v in prof.items()}
+    total = sum(shares.values()) or 1.0
+    table = {}
+    for name, (launches, ms) in prof.items():
+        mults, byts = kernel_work(name, S, n, L_)
+        per = ms / max(1, launches) * 1e-3
+        table[name] = {"launches": launches, "ms_per_launch": per * 1e3, "share": ms / total,
+                       "tmul_per_s": mults / per / 1e12 if mults else None,
+                       "gb_per_s": byts / per / 1e9 if byts else None}
+    dom = max((k for k in table if kernel_work(k, S, n, L_)[0] > 0), key=lambda k: table[k]["share"])
+    mults, byts = kernel_work(dom, S, n, L_)
+    per = table[dom]["ms_per_launch"] * 1e-3
+    alu_peak = peaks["alu_tmul"]
+    achieved = mults / per / 1e12
+    return dom, table, {
+        "kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 3),
+        "unit": "T 32-bit mult/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
+        "peak_source": peaks["alu_source"],
+        "hbm": {"achieved_gbs": round(byts / per / 1e9, 1), "peak_gbs": peaks["hbm_gbs"],
+                "frac": round(byts / per / 1e9 / peaks["hbm_gbs"], 4), "peak_source": "MEASURED_PEAKS.json (measured)"},
+        "algorithmic_mults_per_launch": mults, "algorithmic_bytes_per_launch": byts,
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        hbm = float(d.get("hbm_gbs", hbm))
+        src = "measured"
+    alu = SMS * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e12
+    return {"hbm_gbs": hbm, "hbm_source": src, "alu_tmul": alu,
+            "alu_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz"}
+
+
+# ---------------------------------------------------------------- oracle timing (host cores)
+def oracle_sample(seed: int = 0, part_tuple=(1, 2, 3, 32, 32, 3, 3), min_seconds: float = 0.0):
+    """Times the oracle on one instance of every stage of the workload (repeated
+    until `min_seconds` have passed, median per stage) and scales by the stage
+    counts of the partition.  Returns (products/s, seconds of the full workload
+    step, description, seconds spent)."""
+    from oracle import bfv, protocol
+    from oracle.packing import Partition, counts
+    from oracle.params import BfvParams
+    from paper_2403_11166_gb300 import inputs
+
+    t_all = time.perf_counter()
+    p = BfvParams(log_n=LOG_N, num_primes=L, prime_bits=PRIME_BITS, t_bits=T_BITS)
+    layer = protocol.Layer("conv", B=LAYER["batch"], Ci=LAYER["c_in"], Co=LAYER["c_out"], h=LAYER["h"],
+                           w=LAYER["w"], s=LAYER["s"], pad=LAYER["pad"])
+    part = Partition(*part_tuple)
+    c = counts(protocol.geometry(layer, protocol.FWD), part)
+    g = inputs.rng(seed)
+    W = inputs.gaussian_fixed(g, layer.w_shape())
+    x = inputs.gaussian_fixed(g, layer.x_shape())
+    x0, x1 = inputs.split_shares(g, x)
+    sk = bfv.keygen(p, 5)
+    from oracle.packing import pack_input
+    V0 = protocol.role_input(layer, protocol.FWD, x0)
+    times = {k: [] for k in ("enc", "encode", "add", "mul", "mask", "dec")}
+    while True:
+        t0 = time.perf_counter()
+        cts = protocol.encrypt_inputs(p, sk, layer, protocol.FWD, part, x1, 9, indices=[0])
+        t1 = time.perf_counter()
+        pts = protocol.encode_kernel(p, layer, protocol.FWD, part, W, indices=[0])
+        t2 = time.perf_counter()
+        ct = bfv.add_plain(p, cts[0], pack_input(V0, protocol.geometry(layer, protocol.FWD), part, p.n, 0, 0))
+        t3 = time.perf_counter()
+        prod = bfv.mul_plain(p, ct, pts[0])
+        acc = bfv.add_ct(p, prod, prod)
+        t4 = time.perf_counter()
+        out = bfv.sub_plain(p, acc, protocol.mask_polynomial(p, layer, protocol.FWD, part, 3, 0))
+        t5 = time.perf_counter()
+        bfv.decrypt(p, sk, out)
+        t6 = time.perf_counter()
+        for k, v in zip(times, (t1 - t0, t2 - t1, t3 - t2, t4 - t3, t5 - t4, t6 - t5)):
+            times[k].append(v)
+        if time.perf_counter() - t_all >= min_seconds:
+            break
+    med = {k: statistics.median(v) for k, v in times.items()}
+    t_enc, t_encode, t_add, t_mul, t_mask, t_dec = (med[k] for k in times)
+    step = (c.ct_in * (t_enc + t_add) + c.pt * t_encode + c.products * t_mul + c.ct_out * (t_mask + t_dec))
+    desc = (f"oracle (Python, exact big integers) timed on {len(times['enc'])} rounds of: one ct_in encryption "
+            f"({t_enc:.2f}s), one add_plain, one pt encoding, one ct x pt product + accumulate, one re-mask and "
+            f"one decryption ({t_dec:.2f}s) at N=8192, L=3; median per stage "
+            f"scaled by the partition's counts ({c.ct_in} ct_in, {c.pt} pt, {c.products} products, "
+            f"{c.ct_out} ct_out)")
+    return c.products / step, step, desc, time.perf_counter() - t_all
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals, steps_s = [], []
+    desc, spent = "", 0.0
+    for i in range(args.warmup + args.steps):
+        v, st, desc, sp = oracle_sample(seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+            steps_s.append(st)
+            spent += sp
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(steps_s) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS mod q_i), u64 mod 2^41",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "inputs": "larger than L2 (201 MB of ct_in)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.nn.functional as F
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_2403_11166_gb300 import build
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2403_11166_gb300 import he, inputs
+
+    dev = f"cuda:{local}"
+    stream = torch.cuda.current_stream()
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=local)
+    sk = ctx.keygen(1234 + rank)
+    layer = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
+                     LAYER["pad"])
+    plan = he.Plan(ctx, layer, he.ROLE_FWD, None)
+    S = plan.sizes
+    g = inputs.rng(100 + rank)
+    W = inputs.gaussian_fixed(g, (LAYER["c_out"], LAYER["c_in"], 3, 3))
+    x = inputs.gaussian_fixed(g, (LAYER["batch"], LAYER["c_in"], LAYER["h"], LAYER["w"]))
+    bias = inputs.gaussian_fixed(g, (LAYER["c_out"],), frac_bits=24)
+    x0, x1 = inputs.split_shares(g, x)
+
+    def to_i64(a):
+        a = np.ascontiguousarray(a)
+        return torch.from_numpy((a if a.dtype == np.int64 else a.view(np.int64)).copy())
+
+    host = {"W": to_i64(W).pin_memory(), "x0": to_i64(x0).pin_memory(), "x1": to_i64(x1).pin_memory(),
+            "bias": to_i64(bias.astype(np.uint64) & np.uint64((1 << T_BITS) - 1)).pin_memory()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    pt = plan.new_pt(S.pt)
+    ct_in = plan.new_ct(S.ct_in)
+    ct_out = plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
+    y1 = torch.empty_like(y0)
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+    hy0 = torch.empty(S.out_elems, dtype=torch.int64).pin_memory()
+    hy1 = torch.empty_like(hy0).pin_memory()
+
+    def step(i):
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 1000 + i, ct_in, ws)
+        he.he_linear_forward(ctx, plan, ct_in, pt, d["x0"], d["bias"], 5000 + i, ct_out, y0, ws)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    # self-check: reconstruction equals the plaintext convolution (exact in float64)
+    rec = ((y0 + y1) & ((1 << T_BITS) - 1)).view(LAYER["batch"], LAYER["c_out"], LAYER["h"], LAYER["w"])
+    rec = torch.where(rec >= (1 << (T_BITS - 1)), rec - (1 << T_BITS), rec).double()
+    ref = F.conv2d(torch.from_numpy(x).double().to(dev), torch.from_numpy(W).double().to(dev),
+                   torch.from_numpy(bias).double().to(dev), padding=1)
+    parity_ok = bool(torch.equal(rec, ref))
+
+    # multiply-pipe probe: measured 32-bit IMAD and 64-bit Shoup rates (register-only)
+    probe = {}
+    for which, key in ((0, "imad32"), (1, "shoup64")):
+        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
+        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
+        probe[key] = steps_p / (ms_p * 1e-3) / 1e12
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    # ---- timed region (inputs resident in HBM)
+    ctx.profile(True)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    # ---- end to end: host buffers, H2D of the step's inputs and D2H of the shares inside the region
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = 2 * S.out_elems * 8
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(args.steps):
+        for k in host:
+            d[k].copy_(host[k], non_blocking=True)
+        step(10_000 + i)
+        hy0.copy_(y0, non_blocking=True)
+        hy1.copy_(y1, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    products = S.products * args.steps * world
+    value = products / (ms * 1e-3)
+    peaks = load_peaks()
+    dom, table, roof = roofline(prof, S, ctx.n, ctx.L, args.steps, peaks, ck)
+    roof["probe"] = {"imad32_T_per_s": round(probe["imad32"], 3), "shoup64_T_per_s": round(probe["shoup64"], 3),
+                     "note": "register-only chains, 8 per thread, 1216 x 256 threads, measured before the timed region"}
+    launches = sum(v[0] for v in prof.values())
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64 (RNS mod q_i), u64 mod 2^41", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "partition": dict(zip(("bb", "cib", "cob", "th", "tw", "kth", "ktw"),
+                                                            plan.part)),
+                   "ct_in": S.ct_in, "pt": S.pt, "ct_out": S.ct_out, "products_per_step": S.products,
+                   "l2": "inputs larger than L2 (ct_in %.0f MB per step)" % (S.ct_in * S.ct_words * 8 / 1e6),
+                   "parallelism": f"replicas x{world} (independent layers, no collective)"},
+        "parity_selfcheck": parity_ok,
+        "roofline": roof,
+        "kernels": table,
+        "clocks": ck,
+        "gpu_launches": launches,
+        "e2e": {"value": products / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, st, desc, spent = oracle_sample(part_tuple=plan.part, min_seconds=12.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": round(spent, 1), "host_cores_available": len(os.sched_getaffinity(0))}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -202,6 +202,24 @@ int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan
                      const uint64_t* ct_out, uint64_t* y1, int32_t check_noise,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* Plaintext ring operator of the plan's role over Z_t (uint64 wrap-around,
+ * exact because t divides 2^64): out = addend + addend2 + op(kernel_operand,
+ * input_operand) mod t, with op = W o X (FWD), grad_X = W (.)_x grad_Y (DGRAD),
+ * grad_W = grad_Y (.) X (WGRAD).  This is Alg. 2's local term
+ * <gY>_j (.) <X>_j (steps 4 and 6) when called on one party's shares, with the
+ * decrypted cross term (DO) or the decrypted value plus mask (MO) as addend.
+ * Operands in the user's layouts: kernel_operand = W (FWD, DGRAD; int64 bits) or
+ * grad_Y (WGRAD); input_operand = X (FWD, WGRAD) or grad_Y (DGRAD).  The
+ * addends (output layout) are nullable; out may alias either. */
+int pencil_ring_linear(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* kernel_operand,
+                       const uint64_t* input_operand, const uint64_t* addend, const uint64_t* addend2,
+                       uint64_t* out, void* stream);
+
+/* Bias gradient (Sec. 3.2.2, its footnote): out[o] = sum over the batch and
+ * the output positions of g mod t, g in the forward output layout of the plan's
+ * layer ([B][n_o] or [B][C_out][H_out][W_out]); each party sums its own share. */
+int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* g, uint64_t* out, void* stream);
+
 /* In-place batched negacyclic NTT (inverse = 0) or INTT (inverse = 1) of
  * `count` polynomials laid out [count][L][N], canonical in and out (Sec. 5 "NTT"). */
 int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream);
@@ -215,7 +233,8 @@ int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inv
 enum {
   PENCIL_K_NTT_RAW = 0, PENCIL_K_INTT_RAW, PENCIL_K_NTT_ENCRYPT, PENCIL_K_NTT_ADDPLAIN, PENCIL_K_NTT_ENCODE,
   PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
-  PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_COUNT
+  PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_RING,
+  PENCIL_K_BIAS_GRAD, PENCIL_K_COUNT
 };
 typedef struct {
   int32_t kernel;   /* PENCIL_K_* */
@@ -224,6 +243,15 @@ typedef struct {
 } PencilProfEntry;
 int pencil_profile(PencilCtx* ctx, int32_t enable);
 int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t max_entries, int32_t* n_entries);
+
+/* Multiply-pipe probe used to measure the integer roofline: `blocks` x
+ * `threads` threads each run 8 independent register-only chains of `iters`
+ * steps; which = 0: 32-bit multiply-add (mad.lo.u32), which = 1: 64-bit Shoup
+ * modular multiply.  Times the launch with CUDA events on `stream` and returns
+ * the elapsed milliseconds and the number of chain steps (threads * 8 * iters).
+ * Synchronises `stream`. */
+int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads, double* ms,
+                     double* steps, void* stream);
 
 #ifdef __cplusplus
 }

@@ -932,6 +932,43 @@ extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const
   return PENCIL_OK;
 }
 
+extern "C" int pencil_ring_linear(PencilCtx* ctx, const PencilPlan* P, const uint64_t* kernel_operand,
+                                  const uint64_t* input_operand, const uint64_t* addend,
+                                  const uint64_t* addend2, uint64_t* out, void* stream) {
+  if (!ctx || !P || !kernel_operand || !input_operand || !out || P->ctx != ctx) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  RingParams R;
+  R.kbound = make_int4(P->g.Co, P->g.Ci, P->g.KH, P->g.KW);
+  R.Ho = P->g.Ho();
+  R.Wo = P->g.Wo();
+  R.v = P->acc_v;
+  R.v.ptr = input_operand;
+  R.w = P->acc_w;
+  R.w.ptr = kernel_operand;
+  R.y = P->acc_y;
+  R.addend = addend;
+  R.addend2 = addend2;
+  R.out = out;
+  R.outs = (long long)P->g.B * P->g.Co * R.Ho * R.Wo;
+  R.t_mask = ctx->dev.t_mask;
+  PROF(ctx, PENCIL_K_RING, s);
+  CUDA_TRY(launch_ring(R, s));
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* P, const uint64_t* g, uint64_t* out,
+                                void* stream) {
+  if (!ctx || !P || !g || !out || P->ctx != ctx) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  const PencilLayerDesc& L = P->layer;
+  const long long ho = L.height + 2 * L.pad - L.kernel + 1, wo = L.width + 2 * L.pad - L.kernel + 1;
+  const long long hw = L.kind == PENCIL_FC ? 1 : ho * wo;
+  PROF(ctx, PENCIL_K_BIAS_GRAD, (cudaStream_t)stream);
+  CUDA_TRY(launch_bias_grad(g, L.batch, L.c_out, hw, ctx->dev.t_mask, out, (cudaStream_t)stream));
+  return PENCIL_OK;
+}
+
 extern "C" int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream) {
   if (!ctx || !polys || count < 0 || count > (1ll << 31) - 1) return PENCIL_E_ARG;
   if (!aligned16(polys)) return PENCIL_E_ARG;
@@ -982,5 +1019,32 @@ extern "C" int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t
     ++n;
   }
   *n_entries = n;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads,
+                                double* ms, double* steps, void* stream) {
+  if (!ctx || !ms || !steps || (which != 0 && which != 1) || iters < 1 || blocks < 1 || threads < 32 ||
+      threads > 1024)
+    return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  u64* sink = nullptr;
+  CUDA_TRY(cudaMalloc(&sink, sizeof(u64)));
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  CUDA_TRY(cudaEventRecord(a, s));
+  cudaError_t e = launch_mul_probe(which, iters, blocks, threads, 0x1234567887654321ull, sink, s);
+  CUDA_TRY(cudaEventRecord(b, s));
+  CUDA_TRY(cudaEventSynchronize(b));
+  float t = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  CUDA_TRY(e);
+  *ms = t;
+  *steps = (double)blocks * threads * 8.0 * (double)iters;
   return PENCIL_OK;
 }

@@ -227,4 +227,146 @@ cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const A
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ plaintext ring operators
+// Alg. 2's local terms <gY>_j (.) <X>_j and the direct operators over Z_t,
+// t = 2^t_bits: u64 wrap-around arithmetic is exact mod t because t | 2^64.
+//   out[flat(a, o, i, j)] = addend[flat] + sum_{c, u, v} Wt(o, c, u, v) V(a, c, i + u, j + v)  (mod t)
+// Reduction length R = Ci * KH * KW.  Short reductions: one thread per output;
+// long ones (grad_W: R = batch x H_out x W_out): one block per output.
+__device__ __forceinline__ u64 ring_term(const RingParams& P, int a, int o, int i, int j, long long r) {
+  const int KW = P.kbound.w, KH = P.kbound.z;
+  const int v = (int)(r % KW);
+  const int u = (int)((r / KW) % KH);
+  const int c = (int)(r / ((long long)KW * KH));
+  int rr = i + u - P.v.pr, ss = j + v - P.v.ps;
+  if ((unsigned)rr >= (unsigned)P.v.hr || (unsigned)ss >= (unsigned)P.v.wr) return 0;
+  const u64 x = __ldg(P.v.ptr + P.v.base + a * P.v.s0 + c * P.v.s1 + rr * P.v.s2 + ss * P.v.s3);
+  const u64 w = __ldg(P.w.ptr + P.w.base + o * P.w.s0 + c * P.w.s1 + u * P.w.s2 + v * P.w.s3);
+  return x * w;
+}
+
+__device__ __forceinline__ void ring_coords(const RingParams& P, long long id, int& a, int& o, int& i, int& j) {
+  j = (int)(id % P.Wo);
+  i = (int)((id / P.Wo) % P.Ho);
+  o = (int)((id / ((long long)P.Wo * P.Ho)) % P.kbound.x);
+  a = (int)(id / ((long long)P.Wo * P.Ho * P.kbound.x));
+}
+
+__device__ __forceinline__ void ring_store(const RingParams& P, int a, int o, int i, int j, u64 acc) {
+  const i64 flat = P.y.base + a * P.y.s0 + o * P.y.s1 + i * P.y.s2 + j * P.y.s3;
+  if (P.addend) acc += P.addend[flat];
+  if (P.addend2) acc += P.addend2[flat];
+  P.out[flat] = acc & P.t_mask;
+}
+
+__global__ void k_ring_thread(RingParams P, long long R) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= P.outs) return;
+  int a, o, i, j;
+  ring_coords(P, id, a, o, i, j);
+  u64 acc = 0;
+  for (long long r = 0; r < R; ++r) acc += ring_term(P, a, o, i, j, r);
+  ring_store(P, a, o, i, j, acc);
+}
+
+__global__ void __launch_bounds__(256) k_ring_block(RingParams P, long long R) {
+  const long long id = blockIdx.x;
+  int a, o, i, j;
+  ring_coords(P, id, a, o, i, j);
+  u64 acc = 0;
+  for (long long r = threadIdx.x; r < R; r += blockDim.x) acc += ring_term(P, a, o, i, j, r);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ u64 part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    ring_store(P, a, o, i, j, s);
+  }
+}
+
+cudaError_t launch_ring(const RingParams& P, cudaStream_t s) {
+  const long long R = (long long)P.kbound.y * P.kbound.z * P.kbound.w;
+  if (P.outs == 0) return cudaSuccess;
+  if (R >= 2048 && P.outs <= (1ll << 31) - 1) {
+    k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P, R);
+  } else {
+    k_ring_thread<<<(unsigned)((P.outs + 255) / 256), 256, 0, s>>>(P, R);
+  }
+  return cudaGetLastError();
+}
+
+// Bias gradient: out[o] = sum_{b, i, j} g[b, o, i, j] mod t   (g row-major [B][Co][HW]).
+__global__ void __launch_bounds__(256) k_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_mask, u64* out) {
+  const int o = blockIdx.x;
+  const long long R = (long long)B * hw;
+  u64 acc = 0;
+  for (long long r = threadIdx.x; r < R; r += blockDim.x) {
+    const long long b = r / hw, p = r % hw;
+    acc += __ldg(g + (b * Co + o) * hw + p);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ u64 part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 s = 0;
+    for (int w = 0; w < 8; ++w) s += part[w];
+    out[o] = s & t_mask;
+  }
+}
+
+cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_mask, u64* out, cudaStream_t s) {
+  if (Co == 0) return cudaSuccess;
+  k_bias_grad<<<Co, 256, 0, s>>>(g, B, Co, hw, t_mask, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ multiply-pipe probe
+// Register-only chains measuring the 32-bit integer multiply-add rate (which = 0)
+// or the 64-bit Shoup modular-multiply rate (which = 1).  Eight independent
+// chains per thread; the result is stored only if it equals a value it cannot
+// take, so nothing is optimised away and nothing is written.
+__global__ void k_mul_probe(int which, long long iters, u64 seed, u64* sink) {
+  const u32 t = threadIdx.x + blockIdx.x * blockDim.x;
+  if (which == 0) {
+    u32 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (u32)seed + t * 2654435761u + i;
+    const u32 a = (u32)(seed >> 32) | 1u, b = (u32)seed ^ 0x9e3779b9u;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[i]) : "r"(a), "r"(b));
+    }
+    u32 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == 0xFFFFFFFFu && seed == 0) sink[0] = acc;
+  } else {
+    const u64 q = 0xfffffffffffc001ull;
+    const u64 w = (seed | 1ull) % q;
+    const u64 ws = (u64)((((unsigned __int128)w) << 64) / q);
+    u64 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (seed + t * 0x9E3779B97F4A7C15ull + i) % q;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = mul_shoup_lazy(x[i], w, ws, q);
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == ~0ull && seed == 0) sink[0] = acc;
+  }
+}
+
+cudaError_t launch_mul_probe(int which, long long iters, int blocks, int threads, u64 seed, u64* sink,
+                             cudaStream_t s) {
+  k_mul_probe<<<blocks, threads, 0, s>>>(which, iters, seed, sink);
+  return cudaGetLastError();
+}
+
 }  // namespace pencil

@@ -36,6 +36,23 @@ cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bi
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
                                    int count, int check, u64* y1, cudaStream_t s);
 
+// Plaintext correlation over Z_t of one plan role (see k_ring_* in kernels.cu).
+struct RingParams {
+  int4 kbound;        // (Co, Ci, KH, KW) of the role's kernel
+  int Ho, Wo;         // output spatial size
+  Accessor v, w, y;   // input, kernel and output views of the user's tensors
+  const u64* addend;  // nullable, output layout
+  const u64* addend2; // nullable, output layout
+  u64* out;           // output layout
+  long long outs;     // B * Co * Ho * Wo
+  u64 t_mask;
+};
+cudaError_t launch_ring(const RingParams& P, cudaStream_t s);
+cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_mask, u64* out, cudaStream_t s);
+
+cudaError_t launch_mul_probe(int which, long long iters, int blocks, int threads, u64 seed, u64* sink,
+                             cudaStream_t s);
+
 PENCIL_NTT_INSTANTIATE(extern, 12)
 PENCIL_NTT_INSTANTIATE(extern, 13)
 PENCIL_NTT_INSTANTIATE(extern, 14)

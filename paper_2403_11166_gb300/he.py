@@ -29,9 +29,10 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_keygen", "pencil_sk_destroy", "pencil_plan_linear", "pencil_plan_destroy",
            "pencil_plan_sizes", "encode_weights", "encrypt_share", "he_linear_forward",
            "he_linear_backward", "decrypt_to_share", "pencil_ntt_batch", "pencil_profile",
-           "pencil_profile_read")
+           "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad")
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
-                "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine")
+                "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
+                "ring", "bias_grad")
 
 
 class PencilError(RuntimeError):
@@ -92,6 +93,10 @@ def _load():
         "pencil_ntt_batch": [P, P, I64, I32, P],
         "pencil_profile": [P, I32],
         "pencil_profile_read": [P, ctypes.POINTER(ProfEntry), I32, ctypes.POINTER(I32)],
+        "pencil_mul_probe": [P, I32, I64, I32, I32, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), P],
+        "pencil_ring_linear": [P, P, P, P, P, P, P, P],
+        "pencil_bias_grad": [P, P, P, P, P],
     }
     for name in EXPORTS:
         fn = getattr(lib, name)
@@ -157,6 +162,13 @@ class Context:
         n = ctypes.c_int32()
         _check(lib.pencil_profile_read(self.h, buf, 32, ctypes.byref(n)), "pencil_profile_read")
         return {KERNEL_NAMES[buf[i].kernel]: (buf[i].launches, buf[i].ms) for i in range(n.value)}
+
+    def mul_probe(self, which: int, iters: int, blocks: int, threads: int = 256, stream=None):
+        """(ms, chain steps) of the register-only multiply probe (0: mad.lo.u32, 1: Shoup mod-mul)."""
+        ms, steps = ctypes.c_double(), ctypes.c_double()
+        _check(lib.pencil_mul_probe(self.h, which, iters, blocks, threads, ctypes.byref(ms), ctypes.byref(steps),
+                                    _stream(stream)), "pencil_mul_probe")
+        return ms.value, steps.value
 
     def keygen(self, seed: int, stream=None) -> "SecretKey":
         return SecretKey(self, seed, stream)
@@ -278,3 +290,13 @@ def decrypt_to_share(ctx: Context, sk: SecretKey, plan: Plan, ct_out, y1, check_
 def pencil_ntt_batch(ctx: Context, polys: torch.Tensor, inverse: bool, stream=None):
     count = polys.numel() // (ctx.L * ctx.n)
     _check(lib.pencil_ntt_batch(ctx.h, _ptr(polys), count, int(inverse), _stream(stream)), "pencil_ntt_batch")
+
+
+def pencil_ring_linear(ctx: Context, plan: Plan, kernel_operand, input_operand, addend, out, addend2=None,
+                       stream=None):
+    _check(lib.pencil_ring_linear(ctx.h, plan.h, _ptr(kernel_operand), _ptr(input_operand), _ptr(addend),
+                                  _ptr(addend2), _ptr(out), _stream(stream)), "pencil_ring_linear")
+
+
+def pencil_bias_grad(ctx: Context, plan: Plan, g, out, stream=None):
+    _check(lib.pencil_bias_grad(ctx.h, plan.h, _ptr(g), _ptr(out), _stream(stream)), "pencil_bias_grad")
