@@ -1048,3 +1048,4 @@ extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, in
   *steps = (double)blocks * threads * 8.0 * (double)iters;
   return PENCIL_OK;
 }
+

@@ -300,3 +300,4 @@ def pencil_ring_linear(ctx: Context, plan: Plan, kernel_operand, input_operand, 
 
 def pencil_bias_grad(ctx: Context, plan: Plan, g, out, stream=None):
     _check(lib.pencil_bias_grad(ctx.h, plan.h, _ptr(g), _ptr(out), _stream(stream)), "pencil_bias_grad")
+

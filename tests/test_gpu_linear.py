@@ -193,6 +193,13 @@ def test_wgrad_small(he, L, part):
     local = _add(protocol.ring_op(L, WGRAD, gy1, x1, T_BITS), protocol.ring_op(L, WGRAD, gy0, x0, T_BITS))
     assert (_add(_add(to_np(tilde), to_np(gw_mask)), local.reshape(-1)) == gw.reshape(-1)).all()
     assert (gw == protocol.ring_op(L, WGRAD, gy, x, T_BITS)).all()
+    # ... and the same reconstruction on the GPU: DO adds its local term to the
+    # decrypted value (step 4), MO adds the mask and its own local term (step 6)
+    tilde_do = torch.empty_like(tilde)
+    he.pencil_ring_linear(ctx, plan, to_dev(gy1), to_dev(x1), tilde, tilde_do)
+    gw_dev = torch.empty_like(tilde)
+    he.pencil_ring_linear(ctx, plan, to_dev(gy0), to_dev(x0), tilde_do, gw_dev, addend2=gw_mask)
+    assert (to_np(gw_dev) == gw.reshape(-1)).all()
 
 
 def test_noise_check_flags_corrupted_ciphertext(he):
