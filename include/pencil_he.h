@@ -161,6 +161,29 @@ int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* p
                   int32_t operand, const uint64_t* share, uint64_t seed, uint64_t* ct,
                   void* ws, size_t ws_bytes, void* stream);
 
+/* encrypt_share without a workspace argument and without any allocation.
+ * (The paper has no counterpart: this is a deployment variant of the call
+ * above.)  It exists for data-owner code that must not allocate device memory
+ * when it encrypts: code running under a caching allocator that has already
+ * reserved the device's memory, a serving loop in which cudaMalloc's implicit
+ * device-wide synchronisation would stall every other stream, or embedders
+ * that have no device allocator of their own.
+ * Scratch: the sampled errors (count x N bytes, count = ct_in for INPUT,
+ * pt for KERNEL) live in a file-scope static device array of 8 MiB
+ * (8388608 bytes) inside the library, which every GPU that loads the
+ * library holds until the process exits.  Larger calls (e.g. more than 1024
+ * ciphertexts at N = 8192) return PENCIL_E_CAPACITY, print the reason on
+ * stderr and launch nothing.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the previous call's contents: each call writes every byte it
+ * then reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (different streams, or threads) race on it -- the caller must serialise
+ * them.  Outputs are bit-identical to encrypt_share with the same arguments. */
+int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* plan, int32_t operand,
+                          const uint64_t* share, uint64_t seed, uint64_t* ct, void* stream);
+
 /* MO: Algorithm 1 steps 2-3 for a FWD or DGRAD plan.
  *   ct_out[m,n] = sum_k (ct_in[m,k] + Delta*pi_v(x0)[m,k]) * pt[k,n] - Delta * s
  * with s one Z_t value per output element from Philox (key (mask_seed, 4),

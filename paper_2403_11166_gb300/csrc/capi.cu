@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1049,3 +1050,65 @@ extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, in
   return PENCIL_OK;
 }
 
+// ================================================================== allocation-free encryption
+// Scratch of encrypt_share_noalloc: the sampled encryption errors, one byte per
+// coefficient of every ciphertext of the call.  A file-scope device array, so
+// the call needs no workspace and allocates nothing; each GPU that loads the
+// library holds these 8 MiB until the process exits.
+#define PENCIL_NOALLOC_SCRATCH_BYTES (8ull << 20)
+#define PENCIL_NOALLOC_MAX_DEVICES 64
+static __device__ __align__(256) int8_t g_noalloc_scratch[PENCIL_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[PENCIL_NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on `device` (which must be current).
+// Host code cannot use the symbol itself: its name stands for a host-side
+// shadow, not for device memory.  Looked up once per device.
+static int noalloc_scratch(int device, int8_t** out) {
+  if (device < 0 || device >= PENCIL_NOALLOC_MAX_DEVICES) return PENCIL_E_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "pencil: encrypt_share_noalloc: cudaGetSymbolAddress failed on device %d: %s\n", device,
+              cudaGetErrorString(e));
+      return PENCIL_E_CUDA;
+    }
+    g_noalloc_addr[device] = p;
+  }
+  *out = reinterpret_cast<int8_t*>(g_noalloc_addr[device]);
+  return PENCIL_OK;
+}
+
+extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* P, int32_t operand,
+                                     const uint64_t* share, uint64_t seed, uint64_t* ct, void* stream) {
+  if (!ctx || !sk || !P || !share || !ct || P->ctx != ctx || sk->ctx != ctx) return PENCIL_E_ARG;
+  if (operand != PENCIL_OPERAND_INPUT && operand != PENCIL_OPERAND_KERNEL) return PENCIL_E_ARG;
+  if (!aligned16(ct)) return PENCIL_E_ARG;
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
+  const unsigned long long need = (unsigned long long)count * (unsigned long long)ctx->n;
+  if (need > PENCIL_NOALLOC_SCRATCH_BYTES) {
+    fprintf(stderr,
+            "pencil: encrypt_share_noalloc: %lld ciphertexts x N = %d need %llu bytes of scratch, more than the "
+            "%llu-byte static buffer; use encrypt_share with a workspace\n",
+            count, ctx->n, need, (unsigned long long)PENCIL_NOALLOC_SCRATCH_BYTES);
+    return PENCIL_E_CAPACITY;
+  }
+  DeviceGuard guard(ctx->device);
+  int8_t* err = nullptr;
+  const int rc = noalloc_scratch(ctx->device, &err);
+  if (rc != PENCIL_OK) return rc;
+  const cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(launch_sample_err(seed, (int)count, ctx->n, err, s));
+  ModeEncrypt::Params M;
+  M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
+  M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
+  M.ac.ptr = share;
+  M.err = err;
+  M.sk = sk->sk;
+  M.ct = ct;
+  M.seed = seed;
+  CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+  return PENCIL_OK;
+}

@@ -29,7 +29,8 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_keygen", "pencil_sk_destroy", "pencil_plan_linear", "pencil_plan_destroy",
            "pencil_plan_sizes", "encode_weights", "encrypt_share", "he_linear_forward",
            "he_linear_backward", "decrypt_to_share", "pencil_ntt_batch", "pencil_profile",
-           "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad")
+           "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad",
+           "encrypt_share_noalloc")
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
                 "ring", "bias_grad")
@@ -97,6 +98,7 @@ def _load():
                              ctypes.POINTER(ctypes.c_double), P],
         "pencil_ring_linear": [P, P, P, P, P, P, P, P],
         "pencil_bias_grad": [P, P, P, P, P],
+        "encrypt_share_noalloc": [P, P, P, I32, P, U64, P, P],
     }
     for name in EXPORTS:
         fn = getattr(lib, name)
@@ -301,3 +303,13 @@ def pencil_ring_linear(ctx: Context, plan: Plan, kernel_operand, input_operand, 
 def pencil_bias_grad(ctx: Context, plan: Plan, g, out, stream=None):
     _check(lib.pencil_bias_grad(ctx.h, plan.h, _ptr(g), _ptr(out), _stream(stream)), "pencil_bias_grad")
 
+
+def encrypt_share_noalloc(ctx: Context, sk: SecretKey, plan: Plan, operand: int, share: torch.Tensor, seed: int,
+                          ct: torch.Tensor, stream=None):
+    """encrypt_share without a workspace: for callers that may not allocate device
+    memory while encrypting.  Its scratch is a static 8 MiB device array in the
+    library (count x N bytes at most), shared by every call on a device: calls must
+    not overlap on the GPU.  The first call on a device should precede any stream
+    capture."""
+    _check(lib.encrypt_share_noalloc(ctx.h, sk.h, plan.h, operand, _ptr(share), seed, _ptr(ct), _stream(stream)),
+           "encrypt_share_noalloc")
