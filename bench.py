@@ -46,6 +46,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-only", action="store_true", help="run only the batched NTT sweep")
+    ap.add_argument("--sweep-polys", type=int, default=10000)
+    ap.add_argument("--sweep-points", default="12x2,12x3,12x4,13x2,13x3,13x4,14x2,14x3,14x4")
+    ap.add_argument("--sweep-reps", type=int, default=3)
+    ap.add_argument("--ntt-log-radix", type=int, default=0, help="force the NTT radix knob (4 or 5)")
+    ap.add_argument("--mac-columns", type=int, default=0, help="force the MAC columns knob (2, 4, 8)")
     return ap.parse_args()
 
 
@@ -159,6 +166,47 @@ def load_peaks():
             "alu_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz"}
 
 
+# ---------------------------------------------------------------- batched NTT sweep (row a10)
+def ntt_sweep(he, device: int, polys: int, points: str, reps: int, log_radix: int = 0):
+    """Sustained batched forward NTT and inverse NTT over `polys` uniform random
+    polynomials per (N, L) point (60-bit primes), CUDA events on the launch stream."""
+    import torch
+    peaks = load_peaks()
+    out = []
+    stream = torch.cuda.current_stream()
+    for pt in points.split(","):
+        log_n, L_ = (int(v) for v in pt.split("x"))
+        ctx = he.Context(log_n, L_, 60, T_BITS, device=device)
+        if log_radix:
+            ctx.tune(he.TUNE_NTT_LOG_RADIX, log_radix)
+        n = 1 << log_n
+        q_min = min(ctx.primes()[0])
+        a = torch.randint(0, q_min, (polys, L_, n), dtype=torch.int64, device=f"cuda:{device}")
+        he.pencil_ntt_batch(ctx, a, inverse=False)
+        he.pencil_ntt_batch(ctx, a, inverse=True)
+        res = {}
+        for inv in (False, True):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                he.pencil_ntt_batch(ctx, a, inverse=inv)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3 / reps
+            limb_ntts = polys * L_
+            mults = limb_ntts * limb_ntt_mults(n)
+            byts = limb_ntts * 16 * n
+            res["inv" if inv else "fwd"] = {
+                "limb_ntts_per_s": limb_ntts / sec, "ms": sec * 1e3,
+                "frac_alu": round(mults / sec / 1e12 / peaks["alu_tmul"], 4),
+                "frac_hbm": round(byts / sec / 1e9 / peaks["hbm_gbs"], 4)}
+        out.append({"N": n, "L": L_, "polys": polys, "log_radix": ctx.get_tune(he.TUNE_NTT_LOG_RADIX), **res})
+        del a
+        ctx.close()
+    return out
+
+
 # ---------------------------------------------------------------- oracle timing (host cores)
 def oracle_sample(seed: int = 0, part_tuple=(1, 2, 3, 32, 32, 3, 3), min_seconds: float = 0.0):
     """Times the oracle on one instance of every stage of the workload (repeated
@@ -255,7 +303,16 @@ def run_ours(args):
 
     dev = f"cuda:{local}"
     stream = torch.cuda.current_stream()
+    if args.sweep_only:
+        sw = ntt_sweep(he, local, args.sweep_polys, args.sweep_points, args.sweep_reps, args.ntt_log_radix)
+        if rank == 0:
+            print(json.dumps({"ntt_sweep": sw}), flush=True)
+        return
     ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=local)
+    if args.ntt_log_radix:
+        ctx.tune(he.TUNE_NTT_LOG_RADIX, args.ntt_log_radix)
+    if args.mac_columns:
+        ctx.tune(he.TUNE_MAC_COLUMNS, args.mac_columns)
     sk = ctx.keygen(1234 + rank)
     layer = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
                      LAYER["pad"])
@@ -301,7 +358,7 @@ def run_ours(args):
 
     # multiply-pipe probe: measured 32-bit IMAD and 64-bit Shoup rates (register-only)
     probe = {}
-    for which, key in ((0, "imad32"), (1, "shoup64")):
+    for which, key in ((0, "imad32"), (1, "shoup64"), (2, "madwide32"), (3, "mac128")):
         ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
         ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
         probe[key] = steps_p / (ms_p * 1e-3) / 1e12
@@ -354,6 +411,7 @@ def run_ours(args):
     peaks = load_peaks()
     dom, table, roof = roofline(prof, S, ctx.n, ctx.L, args.steps, peaks, ck)
     roof["probe"] = {"imad32_T_per_s": round(probe["imad32"], 3), "shoup64_T_per_s": round(probe["shoup64"], 3),
+                     "madwide32_T_per_s": round(probe["madwide32"], 3), "mac128_T_per_s": round(probe["mac128"], 3),
                      "note": "register-only chains, 8 per thread, 1216 x 256 threads, measured before the timed region"}
     launches = sum(v[0] for v in prof.values())
     if rank != 0:
@@ -377,6 +435,9 @@ def run_ours(args):
         "e2e": {"value": products / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
     }
+    if not args.no_sweep:
+        line["ntt_sweep"] = ntt_sweep(he, local, args.sweep_polys, args.sweep_points, args.sweep_reps,
+                                      args.ntt_log_radix)
     if world == 1 and not args.no_cpu_baseline:
         v, st, desc, spent = oracle_sample(part_tuple=plan.part, min_seconds=12.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,

@@ -72,6 +72,15 @@ int pencil_ctx_create(const PencilParams* params, int device, PencilCtx** out);
 int pencil_ctx_destroy(PencilCtx* ctx);
 /* Copies the L primes and roots (host arrays of length num_primes). */
 int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
+/* Tuning knobs of a context (chosen by the autotuner; results never depend on them).
+ * PENCIL_TUNE_NTT_LOG_RADIX: log2 of the coefficients each thread holds in the
+ * NTT kernels, i.e. the radix of one shared-memory round: 4 or 5.
+ * PENCIL_TUNE_MAC_COLUMNS: output ciphertexts per thread of the ct x pt
+ * multiply-accumulate: 2, 4 or 8. */
+enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1 };
+int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value);
+int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value);
+
 /* Reads and clears the device status word (synchronises the device):
  * *status = 0, or a PENCIL_E_* code recorded by a kernel. */
 int pencil_sync_status(PencilCtx* ctx, int32_t* status);
@@ -269,8 +278,12 @@ int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t max_entrie
 
 /* Multiply-pipe probe used to measure the integer roofline: `blocks` x
  * `threads` threads each run 8 independent register-only chains of `iters`
- * steps; which = 0: 32-bit multiply-add (mad.lo.u32), which = 1: 64-bit Shoup
- * modular multiply.  Times the launch with CUDA events on `stream` and returns
+ * steps; which = 0: 32-bit multiply-add (mad.lo.u32), 1: 64-bit Shoup modular
+ * multiply, 2: 32x32->64 multiply-add (mad.wide.u32), 3: 64x64->128
+ * multiply-accumulate, 4: split-quotient Shoup multiply (mul_shoup3), 5: forward
+ * butterfly on [0, 8q), 6: forward butterfly on [0, 4q) (Harvey), 7: inverse
+ * butterfly on [0, 4q), 8: inverse butterfly on [0, 2q) (Harvey), 9: 32x32
+ * high half (mul.hi.u32); for 5-8 a step is one butterfly.  Times the launch with CUDA events on `stream` and returns
  * the elapsed milliseconds and the number of chain steps (threads * 8 * iters).
  * Synchronises `stream`. */
 int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads, double* ms,

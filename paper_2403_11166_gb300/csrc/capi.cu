@@ -278,6 +278,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   DevCtx& d = ctx->dev;
   memset(&d, 0, sizeof(d));
   d.log_n = p.log_n;
+  d.ntt_loge = p.log_n <= 12 ? 4 : 5;
   d.n = n;
   d.L = p.num_primes;
   d.t_bits = p.t_bits;
@@ -311,7 +312,13 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     const u128 th = floor_pow2_div(128 + p.t_bits, q);
     lc.th_hi = (u64)(th >> 64);
     lc.th_lo = (u64)th;
+    lc.c60 = (u64)((((u128)1) << 60) % q);
+    lc.c64 = (u64)((((u128)1) << 64) % q);
   }
+  d.mac_nt = 4;
+  d.mac_split = 1;
+  for (int j = 0; j < d.L; ++j)
+    if (qs[j] >= (1ull << 60) || d.limb[j].c60 >= (1ull << 28) || d.limb[j].c64 >= (1ull << 28)) d.mac_split = 0;
   cudaError_t e1 = cudaMalloc(&ctx->tw_fwd, tf.size() * sizeof(ulonglong2));
   cudaError_t e2 = cudaMalloc(&ctx->tw_inv, ti.size() * sizeof(ulonglong2));
   cudaError_t e3 = cudaMalloc(&ctx->status, sizeof(int));
@@ -354,6 +361,34 @@ extern "C" int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_
     psis[j] = ctx->psis[j];
   }
   return PENCIL_OK;
+}
+
+extern "C" int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value) {
+  if (!ctx) return PENCIL_E_ARG;
+  if (knob == PENCIL_TUNE_NTT_LOG_RADIX) {
+    if (value != 4 && value != 5) return PENCIL_E_ARG;
+    ctx->dev.ntt_loge = value;
+    return PENCIL_OK;
+  }
+  if (knob == PENCIL_TUNE_MAC_COLUMNS) {
+    if (value != 2 && value != 4 && value != 8) return PENCIL_E_ARG;
+    ctx->dev.mac_nt = value;
+    return PENCIL_OK;
+  }
+  return PENCIL_E_ARG;
+}
+
+extern "C" int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value) {
+  if (!ctx || !value) return PENCIL_E_ARG;
+  if (knob == PENCIL_TUNE_NTT_LOG_RADIX) {
+    *value = ctx->dev.ntt_loge;
+    return PENCIL_OK;
+  }
+  if (knob == PENCIL_TUNE_MAC_COLUMNS) {
+    *value = ctx->dev.mac_nt;
+    return PENCIL_OK;
+  }
+  return PENCIL_E_ARG;
 }
 
 extern "C" int pencil_sync_status(PencilCtx* ctx, int32_t* status) {
@@ -1025,7 +1060,7 @@ extern "C" int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t
 
 extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads,
                                 double* ms, double* steps, void* stream) {
-  if (!ctx || !ms || !steps || (which != 0 && which != 1) || iters < 1 || blocks < 1 || threads < 32 ||
+  if (!ctx || !ms || !steps || which < 0 || which > 9 || iters < 1 || blocks < 1 || threads < 32 ||
       threads > 1024)
     return PENCIL_E_ARG;
   DeviceGuard guard(ctx->device);

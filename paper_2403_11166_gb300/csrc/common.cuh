@@ -21,10 +21,12 @@ struct LimbConst {
   u64 delta, deltas; // floor(q_total / t) mod q                  (BFV Delta)
   u64 qtil, qtils;   // (q_total / q_j)^{-1} mod q_j              (CRT)
   u64 th_hi, th_lo;  // floor(2^(128 + t_bits) / q_j), 128 bits   (t / q_j in 0.128 fixed point)
+  u64 c60, c64;      // 2^60 mod q and 2^64 mod q                 (split multiply-accumulate folds)
 };
 
 struct DevCtx {
   int log_n;
+  int ntt_loge;              // log2(coefficients per thread) of the NTT kernels: 4 or 5
   int n;
   int L;
   int t_bits;
@@ -33,6 +35,8 @@ struct DevCtx {
   const ulonglong2* tw_fwd;  // [L][N] (psi^brv(k), Shoup companion)
   const ulonglong2* tw_inv;  // [L][N] (psi^-brv(k), Shoup companion)
   int* status;               // device status word (atomicOr of error bits)
+  int mac_split;             // 1: every q_j < 2^60 with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
+  int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
 };
 
 // A strided view of a user tensor seen as (a, b, r, s) with spatial zero
@@ -88,6 +92,55 @@ __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const LimbConst& c) {
   return csub(s, c.q);
 }
 
+// Alternative formulations measured by pencil_mul_probe (variants 4, 5, 7):
+// on GB300 32x32 high products and 32x32->64 products run at half the rate of
+// 32-bit multiply-adds, and these variants came out no faster than the
+// compiler's Shoup product, so the NTT kernels use Harvey's butterflies below.
+//
+// a * w mod q in [0, 3q) for ANY a < 2^64, with w < q < 2^62, ws = floor(w 2^64 / q)
+// and nq = 2^64 - q.  Shoup's quotient hi64(a * ws) is formed from three
+// 32x32->64 multiply-adds (the low x low partial product is dropped, so the
+// quotient may be one below Shoup's and the remainder one q above his range
+// [0, 2q)); the remainder a * w - qt * q is computed as a * w + qt * nq mod 2^64
+// from two more 32x32->64 products and four 32-bit multiply-adds.
+__host__ __device__ __forceinline__ u64 mul_shoup3(u64 a, u64 w, u64 ws, u64 nq) {
+  const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+  const u32 s0 = (u32)ws, s1 = (u32)(ws >> 32);
+  const u64 t = (u64)a0 * s1;
+  const u64 u = (u64)a1 * s0 + (u32)t;
+  const u64 qt = (u64)a1 * s1 + ((t >> 32) + (u >> 32));
+  const u32 w0 = (u32)w, w1 = (u32)(w >> 32);
+  const u32 n0 = (u32)nq, n1 = (u32)(nq >> 32);
+  const u32 q0 = (u32)qt, q1 = (u32)(qt >> 32);
+  const u64 r = (u64)a0 * w0 + (u64)q0 * n0;
+  const u32 hi = a1 * w0 + a0 * w1 + q1 * n0 + q0 * n1;
+  return r + ((u64)hi << 32);
+}
+
+// x - c if x >= c else x, for x < 2^63 and c < 2^63 (sign of the difference).
+__host__ __device__ __forceinline__ u64 csub_s(u64 x, u64 c) {
+  const u64 d = x - c;
+  return ((i64)d < 0) ? x : d;
+}
+
+// Cooley-Tukey butterfly on the lazy range [0, 8q) (needs q < 2^60):
+// x, y in [0, 8q) -> x + w y, x - w y (mod q) in [0, 8q).
+__host__ __device__ __forceinline__ void ct_bf8(u64& x, u64& y, u64 w, u64 ws, u64 nq, u64 q3, u64 q4) {
+  const u64 a = csub_s(x, q4);                 // [0, 4q)
+  const u64 t = mul_shoup3(y, w, ws, nq);      // [0, 3q)
+  x = a + t;                                   // [0, 7q)
+  y = a + q3 - t;                              // (0, 7q]
+}
+
+// Gentleman-Sande butterfly on the lazy range [0, 4q):
+// x, y in [0, 4q) -> x + y, (x - y) w (mod q) in [0, 4q).
+__host__ __device__ __forceinline__ void gs_bf4(u64& x, u64& y, u64 w, u64 ws, u64 nq, u64 q4) {
+  const u64 s = csub_s(x + y, q4);             // [0, 4q)
+  const u64 d = x + q4 - y;                    // (0, 8q)
+  x = s;
+  y = mul_shoup3(d, w, ws, nq);                // [0, 3q)
+}
+
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
@@ -114,6 +167,11 @@ __device__ __forceinline__ void gs_butterfly(u64& x, u64& y, u64 w, u64 ws, u64 
   u64 d = x - y + q2;
   x = s;
   y = mul_shoup_lazy(d, w, ws, q);
+}
+
+// [0, 8q) -> [0, q)
+__device__ __forceinline__ u64 canon8(u64 x, u64 q) {
+  return csub(csub_s(csub_s(x, 4 * q), 2 * q), q);
 }
 
 // [0, 4q) -> [0, q)

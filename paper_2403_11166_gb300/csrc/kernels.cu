@@ -70,7 +70,161 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx ctx, MacParams P) {
   }
 }
 
+// ------------------------------------------------------------------ MAC, 30-bit split
+// Same product as k_mac, for q_j < 2^60 with 2^60 and 2^64 mod q_j below 2^28.
+// Operands a = aH 2^30 + aL, b = bH 2^30 + bL; each partial product is one
+// 32x32->64 multiply-add into one of three 64-bit accumulators of weight 1,
+// 2^30, 2^60:  S0 += aL bL,  S1 += aH bL + aL bH,  S2 += aH bH.
+// Every FOLD k-steps (products per accumulator <= 8, so all stay < 2^64) the
+// accumulators are folded mod q using 2^60 = c60 and 2^64 = c64:
+//   S0 += lo32(S2) c60;  S1 += hi32(S2) 4 c60;  S2 = 0;
+//   S0 += (S1 >> 34) c64;  S1 &= 2^34 - 1;  S1 += S0 >> 30;  S0 &= 2^30 - 1,
+// after which S0 < 2^30 and S1 < 2^35.  Thread = one slot, NT output columns.
+struct Acc3 {
+  u64 s0, s1, s2;
+};
+
+// Four 32x32->64 multiply-adds with the 64-bit accumulate fused into each
+// multiply (mad.wide.u32), so no separate 64-bit additions are issued.
+__device__ __forceinline__ void mac_split(Acc3& a, u32 aL, u32 aH, u32 bL, u32 bH) {
+  asm("mad.wide.u32 %0, %3, %5, %0;\n\t"
+      "mad.wide.u32 %1, %4, %5, %1;\n\t"
+      "mad.wide.u32 %1, %3, %6, %1;\n\t"
+      "mad.wide.u32 %2, %4, %6, %2;"
+      : "+l"(a.s0), "+l"(a.s1), "+l"(a.s2)
+      : "r"(aL), "r"(aH), "r"(bL), "r"(bH));
+}
+
+__device__ __forceinline__ void fold3(Acc3& a, u64 c60, u64 c64) {
+  a.s0 += (u64)(u32)a.s2 * (u32)c60;
+  a.s1 += (u64)(u32)(a.s2 >> 32) * (u32)(4 * c60);
+  a.s2 = 0;
+  a.s0 += (u64)(u32)(a.s1 >> 34) * (u32)c64;
+  a.s1 &= (1ull << 34) - 1;
+  a.s1 += a.s0 >> 30;
+  a.s0 &= (1ull << 30) - 1;
+}
+
+// canonical value of a folded accumulator: S0 + S1 2^30 (< 2^66) mod q
+__device__ __forceinline__ u64 acc3_value(Acc3 a, const LimbConst& lc) {
+  fold3(a, lc.c60, lc.c64);
+  const u64 lo = a.s0 + (a.s1 << 30);
+  const u64 hi = (a.s1 >> 34) + (lo < a.s0 ? 1ull : 0ull);
+  return reduce128(hi, lo, lc);
+}
+
+template <int NT, bool DUAL>
+__global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
+  const int ntiles = (P.NC + NT - 1) / NT;
+  const int m = blockIdx.x / ntiles + P.m_base;
+  const int n0 = (blockIdx.x % ntiles) * NT;
+  const int lane = blockIdx.y * blockDim.x + threadIdx.x;
+  if (lane >= P.lanes || m >= P.M) return;
+  const int nn = min(NT, P.NC - n0);
+  const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
+  const u64 c60 = lc.c60, c64 = lc.c64;
+  constexpr u32 M30 = (1u << 30) - 1;
+  Acc3 acc[NT][2];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) acc[j][c] = Acc3{0, 0, 0};
+  constexpr int FOLD = DUAL ? 2 : 4;
+  // operands of step k, loaded one step ahead
+  u64 a0, a1, pa = 0, b[NT], c0[NT], c1[NT];
+  auto load = [&](int k) {
+    const size_t mk = (size_t)m * P.K + k;
+    a0 = __ldg(P.a0 + mk * P.a0_stride + lane);
+    a1 = __ldg(P.a1 + mk * P.a1_stride + lane);
+    if constexpr (DUAL) pa = __ldg(P.pa + mk * P.pa_stride + lane);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const size_t kn = (size_t)k * P.NC + n0 + (j < nn ? j : 0);
+      b[j] = __ldg(P.b + kn * P.b_stride + lane);
+      if constexpr (DUAL) {
+        c0[j] = __ldg(P.cb0 + kn * P.cb_stride + lane);
+        c1[j] = __ldg(P.cb1 + kn * P.cb_stride + lane);
+      }
+    }
+  };
+  load(0);
+  for (int k = 0; k < P.K; ++k) {
+    const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
+    const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
+    const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
+    u32 bL[NT], bH[NT], c0L[NT], c0H[NT], c1L[NT], c1H[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      bL[j] = (u32)b[j] & M30;
+      bH[j] = (u32)(b[j] >> 30);
+      if constexpr (DUAL) {
+        c0L[j] = (u32)c0[j] & M30;
+        c0H[j] = (u32)(c0[j] >> 30);
+        c1L[j] = (u32)c1[j] & M30;
+        c1H[j] = (u32)(c1[j] >> 30);
+      }
+    }
+    if (k + 1 < P.K) load(k + 1);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      mac_split(acc[j][0], a0L, a0H, bL[j], bH[j]);
+      mac_split(acc[j][1], a1L, a1H, bL[j], bH[j]);
+      if constexpr (DUAL) {
+        mac_split(acc[j][0], c0L[j], c0H[j], pL, pH);
+        mac_split(acc[j][1], c1L[j], c1H[j], pL, pH);
+      }
+    }
+    if ((k % FOLD) == FOLD - 1) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        fold3(acc[j][0], c60, c64);
+        fold3(acc[j][1], c60, c64);
+      }
+    }
+  }
+  const size_t ln = (size_t)P.lanes;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (j < nn) {
+      const size_t o = ((size_t)m * P.NC + n0 + j) * 2 * ln + lane;
+      P.out[o] = acc3_value(acc[j][0], lc);
+      P.out[o + ln] = acc3_value(acc[j][1], lc);
+    }
+  }
+}
+
+template <int NT>
+static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  const int threads = 128;
+  MacParams P = P0;
+  const int ntiles = (P.NC + NT - 1) / NT;
+  const unsigned gy = (unsigned)((P.lanes + threads - 1) / threads);
+  const int mchunk = max(1, 2147483647 / max(1, ntiles));
+  for (int base = 0; base < P0.M; base += mchunk) {
+    P.m_base = base;
+    const int mc = min(mchunk, P0.M - base);
+    dim3 grid((unsigned)(mc * ntiles), gy);
+    if (dual)
+      k_mac_split<NT, true><<<grid, threads, 0, s>>>(ctx, P);
+    else
+      k_mac_split<NT, false><<<grid, threads, 0, s>>>(ctx, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  if (ctx.mac_split) {
+    switch (ctx.mac_nt) {
+      case 2:
+        return launch_mac_split<2>(ctx, P0, dual, s);
+      case 8:
+        return launch_mac_split<8>(ctx, P0, dual, s);
+      default:
+        return launch_mac_split<4>(ctx, P0, dual, s);
+    }
+  }
   constexpr int NT = 8;
   const int threads = 256;
   MacParams P = P0;
@@ -345,7 +499,7 @@ __global__ void k_mul_probe(int which, long long iters, u64 seed, u64* sink) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc ^= x[i];
     if (acc == 0xFFFFFFFFu && seed == 0) sink[0] = acc;
-  } else {
+  } else if (which == 1) {
     const u64 q = 0xfffffffffffc001ull;
     const u64 w = (seed | 1ull) % q;
     const u64 ws = (u64)((((unsigned __int128)w) << 64) / q);
@@ -359,6 +513,89 @@ __global__ void k_mul_probe(int which, long long iters, u64 seed, u64* sink) {
     u64 acc = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == ~0ull && seed == 0) sink[0] = acc;
+  } else if (which == 2) {
+    // 32 x 32 -> 64 multiply with 64-bit accumulate (mad.wide.u32), 8 chains
+    u64 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = seed + t + i;
+    const u32 a = (u32)(seed >> 32) | 1u, b = (u32)seed ^ 0x9e3779b9u;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        asm volatile("{\n\t.reg .u32 lo;\n\tcvt.u32.u64 lo, %0;\n\tmad.wide.u32 %0, lo, %1, %0;\n\t}"
+                     : "+l"(x[i])
+                     : "r"(a ^ (b + i)));
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == ~0ull && seed == 0) sink[0] = acc;
+  } else if (which == 9) {
+    // 32 x 32 -> high 32 bits (mul.hi.u32), 8 dependent chains
+    u32 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (u32)seed + t * 2654435761u + i;
+    const u32 a = (u32)(seed >> 32) | 0x80000001u;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(x[i]) : "r"(a + i));
+    }
+    u32 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == 0xFFFFFFFFu && seed == 0) sink[0] = acc;
+  } else if (which >= 4) {
+    // butterfly / modmul formulations of the NTT kernels, 8 independent values
+    const u64 q = 0xfffffffffffc001ull, q2 = 2 * q, q3 = 3 * q, q4 = 4 * q, nq = 0ull - q;
+    const u64 w = (seed | 1ull) % q;
+    const u64 ws = (u64)((((unsigned __int128)w) << 64) / q);
+    u64 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (seed + t * 0x9E3779B97F4A7C15ull + i) % q;
+    for (long long it = 0; it < iters; ++it) {
+      if (which == 4) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = mul_shoup3(x[i], w, ws, nq);
+      } else if (which == 5) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ct_bf8(x[i], x[i + 1], w, ws, nq, q3, q4);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ct_bf8(x[i + 1], x[i], w, ws, nq, q3, q4);
+      } else if (which == 6) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ct_butterfly(x[i], x[i + 1], w, ws, q, q2);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ct_butterfly(x[i + 1], x[i], w, ws, q, q2);
+      } else if (which == 7) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gs_bf4(x[i], x[i + 1], w, ws, nq, q4);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gs_bf4(x[i + 1], x[i], w, ws, nq, q4);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gs_butterfly(x[i], x[i + 1], w, ws, q, q2);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gs_butterfly(x[i + 1], x[i], w, ws, q, q2);
+      }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    if (acc == ~0ull && seed == 0) sink[0] = acc;
+  } else {
+    // 64 x 64 -> 128 multiply-accumulate as written in the MAC kernel
+    u64 lo[8], hi[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) lo[i] = hi[i] = seed + t + i;
+    const u64 a = seed | 1ull, b = seed ^ 0x0123456789abcdefull;
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) mac128(lo[i], hi[i], a + i, b ^ lo[i]);
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= lo[i] ^ hi[i];
     if (acc == ~0ull && seed == 0) sink[0] = acc;
   }
 }

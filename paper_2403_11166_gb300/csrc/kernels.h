@@ -57,16 +57,17 @@ PENCIL_NTT_INSTANTIATE(extern, 12)
 PENCIL_NTT_INSTANTIATE(extern, 13)
 PENCIL_NTT_INSTANTIATE(extern, 14)
 
-// Dispatch on log2(N) at run time.
+// Dispatch on log2(N) and the context's radix (log2 of coefficients per thread).
 template <class Mode, bool INV>
 cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
+  const bool r4 = ctx.ntt_loge == 4;
   switch (ctx.log_n) {
     case 12:
-      return launch_ntt<12, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<12, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<12, 5, Mode, INV>(ctx, P, count, s);
     case 13:
-      return launch_ntt<13, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<13, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<13, 5, Mode, INV>(ctx, P, count, s);
     case 14:
-      return launch_ntt<14, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<14, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<14, 5, Mode, INV>(ctx, P, count, s);
     default:
       return cudaErrorInvalidValue;
   }

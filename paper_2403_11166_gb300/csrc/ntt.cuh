@@ -4,7 +4,9 @@
 // transform.  Forward = Cooley-Tukey with twiddles psi^brv(m+i) (natural order
 // in, bit-reversed evaluation order out); inverse = Gentleman-Sande with
 // psi^-brv(m+i), then N^{-1}.  Harvey's lazy butterflies keep forward values
-// in [0, 4q) and inverse values in [0, 2q); q < 2^62 keeps 4q < 2^64.
+// in [0, 4q) and inverse values in [0, 2q); q < 2^62 keeps 4q < 2^64.  (The
+// wider-range variants ct_bf8 / gs_bf4 of common.cuh measured slower on GB300
+// with pencil_mul_probe and are not used here.)
 //
 // GB300 mapping: T = N / E threads each hold E = 2^LOGE coefficients in
 // registers and run LOGE radix-2 stages between two shared-memory exchanges
@@ -19,11 +21,14 @@
 
 namespace pencil {
 
-// Shared-memory slot of coefficient x: XOR swizzle at 16-element granularity so
-// that strided round accesses spread over the 32 banks.
+// Shared-memory slot of coefficient x: the low four index bits are XOR-ed with
+// (bits 4..7) ^ (bits 5..8).  8-byte accesses are served per half-warp (16
+// threads over the 16 bank pairs); with this swizzle every round's strided
+// accesses and the epilogue's pair accesses hit 16 distinct bank pairs in each
+// half-warp (two wavefronts per warp access, the minimum), for every N and radix.
 template <int LOGN>
 __device__ __forceinline__ int sidx(int x) {
-  return x ^ ((x >> 4) & 15);
+  return x ^ (((x >> 4) ^ (x >> 5)) & 15);
 }
 
 template <int LOGN, int LOGE, int S0>
@@ -127,22 +132,23 @@ struct InvRounds {
   }
 };
 
-template <int LOGN>
+template <int LOGN, int LOGE_>
 struct NttCfg {
-  static constexpr int LOGE = LOGN <= 12 ? 4 : 5;
+  static constexpr int LOGE = LOGE_;
   static constexpr int N = 1 << LOGN;
   static constexpr int E = 1 << LOGE;
   static constexpr int T = N >> LOGE;
   static constexpr int LAST_S0 = ((LOGN - 1) / LOGE) * LOGE;
   static constexpr size_t SMEM = (size_t)N * sizeof(u64);
-  static constexpr int MIN_BLOCKS = LOGN >= 14 ? 1 : 2;   // 128 KB of smem: one CTA per SM
+  static constexpr int MIN_BLOCKS = T >= 512 ? 1 : 2;   // 512+ threads: one CTA per SM
 };
 
 // Forward transform with a fused prologue (Mode::load, canonical coefficient
 // e) and epilogue (Mode::store2, canonical slots e and e + 1).
-template <int LOGN, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN>::T, NttCfg<LOGN>::MIN_BLOCKS) k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
-  using C = NttCfg<LOGN>;
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
+  using C = NttCfg<LOGN, LOGE>;
   extern __shared__ u64 sm[];
   const int tau = threadIdx.x;
   const int poly = blockIdx.x;
@@ -165,9 +171,10 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::T, NttCfg<LOGN>::MIN_BLOCKS) k_n
 
 // Inverse transform with a fused prologue (Mode::load, value in [0, 2q)) and
 // epilogue (Mode::store, canonical coefficient e).
-template <int LOGN, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN>::T, NttCfg<LOGN>::MIN_BLOCKS) k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
-  using C = NttCfg<LOGN>;
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
+  using C = NttCfg<LOGN, LOGE>;
   extern __shared__ u64 sm[];
   const int tau = threadIdx.x;
   const int poly = blockIdx.x;
@@ -365,40 +372,40 @@ struct ModeDecrypt {
 };
 
 // Host-side launcher; explicitly instantiated per LOGN in ntt12.cu / ntt13.cu / ntt14.cu.
-template <int LOGN, class Mode, bool INV>
+template <int LOGN, int LOGE, class Mode, bool INV>
 cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
-  using C = NttCfg<LOGN>;
+  using C = NttCfg<LOGN, LOGE>;
   if (count <= 0) return cudaSuccess;
   cudaError_t err;
   dim3 grid((unsigned)count, (unsigned)ctx.L);
   if constexpr (INV) {
-    err = cudaFuncSetAttribute(k_ntt_inv<LOGN, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    err = cudaFuncSetAttribute(k_ntt_inv<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_inv<LOGN, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+    k_ntt_inv<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
   } else {
-    err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_fwd<LOGN, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+    k_ntt_fwd<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
   }
   return cudaGetLastError();
 }
 
-#define PENCIL_NTT_INSTANTIATE(SPEC, LOGN)                                                                 \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeRaw, false>(const DevCtx&, const ModeRaw::Params&, int,         \
-                                                             cudaStream_t);                                \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeRaw, true>(const DevCtx&, const ModeRaw::Params&, int,          \
-                                                            cudaStream_t);                                 \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeEncrypt, false>(const DevCtx&, const ModeEncrypt::Params&, int, \
-                                                                 cudaStream_t);                            \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeAddPlain, false>(const DevCtx&, const ModeAddPlain::Params&,    \
-                                                                  int, cudaStream_t);                      \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeEncode, false>(const DevCtx&, const ModeEncode::Params&, int,   \
-                                                                cudaStream_t);                             \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeMask, false>(const DevCtx&, const ModeMask::Params&, int,       \
-                                                              cudaStream_t);                               \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeKeygen, false>(const DevCtx&, const ModeKeygen::Params&, int,   \
-                                                                cudaStream_t);                             \
-  SPEC template cudaError_t launch_ntt<LOGN, ModeDecrypt, true>(const DevCtx&, const ModeDecrypt::Params&, int,  \
-                                                                cudaStream_t);
+#define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV) \
+  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, cudaStream_t);
+#define PENCIL_NTT_INST_E(SPEC, LOGN, LOGE)                \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, false)       \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, true)        \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncrypt, false)   \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeAddPlain, false)  \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMask, false)      \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
+// Radix 2^4 and 2^5 register blocks for one N.
+#define PENCIL_NTT_INSTANTIATE(SPEC, LOGN) \
+  PENCIL_NTT_INST_E(SPEC, LOGN, 4)         \
+  PENCIL_NTT_INST_E(SPEC, LOGN, 5)
 
 }  // namespace pencil

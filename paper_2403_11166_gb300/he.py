@@ -30,7 +30,9 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_plan_sizes", "encode_weights", "encrypt_share", "he_linear_forward",
            "he_linear_backward", "decrypt_to_share", "pencil_ntt_batch", "pencil_profile",
            "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad",
-           "encrypt_share_noalloc")
+           "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune")
+TUNE_NTT_LOG_RADIX = 0
+TUNE_MAC_COLUMNS = 1
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
                 "ring", "bias_grad")
@@ -99,6 +101,8 @@ def _load():
         "pencil_ring_linear": [P, P, P, P, P, P, P, P],
         "pencil_bias_grad": [P, P, P, P, P],
         "encrypt_share_noalloc": [P, P, P, I32, P, U64, P, P],
+        "pencil_ctx_tune": [P, I32, I32],
+        "pencil_ctx_get_tune": [P, I32, ctypes.POINTER(I32)],
     }
     for name in EXPORTS:
         fn = getattr(lib, name)
@@ -149,6 +153,14 @@ class Context:
         r = (ctypes.c_uint64 * self.L)()
         _check(lib.pencil_ctx_primes(self.h, q, r), "pencil_ctx_primes")
         return list(q), list(r)
+
+    def tune(self, knob: int, value: int):
+        _check(lib.pencil_ctx_tune(self.h, knob, value), "pencil_ctx_tune")
+
+    def get_tune(self, knob: int) -> int:
+        v = ctypes.c_int32()
+        _check(lib.pencil_ctx_get_tune(self.h, knob, ctypes.byref(v)), "pencil_ctx_get_tune")
+        return v.value
 
     def sync_status(self) -> int:
         s = ctypes.c_int32()

@@ -37,3 +37,17 @@ def split_shares(g: np.random.Generator, x: np.ndarray, t_bits: int = T_BITS):
     with np.errstate(over="ignore"):
         x0 = (xu - x1) & np.uint64((1 << t_bits) - 1)
     return x0, x1
+
+
+def cnn_params(seed: int, channels=(3, 16, 32), height: int = 32, width: int = 32, classes: int = 10,
+               frac_bits: int = FRAC_BITS) -> dict:
+    """Weights of the 3-layer CNN workload: N(0, 1/fan_in) rounded down to the
+    fixed-point grid, zero biases (float64 numpy arrays)."""
+    g = rng(seed)
+    c0, c1, c2 = channels
+    fc_in = c2 * (height // 2) * (width // 2)
+
+    def w(shape, fan):
+        return np.floor(g.standard_normal(shape) / np.sqrt(fan) * (1 << frac_bits)) / (1 << frac_bits)
+    return {"w1": w((c1, c0, 3, 3), c0 * 9), "b1": np.zeros(c1), "w2": w((c2, c1, 3, 3), c1 * 9),
+            "b2": np.zeros(c2), "w3": w((classes, fc_in), fc_in), "b3": np.zeros(classes)}

@@ -253,3 +253,26 @@ def test_host_validation(he):
                              device="cuda"), None, 1, plan.new_ct(1), torch.zeros(64, dtype=torch.int64,
                              device="cuda"), plan.new_ws(1 << 20))
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("radix,cols", [(4, 2), (5, 4), (4, 8), (5, 8)])
+def test_tuning_knobs_do_not_change_results(he, radix, cols):
+    """Every NTT radix / MAC column setting gives bit-identical ciphertexts and shares
+    (the default setting is checked against the oracle above)."""
+    cfg = (13, 3, 60)
+    L = Layer("conv", B=3, Ci=5, Co=7, h=9, w=8, s=3, pad=1)
+    part = (1, 2, 3, 5, 4, 3, 3)
+    outs = []
+    for setting in (None, (radix, cols)):
+        ctx = he.Context(*cfg)
+        if setting:
+            ctx.tune(he.TUNE_NTT_LOG_RADIX, setting[0])
+            ctx.tune(he.TUNE_MAC_COLUMNS, setting[1])
+            assert ctx.get_tune(he.TUNE_MAC_COLUMNS) == setting[1]
+        sk = ctx.keygen(5)
+        g = inputs.rng(8)
+        W = inputs.gaussian_fixed(g, L.w_shape())
+        x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L.x_shape()))
+        outs.append(gpu_forward(he, ctx, sk, L, he.ROLE_FWD, part, W, x1, x0, None, 3, 4)[1:])
+    for a, b in zip(*outs):
+        assert (a == b).all()
