@@ -82,7 +82,8 @@ int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value);
 int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value);
 
 /* Reads and clears the device status word (synchronises the device):
- * *status = 0, or a PENCIL_E_* code recorded by a kernel. */
+ * *status = 0, or a PENCIL_E_* code recorded by a kernel (PENCIL_E_TIMEOUT
+ * takes precedence over PENCIL_E_NOISE, which it usually causes). */
 int pencil_sync_status(PencilCtx* ctx, int32_t* status);
 
 /* DO side: ternary secret key s_i = (w_i mod 3) - 1, w = Philox4x64-10 word
@@ -255,6 +256,50 @@ int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* g, 
 /* In-place batched negacyclic NTT (inverse = 0) or INTT (inverse = 1) of
  * `count` polynomials laid out [count][L][N], canonical in and out (Sec. 5 "NTT"). */
 int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream);
+
+/* ---------------------------------------------------------------- batched layers
+ * Many FWD plans of one context executed as one fixed launch sequence
+ * (workload of many uneven layers, Sec. 3.2.1 applied layer by layer): every
+ * stage of every layer in one multi-plan launch, and the ct x pt products of
+ * all layers in ONE persistent launch over a (layer, block, output tile, slot
+ * block) work list.  pencil_batch_forward launches kernels only (no
+ * allocation, no copy), so a sequence of calls can be captured in a CUDA graph.
+ * A device step counter, advanced by every call, re-keys the randomness: layer
+ * l of call number k uses encryption seed enc_seed + l + (k << 32) and mask
+ * seed mask_seed + l + (k << 32), i.e. exactly the per-layer calls
+ * encrypt_share / he_linear_forward with those seeds; encode_weights and
+ * decrypt_to_share complete the sequence.
+ * The persistent multiply-accumulate waits (bounded by clock64, about 2 ms)
+ * for each layer's ready word written after its input stages; on expiry it
+ * sets PENCIL_E_TIMEOUT in the status word and abandons the remaining work
+ * (the outputs of that call are then invalid). */
+typedef struct PencilBatch PencilBatch;
+enum { PENCIL_BATCH_PT = 0, PENCIL_BATCH_CT_IN = 1, PENCIL_BATCH_CT_OUT = 2 };
+/* plans: `count` FWD plans of ctx (each may appear once per layer). */
+int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plans, int32_t count, PencilBatch** out);
+int pencil_batch_destroy(PencilBatch* batch);
+/* Bytes of device workspace holding every layer's plaintexts and ciphertexts. */
+int pencil_batch_workspace(const PencilBatch* batch, int64_t* bytes);
+/* Device buffers of layer `layer` (user layouts as for the per-layer calls;
+ * bias nullable). */
+int pencil_batch_bind(PencilBatch* batch, int32_t layer, const int64_t* W, const uint64_t* x1, const uint64_t* x0,
+                      const uint64_t* bias, uint64_t* y0, uint64_t* y1);
+/* Builds the device work lists and parameters (allocates and copies: call it
+ * before any capture).  Requires every layer bound, ws >= pencil_batch_workspace
+ * bytes, and primes near 2^bits (the split multiply-accumulate; else
+ * PENCIL_E_UNIMPL).  Re-commit after changing PENCIL_TUNE_MAC_COLUMNS. */
+int pencil_batch_commit(PencilBatch* batch, const PencilSecretKey* sk, void* ws, size_t ws_bytes, uint64_t enc_seed,
+                        uint64_t mask_seed);
+/* One forward pass of every layer on `stream` (capturable). */
+int pencil_batch_forward(PencilCtx* ctx, PencilBatch* batch, void* stream);
+/* Sets the step counter (synchronises the device) and clears an earlier abort. */
+int pencil_batch_set_step(PencilBatch* batch, uint64_t step);
+/* Copies layer `layer`'s plaintexts / input / output ciphertexts (as left by the
+ * last call) to `dst` (device memory of the plan's counts, stream-ordered). */
+int pencil_batch_read(const PencilBatch* batch, int32_t layer, int32_t which, uint64_t* dst, void* stream);
+/* Failure injection for tests: layer `layer`'s ready word is never written
+ * (-1: none), so the multiply-accumulate times out instead of hanging. */
+int pencil_batch_withhold(PencilBatch* batch, int32_t layer);
 
 /* ---------------------------------------------------------------- profiling
  * Per-kernel timing with CUDA events recorded on the launch stream around every

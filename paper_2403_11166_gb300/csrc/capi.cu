@@ -398,7 +398,8 @@ extern "C" int pencil_sync_status(PencilCtx* ctx, int32_t* status) {
   CUDA_TRY(cudaDeviceSynchronize());
   CUDA_TRY(cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(int)));
-  *status = (v & 1) ? PENCIL_E_NOISE : (v & 2) ? PENCIL_E_TIMEOUT : PENCIL_OK;
+  // a timed-out wait leaves outputs unwritten, which then also fail the noise check
+  *status = (v & 2) ? PENCIL_E_TIMEOUT : (v & 1) ? PENCIL_E_NOISE : PENCIL_OK;
   return PENCIL_OK;
 }
 
@@ -1145,5 +1146,292 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
   M.ct = ct;
   M.seed = seed;
   CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+  return PENCIL_OK;
+}
+
+// ================================================================== batched layers
+struct PencilBatch {
+  PencilCtx* ctx = nullptr;
+  std::vector<const PencilPlan*> plans;
+  struct User {
+    const int64_t* W = nullptr;
+    const u64 *x1 = nullptr, *x0 = nullptr, *bias = nullptr;
+    u64 *y0 = nullptr, *y1 = nullptr;
+    bool bound = false;
+  };
+  struct Off {
+    long long pt, ct_in, ct_out, err, c0p, mpoly, yres;
+  };
+  std::vector<User> user;
+  std::vector<Off> off;
+  long long ws_bytes = 0;
+  char* ws = nullptr;
+  void* d_mem = nullptr;
+  BatchDev dev;
+  int mac_nt = 0;
+  bool committed = false;
+};
+
+extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plans, int32_t count, PencilBatch** out) {
+  if (!ctx || !plans || !out || count < 1) return PENCIL_E_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!plans[i] || plans[i]->ctx != ctx || plans[i]->role != PENCIL_ROLE_FWD) return PENCIL_E_ARG;
+  PencilBatch* B = new (std::nothrow) PencilBatch();
+  if (!B) return PENCIL_E_CUDA;
+  B->ctx = ctx;
+  B->plans.assign(plans, plans + count);
+  B->user.resize(count);
+  const long long n = ctx->n, lnb = (long long)ctx->dev.L * n * 8;
+  auto al = [](long long b) { return (b + 255) / 256 * 256; };
+  long long o = 0;
+  for (int i = 0; i < count; ++i) {
+    const PencilPlan* P = plans[i];
+    PencilBatch::Off f;
+    f.pt = o;
+    o += al(P->pt * lnb);
+    f.ct_in = o;
+    o += al(P->ct_in * 2 * lnb);
+    f.ct_out = o;
+    o += al(P->ct_out * 2 * lnb);
+    f.err = o;
+    o += al(P->ct_in * n);
+    f.c0p = o;
+    o += al(P->ct_in * lnb);
+    f.mpoly = o;
+    o += al(P->ct_out * n * 8);
+    f.yres = o;
+    o += al(P->ct_out * lnb);
+    B->off.push_back(f);
+  }
+  B->ws_bytes = o;
+  memset(&B->dev, 0, sizeof(B->dev));
+  B->dev.withhold = -1;
+  *out = B;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_destroy(PencilBatch* B) {
+  if (!B) return PENCIL_E_ARG;
+  DeviceGuard guard(B->ctx->device);
+  cudaFree(B->d_mem);
+  delete B;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_workspace(const PencilBatch* B, int64_t* bytes) {
+  if (!B || !bytes) return PENCIL_E_ARG;
+  *bytes = B->ws_bytes;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_bind(PencilBatch* B, int32_t layer, const int64_t* W, const uint64_t* x1,
+                                 const uint64_t* x0, const uint64_t* bias, uint64_t* y0, uint64_t* y1) {
+  if (!B || layer < 0 || layer >= (int)B->plans.size() || !W || !x1 || !x0 || !y0 || !y1) return PENCIL_E_ARG;
+  B->user[layer] = PencilBatch::User{W, x1, x0, bias, y0, y1, true};
+  B->committed = false;
+  return PENCIL_OK;
+}
+
+template <class T>
+static void put(std::vector<char>& blob, size_t& at, const std::vector<T>& v, size_t& where) {
+  at = (at + 255) / 256 * 256;
+  where = at;
+  blob.resize(at + v.size() * sizeof(T));
+  if (!v.empty()) memcpy(blob.data() + at, v.data(), v.size() * sizeof(T));
+  at += v.size() * sizeof(T);
+}
+
+extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, void* ws, size_t ws_bytes,
+                                   uint64_t enc_seed, uint64_t mask_seed) {
+  if (!B || !sk || !ws || sk->ctx != B->ctx || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < B->ws_bytes) return PENCIL_E_CAPACITY;
+  for (const auto& u : B->user)
+    if (!u.bound) return PENCIL_E_ARG;
+  PencilCtx* ctx = B->ctx;
+  DeviceGuard guard(ctx->device);
+  const int L = ctx->dev.L, n = ctx->n;
+  const long long lnw = (long long)L * n;
+  char* w = reinterpret_cast<char*>(ws);
+  const int nl = (int)B->plans.size();
+  const int nt = ctx->dev.mac_nt;
+  std::vector<ModeEncode::Params> enc(nl);
+  std::vector<ModeEncrypt::Params> encr(nl);
+  std::vector<ModeAddPlain::Params> addp(nl);
+  std::vector<ModeMask::Params> mask(nl);
+  std::vector<ModeDecrypt::Params> dec(nl);
+  std::vector<SampleP> samp(nl);
+  std::vector<MaskPolyP> mpol(nl);
+  std::vector<MoShareP> mosh(nl);
+  std::vector<CombineP> comb(nl);
+  std::vector<MacParams> mac(nl);
+  std::vector<int2> it_pt, it_in, it_out, it_sh;
+  std::vector<int4> it_mac;
+  for (int l = 0; l < nl; ++l) {
+    const PencilPlan* P = B->plans[l];
+    const auto& u = B->user[l];
+    const auto& f = B->off[l];
+    u64* pt = reinterpret_cast<u64*>(w + f.pt);
+    u64* ct_in = reinterpret_cast<u64*>(w + f.ct_in);
+    u64* ct_out = reinterpret_cast<u64*>(w + f.ct_out);
+    int8_t* err = reinterpret_cast<int8_t*>(w + f.err);
+    u64* c0p = reinterpret_cast<u64*>(w + f.c0p);
+    u64* mpoly = reinterpret_cast<u64*>(w + f.mpoly);
+    u64* yres = reinterpret_cast<u64*>(w + f.yres);
+    enc[l].pk = P->pk_w;
+    enc[l].ac = P->acc_w;
+    enc[l].ac.ptr = reinterpret_cast<const u64*>(u.W);
+    enc[l].pt = pt;
+    samp[l] = SampleP{enc_seed + (u64)l, err};
+    encr[l].pk = P->pk_v;
+    encr[l].ac = P->acc_v;
+    encr[l].ac.ptr = u.x1;
+    encr[l].err = err;
+    encr[l].sk = sk->sk;
+    encr[l].ct = ct_in;
+    encr[l].seed = enc_seed + (u64)l;
+    addp[l].pk = P->pk_v;
+    addp[l].ac = P->acc_v;
+    addp[l].ac.ptr = u.x0;
+    addp[l].ct_in = ct_in;
+    addp[l].out_c0 = c0p;
+    memset(&mac[l], 0, sizeof(MacParams));
+    mac[l].a0 = c0p;
+    mac[l].a0_stride = lnw;
+    mac[l].a1 = ct_in + lnw;
+    mac[l].a1_stride = 2 * lnw;
+    mac[l].b = pt;
+    mac[l].b_stride = lnw;
+    mac[l].out = ct_out;
+    mac[l].M = (int)P->c.M();
+    mac[l].K = (int)P->c.K();
+    mac[l].NC = P->c.NC;
+    mac[l].lanes = (int)lnw;
+    mpol[l] = MaskPolyP{P->pk_y, P->acc_y, mask_seed + (u64)l, mpoly};
+    mask[l].mpoly = mpoly;
+    mask[l].ct = ct_out;
+    mosh[l] = MoShareP{mask_seed + (u64)l, P->out_elems, u.bias, P->hw, P->co_out, u.y0};
+    dec[l].ct = ct_out;
+    dec[l].sk = sk->sk;
+    dec[l].out = yres;
+    comb[l] = CombineP{P->pk_y, P->acc_y, yres, u.y1};
+    for (long long i = 0; i < P->pt; ++i) it_pt.push_back(make_int2(l, (int)i));
+    for (long long i = 0; i < P->ct_in; ++i) it_in.push_back(make_int2(l, (int)i));
+    for (long long i = 0; i < P->ct_out; ++i) it_out.push_back(make_int2(l, (int)i));
+    for (long long c = 0; c < (P->out_elems + 1023) / 1024; ++c) it_sh.push_back(make_int2(l, (int)c));
+    const int lane_blocks = (int)((lnw + 127) / 128);
+    for (long long m = 0; m < P->c.M(); ++m)
+      for (int n0 = 0; n0 < P->c.NC; n0 += nt)
+        for (int lb = 0; lb < lane_blocks; ++lb) it_mac.push_back(make_int4(l, (int)m, n0, lb));
+  }
+  if (!ctx->dev.mac_split) return PENCIL_E_UNIMPL;
+  std::vector<char> blob;
+  size_t at = 0, o_enc, o_encr, o_addp, o_mask, o_dec, o_samp, o_mpol, o_mosh, o_comb, o_mac, o_pt, o_in, o_out,
+         o_sh, o_imac, o_words;
+  put(blob, at, enc, o_enc);
+  put(blob, at, encr, o_encr);
+  put(blob, at, addp, o_addp);
+  put(blob, at, mask, o_mask);
+  put(blob, at, dec, o_dec);
+  put(blob, at, samp, o_samp);
+  put(blob, at, mpol, o_mpol);
+  put(blob, at, mosh, o_mosh);
+  put(blob, at, comb, o_comb);
+  put(blob, at, mac, o_mac);
+  put(blob, at, it_pt, o_pt);
+  put(blob, at, it_in, o_in);
+  put(blob, at, it_out, o_out);
+  put(blob, at, it_sh, o_sh);
+  put(blob, at, it_mac, o_imac);
+  std::vector<u64> words(nl + 2, 0);  // ready[nl], step, abort flag
+  put(blob, at, words, o_words);
+  cudaFree(B->d_mem);
+  B->d_mem = nullptr;
+  B->committed = false;
+  CUDA_TRY(cudaMalloc(&B->d_mem, blob.size()));
+  CUDA_TRY(cudaMemcpy(B->d_mem, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+  char* d = reinterpret_cast<char*>(B->d_mem);
+  BatchDev& D = B->dev;
+  const int withhold = D.withhold;
+  memset(&D, 0, sizeof(D));
+  D.n_layers = nl;
+  D.encode = reinterpret_cast<const ModeEncode::Params*>(d + o_enc);
+  D.encrypt = reinterpret_cast<const ModeEncrypt::Params*>(d + o_encr);
+  D.addplain = reinterpret_cast<const ModeAddPlain::Params*>(d + o_addp);
+  D.mask = reinterpret_cast<const ModeMask::Params*>(d + o_mask);
+  D.decrypt = reinterpret_cast<const ModeDecrypt::Params*>(d + o_dec);
+  D.sample = reinterpret_cast<const SampleP*>(d + o_samp);
+  D.maskpoly = reinterpret_cast<const MaskPolyP*>(d + o_mpol);
+  D.moshare = reinterpret_cast<const MoShareP*>(d + o_mosh);
+  D.combine = reinterpret_cast<const CombineP*>(d + o_comb);
+  D.mac = reinterpret_cast<const MacParams*>(d + o_mac);
+  D.items_pt = reinterpret_cast<const int2*>(d + o_pt);
+  D.n_pt = (long long)it_pt.size();
+  D.items_in = reinterpret_cast<const int2*>(d + o_in);
+  D.n_in = (long long)it_in.size();
+  D.items_out = reinterpret_cast<const int2*>(d + o_out);
+  D.n_out = (long long)it_out.size();
+  D.items_share = reinterpret_cast<const int2*>(d + o_sh);
+  D.n_share = (long long)it_sh.size();
+  D.items_mac = reinterpret_cast<const int4*>(d + o_imac);
+  D.n_mac = (long long)it_mac.size();
+  D.ready = reinterpret_cast<u64*>(d + o_words);
+  D.step = D.ready + nl;
+  D.abort_flag = reinterpret_cast<int*>(D.ready + nl + 1);
+  D.withhold = withhold;
+  CUDA_TRY(batch_mac_blocks(ctx->dev, &D.mac_blocks));
+  B->ws = w;
+  B->mac_nt = nt;
+  B->committed = true;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_forward(PencilCtx* ctx, PencilBatch* B, void* stream) {
+  if (!ctx || !B || B->ctx != ctx) return PENCIL_E_ARG;
+  if (!B->committed || B->mac_nt != ctx->dev.mac_nt) return PENCIL_E_ARG;   // re-commit after re-tuning
+  DeviceGuard guard(ctx->device);
+  CUDA_TRY(launch_batch_forward(ctx->dev, B->dev, (cudaStream_t)stream));
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_set_step(PencilBatch* B, uint64_t step) {
+  if (!B || !B->committed) return PENCIL_E_ARG;
+  DeviceGuard guard(B->ctx->device);
+  const u64 words[2] = {step, 0};
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(B->dev.step, words, sizeof(words), cudaMemcpyHostToDevice));
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_read(const PencilBatch* B, int32_t layer, int32_t which, uint64_t* dst, void* stream) {
+  if (!B || !dst || layer < 0 || layer >= (int)B->plans.size() || !B->committed) return PENCIL_E_ARG;
+  const auto& f = B->off[layer];
+  const PencilPlan* P = B->plans[layer];
+  const long long lnb = (long long)B->ctx->dev.L * B->ctx->n * 8;
+  long long o, bytes;
+  switch (which) {
+    case PENCIL_BATCH_PT:
+      o = f.pt;
+      bytes = P->pt * lnb;
+      break;
+    case PENCIL_BATCH_CT_IN:
+      o = f.ct_in;
+      bytes = P->ct_in * 2 * lnb;
+      break;
+    case PENCIL_BATCH_CT_OUT:
+      o = f.ct_out;
+      bytes = P->ct_out * 2 * lnb;
+      break;
+    default:
+      return PENCIL_E_ARG;
+  }
+  DeviceGuard guard(B->ctx->device);
+  CUDA_TRY(cudaMemcpyAsync(dst, B->ws + o, (size_t)bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_withhold(PencilBatch* B, int32_t layer) {
+  if (!B || layer < -1 || layer >= (int)B->plans.size()) return PENCIL_E_ARG;
+  B->dev.withhold = layer;
   return PENCIL_OK;
 }

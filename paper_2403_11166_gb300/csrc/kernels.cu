@@ -3,6 +3,8 @@
 // encryption error and the re-mask (Alg. 1 step 3), the MO's output share,
 // and the RNS scale-and-round of decryption (Alg. 1 step 4).
 #include "cdt_table.h"
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace pencil {
@@ -113,13 +115,9 @@ __device__ __forceinline__ u64 acc3_value(Acc3 a, const LimbConst& lc) {
   return reduce128(hi, lo, lc);
 }
 
+// Outputs (m, n0 .. n0 + NT - 1) of one slot `lane`.
 template <int NT, bool DUAL>
-__global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
-  const int ntiles = (P.NC + NT - 1) / NT;
-  const int m = blockIdx.x / ntiles + P.m_base;
-  const int n0 = (blockIdx.x % ntiles) * NT;
-  const int lane = blockIdx.y * blockDim.x + threadIdx.x;
-  if (lane >= P.lanes || m >= P.M) return;
+__device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParams& P, int m, int n0, int lane) {
   const int nn = min(NT, P.NC - n0);
   const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
   const u64 c60 = lc.c60, c64 = lc.c64;
@@ -193,6 +191,16 @@ __global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
   }
 }
 
+template <int NT, bool DUAL>
+__global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
+  const int ntiles = (P.NC + NT - 1) / NT;
+  const int m = blockIdx.x / ntiles + P.m_base;
+  const int n0 = (blockIdx.x % ntiles) * NT;
+  const int lane = blockIdx.y * blockDim.x + threadIdx.x;
+  if (lane >= P.lanes || m >= P.M) return;
+  mac_split_tile<NT, DUAL>(ctx, P, m, n0, lane);
+}
+
 template <int NT>
 static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
   const int threads = 128;
@@ -246,6 +254,14 @@ cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaSt
 // ------------------------------------------------------------------ samplers
 // Encryption error: |e| = #{j : T[j] <= w mod 2^63}, sign = top bit of w,
 // w = Philox(key (seed, 3), counter (i/4, ct, 0, 0)) word i%4.
+__device__ __forceinline__ int8_t cdt_sample(u64 w) {
+  const u64 u = w & 0x7FFFFFFFFFFFFFFFull;
+  int mag = 0;
+#pragma unroll
+  for (int j = 0; j < PENCIL_CDT_LEN; ++j) mag += (u >= c_cdt[j]) ? 1 : 0;
+  return (int8_t)((w >> 63) ? -mag : mag);
+}
+
 __global__ void k_sample_err(u64 seed, int count, int n, int8_t* out) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int per = n >> 2;
@@ -253,21 +269,8 @@ __global__ void k_sample_err(u64 seed, int count, int n, int8_t* out) {
   const int ct = (int)(id / per);
   const int blk = (int)(id % per);
   const Philox4 w = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_E);
-  char4 r;
-  int8_t v[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const u64 u = w.v[i] & 0x7FFFFFFFFFFFFFFFull;
-    int mag = 0;
-#pragma unroll
-    for (int j = 0; j < PENCIL_CDT_LEN; ++j) mag += (u >= c_cdt[j]) ? 1 : 0;
-    v[i] = (int8_t)((w.v[i] >> 63) ? -mag : mag);
-  }
-  r.x = v[0];
-  r.y = v[1];
-  r.z = v[2];
-  r.w = v[3];
-  reinterpret_cast<char4*>(out + (size_t)ct * n)[blk] = r;
+  reinterpret_cast<char4*>(out + (size_t)ct * n)[blk] =
+      make_char4(cdt_sample(w.v[0]), cdt_sample(w.v[1]), cdt_sample(w.v[2]), cdt_sample(w.v[3]));
 }
 
 cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStream_t s) {
@@ -280,13 +283,9 @@ cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStrea
 // Mask polynomial of each output ciphertext: at coefficients carrying output
 // element `flat`, Philox(key (seed, 4), counter (flat/4, 0, 0, 0)) word flat%4;
 // elsewhere Philox(key (seed, 5), counter (i/4, ct, 0, 0)) word i%4; mod t.
-__global__ void k_mask_poly(DevCtx ctx, Packing pk, Accessor ac, u64 seed, int count, u64* out) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = ctx.n;
-  const int per = n >> 2;
-  if (id >= (long long)count * per) return;
-  const int ct = (int)(id / per);
-  const int blk = (int)(id % per);
+// Coefficients 4 blk .. 4 blk + 3 of the mask polynomial of output ciphertext ct.
+__device__ __forceinline__ void mask_poly_block(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed,
+                                                int ct, int blk, u64* out_ct) {
   const Philox4 pad = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_MASK_PAD);
   u64 r[4];
 #pragma unroll
@@ -299,9 +298,18 @@ __global__ void k_mask_poly(DevCtx ctx, Packing pk, Accessor ac, u64 seed, int c
     }
     r[i] = w & ctx.t_mask;
   }
-  ulonglong2* o = reinterpret_cast<ulonglong2*>(out + (size_t)ct * n + 4 * blk);
+  ulonglong2* o = reinterpret_cast<ulonglong2*>(out_ct + 4 * blk);
   o[0] = make_ulonglong2(r[0], r[1]);
   o[1] = make_ulonglong2(r[2], r[3]);
+}
+
+__global__ void k_mask_poly(DevCtx ctx, Packing pk, Accessor ac, u64 seed, int count, u64* out) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  const int per = n >> 2;
+  if (id >= (long long)count * per) return;
+  const int ct = (int)(id / per);
+  mask_poly_block(ctx, pk, ac, seed, ct, (int)(id % per), out + (size_t)ct * n);
 }
 
 cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed, int count, u64* out,
@@ -313,8 +321,9 @@ cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accesso
 }
 
 // MO share: y0[flat] = s[flat] (+ bias[(flat / hw) % co]) mod t.
-__global__ void k_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0) {
-  const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Elements 4 blk .. 4 blk + 3 of the MO share.
+__device__ __forceinline__ void mo_share_block(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw,
+                                               int co, u64* y0, long long blk) {
   if (blk * 4 >= count) return;
   const Philox4 w = philox4x64((u64)blk, 0ull, 0ull, 0ull, seed, PENCIL_DOM_MASK);
 #pragma unroll
@@ -326,6 +335,11 @@ __global__ void k_mo_share(u64 seed, long long count, u64 t_mask, const u64* bia
       y0[flat] = v;
     }
   }
+}
+
+__global__ void k_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0) {
+  const long long blk = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  mo_share_block(seed, count, t_mask, bias, hw, co, y0, blk);
 }
 
 cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,
@@ -342,13 +356,9 @@ cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bi
 // so round(t x / q) mod t = round(sum_j y_j th_j / 2^128) mod t with
 // th_j = floor(2^(128 + t_bits) / q_j).  The sum is kept as a 128-bit window
 // (64 integer bits, 64 fraction bits); truncation error < L * 2^-63.
-__global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int count, int check,
-                                  u64* y1) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Packing& pk, const Accessor& ac,
+                                                    const u64* yres, int ct, int e, int check, u64* y1) {
   const int n = ctx.n;
-  if (id >= (long long)count * n) return;
-  const int ct = (int)(id / n);
-  const int e = (int)(id % n);
   const i64 flat = out_index(pk, ac, ct, e);
   if (flat < 0) return;
   u64 s_lo = 0, s_hi = 0;
@@ -371,6 +381,14 @@ __global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64
   const u64 r_lo = s_lo + (1ull << 63);
   const u64 r_hi = s_hi + (r_lo < s_lo ? 1ull : 0ull);
   y1[flat] = r_hi & ctx.t_mask;
+}
+
+__global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int count, int check,
+                                  u64* y1) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  if (id >= (long long)count * n) return;
+  decrypt_combine_one(ctx, pk, ac, yres, (int)(id / n), (int)(id % n), check, y1);
 }
 
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
@@ -477,6 +495,201 @@ cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_ma
   if (Co == 0) return cudaSuccess;
   k_bias_grad<<<Co, 256, 0, s>>>(g, B, Co, hw, t_mask, out);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batched layers
+// Many linear layers (Alg. 1 forward) with a fixed launch sequence: every stage
+// of every layer runs in one multi-plan launch over (layer, polynomial) items,
+// and the ct x pt products of all layers run in ONE persistent launch over a
+// (layer, m, n-tile, lane-block) work list.  Nothing is allocated or copied at
+// run time, so the sequence can be captured in a CUDA graph; a device step
+// counter re-keys the randomness of every replay.  The persistent
+// multiply-accumulate consumes a layer's inputs only after that layer's ready
+// word carries the current step (written by a signal kernel after the input
+// stages); waits are bounded by clock64 and, on expiry, set PENCIL_E_TIMEOUT in
+// the status word and abort the remaining items instead of reading stale data.
+// ------------------------------------------------------------------ small multi-plan kernels
+__global__ void k_sample_err_multi(const SampleP* __restrict__ Ps, const int2* __restrict__ items, long long n_items,
+                                   int n, const u64* step) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = n >> 2;
+  if (id >= n_items * per) return;
+  const int2 it = items[id / per];
+  const int blk = (int)(id % per);
+  const SampleP P = Ps[it.x];
+  const u64 seed = P.seed + ((step ? *step : 0ull) << 32);
+  const Philox4 w = philox4x64((u64)blk, (u64)it.y, 0ull, 0ull, seed, PENCIL_DOM_E);
+  int8_t v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = cdt_sample(w.v[i]);
+  reinterpret_cast<char4*>(P.err + (size_t)it.y * n)[blk] = make_char4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void k_mask_poly_multi(DevCtx ctx, const MaskPolyP* __restrict__ Ps, const int2* __restrict__ items,
+                                  long long n_items, const u64* step) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  const int per = n >> 2;
+  if (id >= n_items * per) return;
+  const int2 it = items[id / per];
+  const int blk = (int)(id % per);
+  const MaskPolyP P = Ps[it.x];
+  const u64 seed = P.seed + ((step ? *step : 0ull) << 32);
+  mask_poly_block(ctx, P.pk, P.ac, seed, it.y, blk, P.out + (size_t)it.y * n);
+}
+
+__global__ void k_mo_share_multi(const MoShareP* __restrict__ Ps, const int2* __restrict__ items, long long n_items,
+                                 u64 t_mask, const u64* step) {
+  // item = (layer, chunk of 1024 elements); thread = 4 consecutive elements
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n_items * 256) return;
+  const int2 it = items[id / 256];
+  const MoShareP P = Ps[it.x];
+  const long long blk = (long long)it.y * 256 + id % 256;
+  const u64 seed = P.seed + ((step ? *step : 0ull) << 32);
+  mo_share_block(seed, P.count, t_mask, P.bias, P.hw, P.co, P.y0, blk);
+}
+
+__global__ void k_combine_multi(DevCtx ctx, const CombineP* __restrict__ Ps, const int2* __restrict__ items,
+                                long long n_items) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = ctx.n;
+  if (id >= n_items * n) return;
+  const int2 it = items[id / n];
+  const CombineP P = Ps[it.x];
+  decrypt_combine_one(ctx, P.pk, P.ac, P.yres, it.y, (int)(id % n), 1, P.y1);
+}
+
+// ready[l] = step + 1 for every layer except one the host asked to withhold
+__global__ void k_signal(u64* ready, int n_layers, int withhold, const u64* step) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n_layers && l != withhold) ready[l] = (step ? *step : 0ull) + 1;
+}
+
+__global__ void k_step_advance(u64* step) { *step += 1; }
+
+// ------------------------------------------------------------------ persistent multiply-accumulate
+#define PENCIL_GATE_LIMIT_CYCLES (4ll << 20)   // about 2 ms at 2 GHz
+
+// Waits until ready[layer] == want; thread 0 polls, the block shares the verdict.
+__device__ __forceinline__ bool wait_ready(const u64* ready, int layer, u64 want, int* status, int* abort_flag) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    const volatile u64* r = ready + layer;
+    const volatile int* ab = abort_flag;
+    int good = 1;
+    if (*r != want) {
+      const long long t0 = clock64();
+      while (*r != want) {
+        if (*ab) {
+          good = 0;
+          break;
+        }
+        if (clock64() - t0 > PENCIL_GATE_LIMIT_CYCLES) {
+          atomicOr(status, 2);
+          atomicExch(abort_flag, 1);
+          good = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    ok = good;
+  }
+  __syncthreads();
+  const int v = ok;
+  __syncthreads();
+  return v != 0;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) k_mac_persistent(DevCtx ctx, const MacParams* __restrict__ Ps,
+                                                        const int4* __restrict__ items, long long n_items,
+                                                        const u64* ready, const u64* step, int* abort_flag) {
+  const u64 want = (step ? *step : 0ull) + 1;
+  for (long long i = blockIdx.x; i < n_items; i += gridDim.x) {
+    const int4 it = items[i];   // (layer, m, n0, lane block)
+    if (!wait_ready(ready, it.x, want, ctx.status, abort_flag)) return;
+    const MacParams& P = Ps[it.x];
+    const int lane = it.w * blockDim.x + threadIdx.x;
+    if (lane < P.lanes) mac_split_tile<NT, false>(ctx, P, it.y, it.z, lane);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static unsigned blocks_for(long long threads, int per) { return (unsigned)((threads + per - 1) / per); }
+
+cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStream_t s) {
+  cudaError_t e;
+  const int n = ctx.n;
+  if (B.n_pt) {
+    e = ntt_multi<ModeEncode, false>(ctx, B.encode, B.items_pt, B.n_pt, B.step, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (B.n_in) {
+    k_sample_err_multi<<<blocks_for(B.n_in * (n / 4), 256), 256, 0, s>>>(B.sample, B.items_in, B.n_in, n, B.step);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = ntt_multi<ModeEncrypt, false>(ctx, B.encrypt, B.items_in, B.n_in, B.step, s);
+    if (e != cudaSuccess) return e;
+    e = ntt_multi<ModeAddPlain, false>(ctx, B.addplain, B.items_in, B.n_in, B.step, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_signal<<<blocks_for(B.n_layers, 128), 128, 0, s>>>(B.ready, B.n_layers, B.withhold, B.step);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (B.n_mac) {
+    const unsigned grid = (unsigned)std::min<long long>(B.n_mac, (long long)B.mac_blocks);
+    switch (ctx.mac_nt) {
+      case 2:
+        k_mac_persistent<2><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+        break;
+      case 8:
+        k_mac_persistent<8><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+        break;
+      default:
+        k_mac_persistent<4><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (B.n_out) {
+    k_mask_poly_multi<<<blocks_for(B.n_out * (n / 4), 256), 256, 0, s>>>(ctx, B.maskpoly, B.items_out, B.n_out,
+                                                                            B.step);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = ntt_multi<ModeMask, false>(ctx, B.mask, B.items_out, B.n_out, B.step, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (B.n_share) {
+    k_mo_share_multi<<<blocks_for(B.n_share * 256, 256), 256, 0, s>>>(B.moshare, B.items_share, B.n_share,
+                                                                         ctx.t_mask, B.step);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (B.n_out) {
+    e = ntt_multi<ModeDecrypt, true>(ctx, B.decrypt, B.items_out, B.n_out, B.step, s);
+    if (e != cudaSuccess) return e;
+    k_combine_multi<<<blocks_for(B.n_out * n, 256), 256, 0, s>>>(ctx, B.combine, B.items_out, B.n_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_step_advance<<<1, 1, 0, s>>>(B.step);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_mac_blocks(const DevCtx& ctx, int* blocks) {
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    switch (ctx.mac_nt) {
+      case 2:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<2>, 128, 0);
+        break;
+      case 8:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<8>, 128, 0);
+        break;
+      default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<4>, 128, 0);
+    }
+  }
+  *blocks = std::max(1, sms * std::max(1, per));
+  return e;
 }
 
 // ------------------------------------------------------------------ multiply-pipe probe

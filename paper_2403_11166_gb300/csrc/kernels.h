@@ -50,6 +50,63 @@ struct RingParams {
 cudaError_t launch_ring(const RingParams& P, cudaStream_t s);
 cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_mask, u64* out, cudaStream_t s);
 
+// ---- batched layers: per-layer parameters of the non-NTT stages
+struct SampleP {
+  u64 seed;
+  int8_t* err;        // [ct_in][N]
+};
+struct MaskPolyP {
+  Packing pk;
+  Accessor ac;
+  u64 seed;
+  u64* out;           // [ct_out][N]
+};
+struct MoShareP {
+  u64 seed;
+  long long count;
+  const u64* bias;
+  long long hw;
+  int co;
+  u64* y0;
+};
+struct CombineP {
+  Packing pk;
+  Accessor ac;
+  const u64* yres;    // [ct_out][L][N]
+  u64* y1;
+};
+// Device-resident description of one batch (all pointers are device memory).
+struct BatchDev {
+  int n_layers;
+  const ModeEncode::Params* encode;
+  const ModeEncrypt::Params* encrypt;
+  const ModeAddPlain::Params* addplain;
+  const ModeMask::Params* mask;
+  const ModeDecrypt::Params* decrypt;
+  const SampleP* sample;
+  const MaskPolyP* maskpoly;
+  const MoShareP* moshare;
+  const CombineP* combine;
+  const MacParams* mac;
+  const int2* items_pt;
+  long long n_pt;
+  const int2* items_in;
+  long long n_in;
+  const int2* items_out;
+  long long n_out;
+  const int2* items_share;
+  long long n_share;
+  const int4* items_mac;
+  long long n_mac;
+  int mac_blocks;
+  u64* ready;          // [n_layers]
+  u64* step;           // replay counter
+  int* abort_flag;
+  int withhold;        // layer whose ready word is not written (failure injection), or -1
+};
+cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStream_t s);
+cudaError_t batch_mac_blocks(const DevCtx& ctx, int* blocks);
+
 cudaError_t launch_mul_probe(int which, long long iters, int blocks, int threads, u64 seed, u64* sink,
                              cudaStream_t s);
 
@@ -58,6 +115,25 @@ PENCIL_NTT_INSTANTIATE(extern, 13)
 PENCIL_NTT_INSTANTIATE(extern, 14)
 
 // Dispatch on log2(N) and the context's radix (log2 of coefficients per thread).
+template <class Mode, bool INV>
+cudaError_t ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const int2* items, long long count,
+                      const u64* step, cudaStream_t s) {
+  const bool r4 = ctx.ntt_loge == 4;
+  switch (ctx.log_n) {
+    case 12:
+      return r4 ? launch_ntt_multi<12, 4, Mode, INV>(ctx, Ps, items, count, step, s)
+                : launch_ntt_multi<12, 5, Mode, INV>(ctx, Ps, items, count, step, s);
+    case 13:
+      return r4 ? launch_ntt_multi<13, 4, Mode, INV>(ctx, Ps, items, count, step, s)
+                : launch_ntt_multi<13, 5, Mode, INV>(ctx, Ps, items, count, step, s);
+    case 14:
+      return r4 ? launch_ntt_multi<14, 4, Mode, INV>(ctx, Ps, items, count, step, s)
+                : launch_ntt_multi<14, 5, Mode, INV>(ctx, Ps, items, count, step, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <class Mode, bool INV>
 cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
   const bool r4 = ctx.ntt_loge == 4;

@@ -143,16 +143,13 @@ struct NttCfg {
   static constexpr int MIN_BLOCKS = T >= 512 ? 1 : 2;   // 512+ threads: one CTA per SM
 };
 
-// Forward transform with a fused prologue (Mode::load, canonical coefficient
-// e) and epilogue (Mode::store2, canonical slots e and e + 1).
+// Forward transform of (poly, limb) with a fused prologue (Mode::load,
+// canonical coefficient e) and epilogue (Mode::store2, canonical slots e, e + 1).
 template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
-    k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
+__device__ __forceinline__ void ntt_fwd_run(const DevCtx& ctx, const typename Mode::Params& P, int poly, int limb,
+                                            u64* sm) {
   using C = NttCfg<LOGN, LOGE>;
-  extern __shared__ u64 sm[];
   const int tau = threadIdx.x;
-  const int poly = blockIdx.x;
-  const int limb = blockIdx.y;
   const LimbConst& lc = ctx.limb[limb];
   const u64 q = lc.q, q2 = 2 * q;
   const ulonglong2* tw = ctx.tw_fwd + (size_t)limb * C::N;
@@ -169,16 +166,13 @@ __global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN
   }
 }
 
-// Inverse transform with a fused prologue (Mode::load, value in [0, 2q)) and
-// epilogue (Mode::store, canonical coefficient e).
+// Inverse transform of (poly, limb) with a fused prologue (Mode::load, value in
+// [0, 2q)) and epilogue (Mode::store, canonical coefficient e).
 template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
-    k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
+__device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mode::Params& P, int poly, int limb,
+                                            u64* sm) {
   using C = NttCfg<LOGN, LOGE>;
-  extern __shared__ u64 sm[];
   const int tau = threadIdx.x;
-  const int poly = blockIdx.x;
-  const int limb = blockIdx.y;
   const LimbConst& lc = ctx.limb[limb];
   const u64 q = lc.q, q2 = 2 * q;
   const ulonglong2* tw = ctx.tw_inv + (size_t)limb * C::N;
@@ -197,6 +191,45 @@ __global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN
   }
 }
 
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
+  extern __shared__ u64 sm[];
+  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, blockIdx.x, blockIdx.y, sm);
+}
+
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
+  extern __shared__ u64 sm[];
+  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, blockIdx.x, blockIdx.y, sm);
+}
+
+// Multi-plan variants: CTA (blockIdx.x, limb) transforms polynomial items[x].y
+// of the plan items[x].x with that plan's parameters; `step` (device word,
+// nullable) re-keys the randomness of each replay (Mode::rebase).
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_fwd_multi(DevCtx ctx, const typename Mode::Params* __restrict__ Ps, const int2* __restrict__ items,
+                    const u64* step) {
+  extern __shared__ u64 sm[];
+  const int2 it = items[blockIdx.x];
+  typename Mode::Params P = Ps[it.x];
+  Mode::rebase(P, step ? *step : 0ull);
+  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, it.y, blockIdx.y, sm);
+}
+
+template <int LOGN, int LOGE, class Mode>
+__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+    k_ntt_inv_multi(DevCtx ctx, const typename Mode::Params* __restrict__ Ps, const int2* __restrict__ items,
+                    const u64* step) {
+  extern __shared__ u64 sm[];
+  const int2 it = items[blockIdx.x];
+  typename Mode::Params P = Ps[it.x];
+  Mode::rebase(P, step ? *step : 0ull);
+  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, it.y, blockIdx.y, sm);
+}
+
 // ------------------------------------------------------------------ fused modes
 __device__ __forceinline__ size_t limb_off(int poly, int limb, int L, int n) {
   return ((size_t)poly * L + limb) * n;
@@ -210,6 +243,7 @@ struct ModeRaw {
   struct Params {
     u64* polys;
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst&, int poly, int limb,
                                              int e) {
@@ -238,6 +272,8 @@ struct ModeEncrypt {
     u64* ct;                  // [count][2][L][N]
     u64 seed;
   };
+  // seed of replay `step` (batched graphs): seed + step * 2^32
+  static __device__ __forceinline__ void rebase(Params& P, u64 step) { P.seed += step << 32; }
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
@@ -269,6 +305,7 @@ struct ModeAddPlain {
     const u64* ct_in;   // [count][2][L][N]
     u64* out_c0;        // [count][L][N]
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
@@ -291,6 +328,7 @@ struct ModeEncode {
     Accessor ac;
     u64* pt;   // [count][L][N]
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
@@ -311,6 +349,7 @@ struct ModeMask {
     const u64* mpoly;   // [count][N] Z_t mask coefficients
     u64* ct;            // [count][2][L][N]
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
@@ -335,6 +374,7 @@ struct ModeKeygen {
     u64 seed;
     ulonglong2* sk;   // [L][N]
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int, int, int e) {
     const Philox4 w = philox4x64((u64)(e >> 2), 0ull, 0ull, 0ull, P.seed, PENCIL_DOM_SECRET);
@@ -356,6 +396,7 @@ struct ModeDecrypt {
     const ulonglong2* sk;   // [L][N]
     u64* out;               // [count][L][N]
   };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                              int limb, int e) {
@@ -392,8 +433,32 @@ cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int co
   return cudaGetLastError();
 }
 
-#define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV) \
-  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, cudaStream_t);
+template <int LOGN, int LOGE, class Mode, bool INV>
+cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const int2* items, long long count,
+                             const u64* step, cudaStream_t s) {
+  using C = NttCfg<LOGN, LOGE>;
+  if (count <= 0) return cudaSuccess;
+  if (count > 2147483647ll) return cudaErrorInvalidValue;
+  cudaError_t err;
+  dim3 grid((unsigned)count, (unsigned)ctx.L);
+  if constexpr (INV) {
+    err = cudaFuncSetAttribute(k_ntt_inv_multi<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)C::SMEM);
+    if (err != cudaSuccess) return err;
+    k_ntt_inv_multi<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
+  } else {
+    err = cudaFuncSetAttribute(k_ntt_fwd_multi<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)C::SMEM);
+    if (err != cudaSuccess) return err;
+    k_ntt_fwd_multi<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
+  }
+  return cudaGetLastError();
+}
+
+#define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV)                                                          \
+  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, cudaStream_t); \
+  SPEC template cudaError_t launch_ntt_multi<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params*, const int2*, \
+                                                                    long long, const u64*, cudaStream_t);
 #define PENCIL_NTT_INST_E(SPEC, LOGN, LOGE)                \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, false)       \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, true)        \

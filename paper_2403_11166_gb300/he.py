@@ -30,7 +30,10 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_plan_sizes", "encode_weights", "encrypt_share", "he_linear_forward",
            "he_linear_backward", "decrypt_to_share", "pencil_ntt_batch", "pencil_profile",
            "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad",
-           "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune")
+           "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune", "pencil_batch_create",
+           "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
+           "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold")
+BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
@@ -102,6 +105,15 @@ def _load():
         "pencil_bias_grad": [P, P, P, P, P],
         "encrypt_share_noalloc": [P, P, P, I32, P, U64, P, P],
         "pencil_ctx_tune": [P, I32, I32],
+        "pencil_batch_create": [P, ctypes.POINTER(P), I32, ctypes.POINTER(P)],
+        "pencil_batch_destroy": [P],
+        "pencil_batch_workspace": [P, ctypes.POINTER(I64)],
+        "pencil_batch_bind": [P, I32, P, P, P, P, P, P],
+        "pencil_batch_commit": [P, P, P, SZ, U64, U64],
+        "pencil_batch_forward": [P, P, P],
+        "pencil_batch_set_step": [P, U64],
+        "pencil_batch_read": [P, I32, I32, P, P],
+        "pencil_batch_withhold": [P, I32],
         "pencil_ctx_get_tune": [P, I32, ctypes.POINTER(I32)],
     }
     for name in EXPORTS:
@@ -325,3 +337,48 @@ def encrypt_share_noalloc(ctx: Context, sk: SecretKey, plan: Plan, operand: int,
     capture."""
     _check(lib.encrypt_share_noalloc(ctx.h, sk.h, plan.h, operand, _ptr(share), seed, _ptr(ct), _stream(stream)),
            "encrypt_share_noalloc")
+
+
+class Batch:
+    """Many FWD plans of one context as one fixed launch sequence (pencil_batch_*)."""
+
+    def __init__(self, ctx: Context, plans):
+        self.ctx = ctx
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.pencil_batch_create(ctx.h, arr, len(self.plans), ctypes.byref(h)), "pencil_batch_create")
+        self.h = h
+        b = ctypes.c_int64()
+        _check(lib.pencil_batch_workspace(h, ctypes.byref(b)), "pencil_batch_workspace")
+        self.workspace_bytes = b.value
+        self._keep = []
+
+    def bind(self, layer: int, W, x1, x0, bias, y0, y1):
+        self._keep.append((W, x1, x0, bias, y0, y1))
+        _check(lib.pencil_batch_bind(self.h, layer, _ptr(W), _ptr(x1), _ptr(x0), _ptr(bias), _ptr(y0), _ptr(y1)),
+               "pencil_batch_bind")
+
+    def commit(self, sk: SecretKey, ws: torch.Tensor, enc_seed: int, mask_seed: int):
+        self._ws = ws
+        _check(lib.pencil_batch_commit(self.h, sk.h, _ptr(ws), ctypes.c_size_t(ws.numel() * 8), enc_seed, mask_seed),
+               "pencil_batch_commit")
+
+    def forward(self, stream=None):
+        _check(lib.pencil_batch_forward(self.ctx.h, self.h, _stream(stream)), "pencil_batch_forward")
+
+    def set_step(self, step: int):
+        _check(lib.pencil_batch_set_step(self.h, step), "pencil_batch_set_step")
+
+    def read(self, layer: int, which: int, dst: torch.Tensor, stream=None):
+        _check(lib.pencil_batch_read(self.h, layer, which, _ptr(dst), _stream(stream)), "pencil_batch_read")
+
+    def withhold(self, layer: int):
+        _check(lib.pencil_batch_withhold(self.h, layer), "pencil_batch_withhold")
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.pencil_batch_destroy(self.h)
+        except Exception:
+            pass

@@ -1,0 +1,132 @@
+"""GPU: many uneven layers as one fixed launch sequence (pencil_batch_*):
+bit-identical to the per-layer C-ABI calls on two consecutive steps (fresh
+randomness per step), inside a captured CUDA graph, and a withheld input stage
+makes the persistent multiply-accumulate time out with PENCIL_E_TIMEOUT (no hang)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_11166_gb300 import inputs
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+ENC, MASK = 1000, 5000
+
+
+@pytest.fixture(scope="module")
+def he():
+    from paper_2403_11166_gb300 import he
+    return he
+
+
+def _layers(he):
+    return [he.Layer(he.FC, 16, 512, 10), he.Layer(he.CONV, 4, 64, 64, 8, 8, 3, 1),
+            he.Layer(he.CONV, 2, 128, 256, 4, 4, 1, 0), he.Layer(he.FC, 3, 100, 33),
+            he.Layer(he.CONV, 3, 5, 7, 9, 8, 3, 1)]
+
+
+def _setup(he, ctx, sk, seed=0):
+    layers = _layers(he)
+    plans = [he.Plan(ctx, L, he.ROLE_FWD, None) for L in layers]
+    batch = he.Batch(ctx, plans)
+    g = inputs.rng(seed)
+    data = []
+    for i, (L, p) in enumerate(zip(layers, plans)):
+        wshape = (L.c_out, L.c_in) if L.kind == he.FC else (L.c_out, L.c_in, L.kernel, L.kernel)
+        xshape = (L.batch, L.c_in) if L.kind == he.FC else (L.batch, L.c_in, L.height, L.width)
+        W = to_dev(inputs.gaussian_fixed(g, wshape))
+        x0, x1 = (to_dev(a) for a in inputs.split_shares(g, inputs.gaussian_fixed(g, xshape)))
+        bias = to_dev(inputs.uniform_zt(g, (L.c_out,))) if i % 2 == 0 else None
+        y0 = torch.full((p.sizes.out_elems,), -1, dtype=torch.int64, device="cuda")
+        y1 = torch.full_like(y0, -1)
+        batch.bind(i, W, x1, x0, bias, y0, y1)
+        data.append((W, x0, x1, bias, y0, y1))
+    ws = torch.empty((batch.workspace_bytes + 7) // 8, dtype=torch.int64, device="cuda")
+    batch.commit(sk, ws, ENC, MASK)
+    return layers, plans, batch, data
+
+
+def _reference(he, ctx, sk, plan, W, x0, x1, bias, enc_seed, mask_seed):
+    S = plan.sizes
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+    pt = plan.new_pt(S.pt)
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, W, pt)
+    ct_in = plan.new_ct(S.ct_in)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1, enc_seed, ct_in, ws)
+    ct_out = plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    y1 = torch.empty_like(y0)
+    he.he_linear_forward(ctx, plan, ct_in, pt, x0, bias, mask_seed, ct_out, y0, ws)
+    he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws)
+    return pt, ct_in, ct_out, y0, y1
+
+
+def _check_step(he, ctx, sk, plans, batch, data, step):
+    for i, (p, (W, x0, x1, bias, y0, y1)) in enumerate(zip(plans, data)):
+        pt, ct_in, ct_out, r0, r1 = _reference(he, ctx, sk, p, W, x0, x1, bias, ENC + i + (step << 32),
+                                               MASK + i + (step << 32))
+        got_in = torch.empty_like(ct_in)
+        got_out = torch.empty_like(ct_out)
+        got_pt = torch.empty_like(pt)
+        batch.read(i, he.BATCH_CT_IN, got_in)
+        batch.read(i, he.BATCH_CT_OUT, got_out)
+        batch.read(i, he.BATCH_PT, got_pt)
+        torch.cuda.synchronize()
+        assert torch.equal(got_pt, pt), i
+        assert torch.equal(got_in, ct_in), i
+        assert torch.equal(got_out, ct_out), i
+        assert torch.equal(y0, r0) and torch.equal(y1, r1), i
+
+
+@pytest.mark.parametrize("cols", [2, 4, 8])
+def test_batch_equals_per_layer_calls(he, cols):
+    ctx = he.Context(13, 3, 60)
+    ctx.tune(he.TUNE_MAC_COLUMNS, cols)
+    sk = ctx.keygen(3)
+    layers, plans, batch, data = _setup(he, ctx, sk)
+    for step in (0, 1):
+        batch.forward()
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        _check_step(he, ctx, sk, plans, batch, data, step)
+
+
+def test_batch_in_cuda_graph(he):
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(4)
+    layers, plans, batch, data = _setup(he, ctx, sk, seed=1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.forward(stream=s)              # warm-up outside capture (step 0)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.forward()
+    batch.set_step(5)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    _check_step(he, ctx, sk, plans, batch, data, 5)
+    graph.replay()
+    torch.cuda.synchronize()
+    _check_step(he, ctx, sk, plans, batch, data, 6)
+
+
+def test_withheld_stage_times_out(he):
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(5)
+    layers, plans, batch, data = _setup(he, ctx, sk, seed=2)
+    batch.withhold(1)
+    batch.commit(sk, batch._ws, ENC, MASK)
+    batch.forward()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == -6
+    batch.withhold(-1)
+    batch.commit(sk, batch._ws, ENC, MASK)
+    batch.set_step(0)
+    batch.forward()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    _check_step(he, ctx, sk, plans, batch, data, 0)
