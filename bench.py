@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--sweep-reps", type=int, default=3)
     ap.add_argument("--ntt-log-radix", type=int, default=0, help="force the NTT radix knob (4 or 5)")
     ap.add_argument("--mac-columns", type=int, default=0, help="force the MAC columns knob (2, 4, 8)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
+    ap.add_argument("--extras-only", action="store_true", help="run only the extra workloads (JSON line)")
     return ap.parse_args()
 
 
@@ -207,6 +209,145 @@ def ntt_sweep(he, device: int, polys: int, points: str, reps: int, log_radix: in
     return out
 
 
+# ---------------------------------------------------------------- other workloads (reported beside the headline)
+def batched_uneven(he, device: int, reps: int = 5):
+    """96 layers: 32 x FC 512->10 (B 16), 32 x conv3x3 64->64 on 8x8 (B 32, pad 1),
+    32 x conv1x1 128->256 on 4x4 (B 8); N = 8192, 3 x 60-bit primes.  Per-layer
+    launches (planner partitions, default knobs) vs one captured graph of the
+    batched sequence, untuned and autotuned."""
+    import torch
+    from paper_2403_11166_gb300 import tuner
+    layers = ([he.Layer(he.FC, 16, 512, 10)] * 32 + [he.Layer(he.CONV, 32, 64, 64, 8, 8, 3, 1)] * 32
+              + [he.Layer(he.CONV, 8, 128, 256, 4, 4, 1, 0)] * 32)
+    out = {"layers": len(layers)}
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=device)
+    sk = ctx.keygen(77)
+    # per-layer launches: 4 C-ABI calls per layer
+    plans = [he.Plan(ctx, Ly, he.ROLE_FWD, None) for Ly in layers]
+    bufs = []
+    for i, (Ly, p) in enumerate(zip(layers, plans)):
+        W, x0, x1 = tuner._layer_buffers(ctx, Ly, i)
+        S = p.sizes
+        bufs.append((W, x0, x1, p.new_pt(S.pt), p.new_ct(S.ct_in), p.new_ct(S.ct_out),
+                     torch.empty(S.out_elems, dtype=torch.int64, device=W.device),
+                     torch.empty(S.out_elems, dtype=torch.int64, device=W.device),
+                     p.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))))
+    products = sum(p.sizes.products for p in plans)
+
+    def per_layer(step):
+        for i, (p, b) in enumerate(zip(plans, bufs)):
+            W, x0, x1, pt, ct_in, ct_out, y0, y1, ws = b
+            he.encode_weights(ctx, p, he.OPERAND_KERNEL, W, pt)
+            he.encrypt_share(ctx, sk, p, he.OPERAND_INPUT, x1, 1000 + i + (step << 32), ct_in, ws)
+            he.he_linear_forward(ctx, p, ct_in, pt, x0, None, 5000 + i + (step << 32), ct_out, y0, ws)
+            he.decrypt_to_share(ctx, sk, p, ct_out, y1, False, ws)
+    per_layer(0)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for r in range(reps):
+        per_layer(r + 1)
+    b.record(stream)
+    b.synchronize()
+    ms_pl = a.elapsed_time(b) / reps
+    out["per_layer_launches"] = {"ms_per_step": ms_pl, "products_per_s": products / (ms_pl * 1e-3),
+                                 "launches_per_step": len(layers) * 10, "products_per_step": products}
+    del bufs, plans
+    torch.cuda.empty_cache()
+    gb = tuner.GraphBatch(ctx, sk, layers, [None] * len(layers))
+    ms_g = gb.time(reps)
+    out["batched_graph_untuned"] = {"ms_per_step": ms_g, "products_per_s": gb.products / (ms_g * 1e-3),
+                                    "launches_per_step": 12, "products_per_step": gb.products}
+    del gb
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    best = tuner.tune_batch(ctx, sk, layers, topk=3, reps=3)
+    tune_s = time.perf_counter() - t0
+    gb = tuner.GraphBatch(ctx, sk, layers, best["partitions"])
+    ms_t = gb.time(reps)
+    out["batched_graph_autotuned"] = {"ms_per_step": ms_t, "products_per_s": gb.products / (ms_t * 1e-3),
+                                      "products_per_step": gb.products, "ntt_log_radix": best["ntt_log_radix"],
+                                      "mac_columns": best["mac_columns"],
+                                      "partitions": sorted({str(p) for p in best["partitions"]}),
+                                      "tuning_seconds": round(tune_s, 1)}
+    del gb
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def training_step(he, device: int, reps: int = 3):
+    """Secure fwd + bwd of the 3-layer CNN (conv3x3 3->16, ReLU, conv3x3 16->32,
+    avgpool 2, FC 8192->10; batch 64, 32x32x3, N = 8192) through HeLinearFn."""
+    import torch
+    from paper_2403_11166_gb300 import autograd, inputs
+    sess = autograd.HeSession(LOG_N, L, PRIME_BITS, T_BITS, seed=3, device=device)
+    model = autograd.SecureCNN(sess, 64, inputs.cnn_params(3), 32, 32)
+    g = inputs.rng(4)
+    x = torch.as_tensor(np.floor(np.clip(g.standard_normal((64, 3, 32, 32)), -8, 8) * 4096) / 4096,
+                        device=sess.device)
+    labels = torch.as_tensor(g.integers(0, 10, 64), device=sess.device)
+
+    def step():
+        model.zero_grad(set_to_none=True)
+        loss = torch.nn.functional.cross_entropy(model(x), labels) * 4096.0
+        loss.backward()
+    step()
+    torch.cuda.synchronize()
+    sess.bytes_do_to_mo = sess.bytes_mo_to_do = 0
+    t = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        b.synchronize()
+        t.append(a.elapsed_time(b))
+    return {"ms_per_step": statistics.median(t), "batch": 64,
+            "ciphertext_MB_per_step": round((sess.bytes_do_to_mo + sess.bytes_mo_to_do) / reps / 1e6, 1)}
+
+
+def large_conv(he, device: int, reps: int = 3):
+    """conv3x3 128->128 on 16x16, batch 128: Alg. 1 forward + grad_X + Alg. 2 grad_W, N = 8192."""
+    import torch
+    from paper_2403_11166_gb300 import autograd, inputs
+    sess = autograd.HeSession(LOG_N, L, PRIME_BITS, T_BITS, seed=5, device=device)
+    Ly = he.Layer(he.CONV, 128, 128, 128, 16, 16, 3, 1)
+    g = inputs.rng(6)
+    dev = sess.device
+    W = torch.as_tensor(inputs.gaussian_fixed(g, (128, 128, 3, 3)), device=dev) & sess.mask
+    x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+              inputs.split_shares(g, inputs.gaussian_fixed(g, (128, 128, 16, 16))))
+    g0, g1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+              inputs.split_shares(g, inputs.gaussian_fixed(g, (128, 128, 16, 16))))
+
+    def fwd_bwd():
+        sess.forward(Ly, W, None, x0, x1)
+        return sess.backward(Ly, W, x0, x1, g0, g1, True)
+    fwd_bwd()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fwd_bwd()
+        b.record()
+        b.synchronize()
+        t.append(a.elapsed_time(b))
+    prods = sum(sess.plan(Ly, r).sizes.products * (2 if r == he.ROLE_WGRAD else 1)
+                for r in (he.ROLE_FWD, he.ROLE_DGRAD, he.ROLE_WGRAD))
+    ms = statistics.median(t)
+    return {"ms_fwd_bwd": ms, "products": prods, "products_per_s": prods / (ms * 1e-3),
+            "partitions": {r: sess.plan(Ly, v).part for r, v in (("fwd", he.ROLE_FWD), ("dgrad", he.ROLE_DGRAD),
+                                                                  ("wgrad", he.ROLE_WGRAD))}}
+
+
+def extras(he, device: int):
+    return {"batched_uneven": batched_uneven(he, device), "training_step_cnn": training_step(he, device),
+            "large_conv_128_fwd_bwd": large_conv(he, device)}
+
+
 # ---------------------------------------------------------------- oracle timing (host cores)
 def oracle_sample(seed: int = 0, part_tuple=(1, 2, 3, 32, 32, 3, 3), min_seconds: float = 0.0):
     """Times the oracle on one instance of every stage of the workload (repeated
@@ -307,6 +448,11 @@ def run_ours(args):
         sw = ntt_sweep(he, local, args.sweep_polys, args.sweep_points, args.sweep_reps, args.ntt_log_radix)
         if rank == 0:
             print(json.dumps({"ntt_sweep": sw}), flush=True)
+        return
+    if args.extras_only:
+        ex = extras(he, local)
+        if rank == 0:
+            print(json.dumps(ex), flush=True)
         return
     ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=local)
     if args.ntt_log_radix:
@@ -435,6 +581,8 @@ def run_ours(args):
         "e2e": {"value": products / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
     }
+    if not args.no_extras and world == 1:
+        line["workloads"] = extras(he, local)
     if not args.no_sweep:
         line["ntt_sweep"] = ntt_sweep(he, local, args.sweep_polys, args.sweep_points, args.sweep_reps,
                                       args.ntt_log_radix)

@@ -145,6 +145,11 @@ typedef struct {
 int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role,
                        const PencilPartition* part, PencilPlan** out);
 int pencil_plan_destroy(PencilPlan* plan);
+/* Up to max_count distinct partitions of `role` of `layer`, cheapest first by
+ * the planner's cost model (the first is the planner's own choice); the
+ * autotuner times them.  Host only. */
+int pencil_plan_candidates(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role, int32_t max_count,
+                           PencilPartition* out, int32_t* count);
 int pencil_plan_sizes(const PencilPlan* plan, PencilPlanSizes* sizes);
 
 /* ---------------------------------------------------------------- hot path */

@@ -553,9 +553,9 @@ static double plan_cost(const Geom& g, const PencilPartition& p, int role, int n
   return ntts * ntt_u + prods * 2 * ln * 8 + bytes * 3;
 }
 
-static PencilPartition choose_partition(const Geom& g, int role, int n, int log_n, int L) {
-  PencilPartition best{1, 1, 1, 1, 1, 1, 1};
-  double best_cost = 1e300;
+// Every valid partition of the candidate grid with its modelled cost.
+static void enumerate_partitions(const Geom& g, int role, int n, int log_n, int L,
+                                 std::vector<std::pair<double, PencilPartition>>& out) {
   const std::vector<int> ths = ceil_divs(g.Ho()), tws = ceil_divs(g.Wo());
   const std::vector<int> khs = ceil_divs(g.KH), kws = ceil_divs(g.KW);
   const std::vector<int> cis = ceil_divs(g.Ci), cos_ = ceil_divs(g.Co), bs = ceil_divs(g.B);
@@ -580,14 +580,22 @@ static PencilPartition choose_partition(const Geom& g, int role, int n, int log_
                 }
               PencilPartition p{bb, ci, co, th, tw, kth, ktw};
               if (!part_valid(g, p, n)) continue;
-              const double cost = plan_cost(g, p, role, n, log_n, L);
-              if (cost < best_cost) {
-                best_cost = cost;
-                best = p;
-              }
+              out.push_back({plan_cost(g, p, role, n, log_n, L), p});
             }
           }
         }
+}
+
+static PencilPartition choose_partition(const Geom& g, int role, int n, int log_n, int L) {
+  std::vector<std::pair<double, PencilPartition>> all;
+  enumerate_partitions(g, role, n, log_n, L, all);
+  PencilPartition best{1, 1, 1, 1, 1, 1, 1};
+  double best_cost = 1e300;
+  for (const auto& c : all)
+    if (c.first < best_cost) {
+      best_cost = c.first;
+      best = c.second;
+    }
   return best;
 }
 
@@ -712,6 +720,45 @@ extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, 
     P->ws_backward = P->ws_forward;
   P->ws_decrypt = al(P->ct_out * lnb);
   *out = P;
+  return PENCIL_OK;
+}
+
+static int validate_layer(const PencilLayerDesc& L) {
+  if (L.kind != PENCIL_FC && L.kind != PENCIL_CONV) return PENCIL_E_ARG;
+  if (L.batch < 1 || L.c_in < 1 || L.c_out < 1) return PENCIL_E_SHAPE;
+  if (L.kind == PENCIL_FC && (L.height != 1 || L.width != 1 || L.kernel != 1 || L.pad != 0)) return PENCIL_E_SHAPE;
+  if (L.kind == PENCIL_CONV) {
+    if (L.height < 1 || L.width < 1 || L.kernel < 1 || L.pad < 0 || L.pad > L.kernel - 1) return PENCIL_E_SHAPE;
+    if (L.height + 2 * L.pad < L.kernel || L.width + 2 * L.pad < L.kernel) return PENCIL_E_SHAPE;
+  }
+  if (L.batch > 65535 || L.c_in > 65535 || L.c_out > 65535 || L.height + 2 * L.pad > 65535 ||
+      L.width + 2 * L.pad > 65535)
+    return PENCIL_E_SHAPE;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_plan_candidates(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role, int32_t max_count,
+                                      PencilPartition* out, int32_t* count) {
+  if (!ctx || !layer || !count || max_count < 0 || (max_count > 0 && !out)) return PENCIL_E_ARG;
+  if (role < PENCIL_ROLE_FWD || role > PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  const int rc = validate_layer(*layer);
+  if (rc != PENCIL_OK) return rc;
+  PencilPlan tmp;
+  role_setup(*layer, role, tmp);
+  std::vector<std::pair<double, PencilPartition>> all;
+  enumerate_partitions(tmp.g, role, ctx->n, ctx->params.log_n, ctx->dev.L, all);
+  std::stable_sort(all.begin(), all.end(),
+                   [](const std::pair<double, PencilPartition>& a, const std::pair<double, PencilPartition>& b) {
+                     return a.first < b.first;
+                   });
+  int k = 0;
+  for (size_t i = 0; i < all.size() && k < max_count; ++i) {
+    bool dup = false;
+    for (int j = 0; j < k; ++j)
+      if (memcmp(&out[j], &all[i].second, sizeof(PencilPartition)) == 0) dup = true;
+    if (!dup) out[k++] = all[i].second;
+  }
+  *count = k;
   return PENCIL_OK;
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_profile_read", "pencil_mul_probe", "pencil_ring_linear", "pencil_bias_grad",
            "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune", "pencil_batch_create",
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
-           "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold")
+           "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
+           "pencil_plan_candidates")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
@@ -114,6 +115,8 @@ def _load():
         "pencil_batch_set_step": [P, U64],
         "pencil_batch_read": [P, I32, I32, P, P],
         "pencil_batch_withhold": [P, I32],
+        "pencil_plan_candidates": [P, ctypes.POINTER(LayerDesc), I32, I32, ctypes.POINTER(Partition),
+                                   ctypes.POINTER(I32)],
         "pencil_ctx_get_tune": [P, I32, ctypes.POINTER(I32)],
     }
     for name in EXPORTS:
@@ -382,3 +385,13 @@ class Batch:
                 lib.pencil_batch_destroy(self.h)
         except Exception:
             pass
+
+
+def plan_candidates(ctx: Context, layer: Layer, role: int, max_count: int = 8):
+    """Cheapest-first partitions of the planner's cost model (tuples)."""
+    out = (Partition * max_count)()
+    n = ctypes.c_int32()
+    d = layer.desc()
+    _check(lib.pencil_plan_candidates(ctx.h, ctypes.byref(d), role, max_count, out, ctypes.byref(n)),
+           "pencil_plan_candidates")
+    return [out[i].astuple() for i in range(n.value)]

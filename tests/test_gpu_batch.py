@@ -130,3 +130,23 @@ def test_withheld_stage_times_out(he):
     torch.cuda.synchronize()
     assert ctx.sync_status() == 0
     _check_step(he, ctx, sk, plans, batch, data, 0)
+
+
+def test_autotuner_choice_keeps_results(he):
+    """The tuner picks knobs and partitions by timing; outputs stay bit-identical
+    to the per-layer calls with the chosen partitions."""
+    from paper_2403_11166_gb300 import tuner
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(6)
+    layers = [he.Layer(he.FC, 8, 96, 12), he.Layer(he.CONV, 2, 8, 6, 6, 6, 3, 1)]
+    best = tuner.tune_batch(ctx, sk, layers, topk=2, reps=1, radices=(4, 5), columns=(2, 8))
+    assert best["ntt_log_radix"] in (4, 5) and best["mac_columns"] in (2, 8)
+    assert ctx.get_tune(he.TUNE_MAC_COLUMNS) == best["mac_columns"]
+    gb = tuner.GraphBatch(ctx, sk, layers, best["partitions"], capture=False)
+    gb.batch.set_step(0)
+    gb.run()
+    torch.cuda.synchronize()
+    for i, (p, (W, x0, x1, y0, y1)) in enumerate(zip(gb.plans, gb.bufs)):
+        assert p.part == tuple(best["partitions"][i])
+        r = _reference(he, ctx, sk, p, W, x0, x1, None, 1000 + i, 5000 + i)
+        assert torch.equal(y0, r[3]) and torch.equal(y1, r[4])
