@@ -403,6 +403,32 @@ def oracle_sample(seed: int = 0, part_tuple=(1, 2, 3, 32, 32, 3, 3), min_seconds
     return c.products / step, step, desc, time.perf_counter() - t_all
 
 
+def cpu_ntt_baseline(seconds: float = 6.0):
+    """The plain CPU NTT build (C, OpenMP) on this host: limb-NTTs/s at 1 thread and
+    at all threads, forward, 60-bit primes, N in {4096, 8192, 16384}."""
+    from oracle import cpu_ntt
+    from oracle.params import min_primitive_root_2n, ntt_primes
+    cores = cpu_ntt.max_threads()
+    out = {"cores": cores}
+    budget = seconds / 6
+    for log_n in (12, 13, 14):
+        n = 1 << log_n
+        q = ntt_primes(60, 1, 2 * n)[0]
+        eng = cpu_ntt.CpuNtt(q, min_primitive_root_2n(q, 2 * n), log_n)
+        res = {}
+        for label, threads in (("threads_1", 1), ("threads_all", cores)):
+            count = 8 * threads
+            a = np.random.default_rng(log_n).integers(0, q, size=(count, n), dtype=np.uint64)
+            eng.run(a, threads=threads)
+            done, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < budget:
+                eng.run(a, threads=threads)
+                done += count
+            res[label] = done / (time.perf_counter() - t0)
+        out[f"N{n}"] = res
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -486,11 +512,20 @@ def run_ours(args):
     hy0 = torch.empty(S.out_elems, dtype=torch.int64).pin_memory()
     hy1 = torch.empty_like(hy0).pin_memory()
 
+    # The MO encodes its weights while the DO encrypts its share (independent
+    # parties): two streams forked and joined inside every step.
+    mo_stream = torch.cuda.Stream(device=dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+
     def step(i):
-        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt)
-        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 1000 + i, ct_in, ws)
-        he.he_linear_forward(ctx, plan, ct_in, pt, d["x0"], d["bias"], 5000 + i, ct_out, y0, ws)
-        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws)
+        fork.record(stream)
+        mo_stream.wait_event(fork)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt, stream=mo_stream)
+        join.record(mo_stream)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 1000 + i, ct_in, ws, stream=stream)
+        stream.wait_event(join)
+        he.he_linear_forward(ctx, plan, ct_in, pt, d["x0"], d["bias"], 5000 + i, ct_out, y0, ws, stream=stream)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws, stream=stream)
 
     for i in range(args.warmup):
         step(i)
@@ -589,7 +624,8 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         v, st, desc, spent = oracle_sample(part_tuple=plan.part, min_seconds=12.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                "seconds": round(spent, 1), "host_cores_available": len(os.sched_getaffinity(0))}
+                                "seconds": round(spent, 1), "host_cores_available": len(os.sched_getaffinity(0)),
+                                "plain_cpu_ntt_limb_ntts_per_s": cpu_ntt_baseline()}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
