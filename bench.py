@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--sweep-points", default="12x2,12x3,12x4,13x2,13x3,13x4,14x2,14x3,14x4")
     ap.add_argument("--sweep-reps", type=int, default=3)
     ap.add_argument("--ntt-log-radix", type=int, default=0, help="force the NTT radix knob (4 or 5)")
-    ap.add_argument("--mac-columns", type=int, default=0, help="force the MAC columns knob (2, 4, 8)")
+    ap.add_argument("--mac-columns", type=int, default=-1,
+                    help="force the MAC knob (0: shared-memory staged; 2, 4, 8: columns per thread)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
     ap.add_argument("--extras-only", action="store_true", help="run only the extra workloads (JSON line)")
     return ap.parse_args()
@@ -483,7 +484,7 @@ def run_ours(args):
     ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=local)
     if args.ntt_log_radix:
         ctx.tune(he.TUNE_NTT_LOG_RADIX, args.ntt_log_radix)
-    if args.mac_columns:
+    if args.mac_columns >= 0:
         ctx.tune(he.TUNE_MAC_COLUMNS, args.mac_columns)
     sk = ctx.keygen(1234 + rank)
     layer = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],

@@ -76,7 +76,9 @@ int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
  * PENCIL_TUNE_NTT_LOG_RADIX: log2 of the coefficients each thread holds in the
  * NTT kernels, i.e. the radix of one shared-memory round: 4 or 5.
  * PENCIL_TUNE_MAC_COLUMNS: output ciphertexts per thread of the ct x pt
- * multiply-accumulate: 2, 4 or 8. */
+ * multiply-accumulate reading operands straight from L2: 2, 4 or 8; or 0: the
+ * shared-memory staged kernel (each CTA stages one input block of 32 slots for
+ * a 64-pair output block; each operand word read once per CTA). */
 enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1 };
 int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value);
 int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value);

@@ -371,7 +371,7 @@ extern "C" int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value) {
     return PENCIL_OK;
   }
   if (knob == PENCIL_TUNE_MAC_COLUMNS) {
-    if (value != 2 && value != 4 && value != 8) return PENCIL_E_ARG;
+    if (value != 0 && value != 2 && value != 4 && value != 8) return PENCIL_E_ARG;
     ctx->dev.mac_nt = value;
     return PENCIL_OK;
   }
@@ -1301,7 +1301,8 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   const long long lnw = (long long)L * n;
   char* w = reinterpret_cast<char*>(ws);
   const int nl = (int)B->plans.size();
-  const int nt = ctx->dev.mac_nt;
+  // the persistent multiply-accumulate tiles 2, 4 or 8 output columns per thread
+  const int nt = ctx->dev.mac_nt == 0 ? 4 : ctx->dev.mac_nt;
   std::vector<ModeEncode::Params> enc(nl);
   std::vector<ModeEncrypt::Params> encr(nl);
   std::vector<ModeAddPlain::Params> addp(nl);
@@ -1426,9 +1427,10 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   D.step = D.ready + nl;
   D.abort_flag = reinterpret_cast<int*>(D.ready + nl + 1);
   D.withhold = withhold;
-  CUDA_TRY(batch_mac_blocks(ctx->dev, &D.mac_blocks));
+  D.mac_nt = nt;
+  CUDA_TRY(batch_mac_blocks(ctx->dev, nt, &D.mac_blocks));
   B->ws = w;
-  B->mac_nt = nt;
+  B->mac_nt = ctx->dev.mac_nt;
   B->committed = true;
   return PENCIL_OK;
 }

@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx ctx, MacParams P) {
 // Operands a = aH 2^30 + aL, b = bH 2^30 + bL; each partial product is one
 // 32x32->64 multiply-add into one of three 64-bit accumulators of weight 1,
 // 2^30, 2^60:  S0 += aL bL,  S1 += aH bL + aL bH,  S2 += aH bH.
-// Every FOLD k-steps (products per accumulator <= 8, so all stay < 2^64) the
-// accumulators are folded mod q using 2^60 = c60 and 2^64 = c64:
+// Every FOLD k-steps (at most 12 products per accumulator, so all stay below
+// 15 * 2^60 even inside the fold) the accumulators are folded mod q using
+// 2^60 = c60 and 2^64 = c64:
 //   S0 += lo32(S2) c60;  S1 += hi32(S2) 4 c60;  S2 = 0;
 //   S0 += (S1 >> 34) c64;  S1 &= 2^34 - 1;  S1 += S0 >> 30;  S0 &= 2^30 - 1,
 // after which S0 < 2^30 and S1 < 2^35.  Thread = one slot, NT output columns.
@@ -127,7 +128,7 @@ __device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParam
   for (int j = 0; j < NT; ++j)
 #pragma unroll
     for (int c = 0; c < 2; ++c) acc[j][c] = Acc3{0, 0, 0};
-  constexpr int FOLD = DUAL ? 2 : 4;
+  constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
   // operands of step k, loaded one step ahead
   u64 a0, a1, pa = 0, b[NT], c0[NT], c1[NT];
   auto load = [&](int k) {
@@ -201,6 +202,177 @@ __global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
   mac_split_tile<NT, DUAL>(ctx, P, m, n0, lane);
 }
 
+// ------------------------------------------------------------------ MAC, shared-memory staged
+// CTA = 32 slots x 8 warps.  The CTA owns an output block of MB x NB (m, n)
+// pairs (MB * NB = 64) for its 32 slots; warp w owns pairs 8w .. 8w + 7
+// (m = p / NB, n = p % NB).  For every input block k the CTA stages A[m, k]
+// (both components), B[k, n] (and, for Alg. 2, A'[m, k], B'[k, n]) of its 32
+// slots in shared memory with asynchronous 16-byte copies (cp.async, zero-fill
+// outside the layer) into a ring of MAC_STAGES buffers, so the next blocks are
+// in flight while block k is multiplied; each operand word is read from L2 / HBM
+// once per CTA.
+// Every thread multiplies its 8 pairs with the 30-bit split accumulators.
+#define MAC_LANES 32
+#define MAC_PAIRS 8
+#define MAC_STAGES 4
+
+__device__ __forceinline__ void cp_async16(u64* smem, const u64* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Global address of row `row` of stage k (or nullptr when outside the layer).
+// Rows: [0, 2MB) A components; [2MB, 2MB + NB) B; Alg. 2: [.., + MB) A', [.., + 2NB) B' components.
+template <bool DUAL>
+__device__ __forceinline__ const u64* mac_row(const MacParams& P, int MB, int NB, int m0, int n0, int k, int row) {
+  if (row < 2 * MB) {
+    const int m = m0 + (row >> 1);
+    if (m >= P.M) return nullptr;
+    const size_t mk = (size_t)m * P.K + k;
+    return (row & 1) ? P.a1 + mk * P.a1_stride : P.a0 + mk * P.a0_stride;
+  }
+  row -= 2 * MB;
+  if (row < NB) {
+    const int n = n0 + row;
+    return n < P.NC ? P.b + ((size_t)k * P.NC + n) * P.b_stride : nullptr;
+  }
+  row -= NB;
+  if (row < MB) {
+    const int m = m0 + row;
+    return m < P.M ? P.pa + ((size_t)m * P.K + k) * P.pa_stride : nullptr;
+  }
+  row -= MB;
+  const int n = n0 + (row >> 1);
+  if (n >= P.NC) return nullptr;
+  const size_t kn = (size_t)k * P.NC + n;
+  return ((row & 1) ? P.cb1 : P.cb0) + kn * P.cb_stride;
+}
+
+template <bool DUAL>
+__device__ __forceinline__ void mac_issue(const MacParams& P, int MB, int NB, int m0, int n0, int k, int lane0, int W,
+                                          u64* buf) {
+  // W rows x 16 chunks of 16 bytes (two slots each)
+  for (int idx = threadIdx.x; idx < W * 16; idx += blockDim.x) {
+    const int row = idx >> 4, chunk = idx & 15;
+    const u64* g = mac_row<DUAL>(P, MB, NB, m0, n0, k, row);
+    cp_async16(buf + row * MAC_LANES + 2 * chunk, g ? g + lane0 + 2 * chunk : P.b, g ? 16 : 0);
+  }
+}
+
+template <bool DUAL>
+__global__ void __launch_bounds__(256, 2) k_mac_smem(DevCtx ctx, MacParams P, int MB, int lnb, int mblocks) {
+  const int NB = 1 << lnb;
+  extern __shared__ u64 st[];                       // [MAC_STAGES][W][MAC_LANES]
+  const int lane0 = blockIdx.x * MAC_LANES;
+  const int mb = blockIdx.y % mblocks, nb = blockIdx.y / mblocks;
+  const int m0 = mb * MB + P.m_base, n0 = nb * NB;
+  const int tid = threadIdx.x, col = tid & (MAC_LANES - 1), warp = tid >> 5;
+  const int lane = lane0 + col;
+  const int W = DUAL ? 3 * (MB + NB) : 2 * MB + NB;
+  constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
+  constexpr u32 M30 = (1u << 30) - 1;
+  const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
+  Acc3 acc[MAC_PAIRS][2];
+#pragma unroll
+  for (int i = 0; i < MAC_PAIRS; ++i) acc[i][0] = acc[i][1] = Acc3{0, 0, 0};
+  // ring of MAC_STAGES buffers: blocks k + 1 .. k + MAC_STAGES - 1 in flight while k is multiplied
+#pragma unroll
+  for (int s = 0; s < MAC_STAGES - 1; ++s) {
+    if (s < P.K) mac_issue<DUAL>(P, MB, NB, m0, n0, s, lane0, W, st + (size_t)s * W * MAC_LANES);
+    cp_async_commit();
+  }
+  for (int k = 0; k < P.K; ++k) {
+    const u64* cur = st + (size_t)(k % MAC_STAGES) * W * MAC_LANES;
+    const int nk = k + MAC_STAGES - 1;
+    if (nk < P.K) mac_issue<DUAL>(P, MB, NB, m0, n0, nk, lane0, W, st + (size_t)(nk % MAC_STAGES) * W * MAC_LANES);
+    cp_async_commit();
+    cp_async_wait<MAC_STAGES - 1>();
+    __syncthreads();
+    {  // split every staged word once: (low 30 bits) | (high 30 bits) << 32
+      u64* w = st + (size_t)(k % MAC_STAGES) * W * MAC_LANES;
+      for (int idx = tid; idx < W * MAC_LANES; idx += blockDim.x) {
+        const u64 x = w[idx];
+        w[idx] = (x & M30) | ((x >> 30) << 32);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MAC_PAIRS; ++i) {
+      const int p = warp * MAC_PAIRS + i;
+      const int mr = p >> lnb, nr = p & (NB - 1);
+      const u64 a0 = cur[(2 * mr) * MAC_LANES + col], a1 = cur[(2 * mr + 1) * MAC_LANES + col];
+      const u64 b = cur[(2 * MB + nr) * MAC_LANES + col];
+      const u32 bL = (u32)b, bH = (u32)(b >> 32);
+      mac_split(acc[i][0], (u32)a0, (u32)(a0 >> 32), bL, bH);
+      mac_split(acc[i][1], (u32)a1, (u32)(a1 >> 32), bL, bH);
+      if constexpr (DUAL) {
+        const u64 pa = cur[(2 * MB + NB + mr) * MAC_LANES + col];
+        const u64 c0 = cur[(3 * MB + NB + 2 * nr) * MAC_LANES + col];
+        const u64 c1 = cur[(3 * MB + NB + 2 * nr + 1) * MAC_LANES + col];
+        const u32 pL = (u32)pa, pH = (u32)(pa >> 32);
+        mac_split(acc[i][0], (u32)c0, (u32)(c0 >> 32), pL, pH);
+        mac_split(acc[i][1], (u32)c1, (u32)(c1 >> 32), pL, pH);
+      }
+    }
+    if ((k % FOLD) == FOLD - 1) {
+#pragma unroll
+      for (int i = 0; i < MAC_PAIRS; ++i) {
+        fold3(acc[i][0], lc.c60, lc.c64);
+        fold3(acc[i][1], lc.c60, lc.c64);
+      }
+    }
+    __syncthreads();   // this buffer is refilled by the next iteration's issue
+  }
+  const size_t ln = (size_t)P.lanes;
+#pragma unroll
+  for (int i = 0; i < MAC_PAIRS; ++i) {
+    const int p = warp * MAC_PAIRS + i;
+    const int m = m0 + (p >> lnb), n = n0 + (p & (NB - 1));
+    if (m < P.M && n < P.NC) {
+      const size_t o = ((size_t)m * P.NC + n) * 2 * ln + lane;
+      P.out[o] = acc3_value(acc[i][0], lc);
+      P.out[o + ln] = acc3_value(acc[i][1], lc);
+    }
+  }
+}
+
+static cudaError_t launch_mac_smem(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  // output block: NB = min(64, next power of two >= NC), MB = 64 / NB
+  int NB = 1, lnb = 0;
+  while (NB < P0.NC && NB < 64) {
+    NB <<= 1;
+    ++lnb;
+  }
+  const int MB = 64 / NB;
+  const int words = dual ? 3 * (MB + NB) : 2 * MB + NB;
+  const size_t smem = (size_t)MAC_STAGES * words * MAC_LANES * sizeof(u64);
+  cudaError_t e = dual ? cudaFuncSetAttribute(k_mac_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(k_mac_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nblocks = (P0.NC + NB - 1) / NB;
+  MacParams P = P0;
+  const unsigned gx = (unsigned)((P.lanes + MAC_LANES - 1) / MAC_LANES);
+  const int mchunk_blocks = std::max(1, 65535 / nblocks);
+  const int mblocks_total = (P0.M + MB - 1) / MB;
+  for (int mbase = 0; mbase < mblocks_total; mbase += mchunk_blocks) {
+    const int mblocks = std::min(mchunk_blocks, mblocks_total - mbase);
+    P.m_base = mbase * MB;
+    dim3 grid(gx, (unsigned)(mblocks * nblocks));
+    if (dual)
+      k_mac_smem<true><<<grid, 256, smem, s>>>(ctx, P, MB, lnb, mblocks);
+    else
+      k_mac_smem<false><<<grid, 256, smem, s>>>(ctx, P, MB, lnb, mblocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <int NT>
 static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
   const int threads = 128;
@@ -223,6 +395,7 @@ static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool
 }
 
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  if (ctx.mac_split && ctx.mac_nt == 0) return launch_mac_smem(ctx, P0, dual, s);
   if (ctx.mac_split) {
     switch (ctx.mac_nt) {
       case 2:
@@ -638,7 +811,7 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (B.n_mac) {
     const unsigned grid = (unsigned)std::min<long long>(B.n_mac, (long long)B.mac_blocks);
-    switch (ctx.mac_nt) {
+    switch (B.mac_nt) {
       case 2:
         k_mac_persistent<2><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
         break;
@@ -672,12 +845,13 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t batch_mac_blocks(const DevCtx& ctx, int* blocks) {
+cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int* blocks) {
+  (void)ctx;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    switch (ctx.mac_nt) {
+    switch (nt) {
       case 2:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<2>, 128, 0);
         break;

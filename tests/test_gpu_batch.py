@@ -78,7 +78,7 @@ def _check_step(he, ctx, sk, plans, batch, data, step):
         assert torch.equal(y0, r0) and torch.equal(y1, r1), i
 
 
-@pytest.mark.parametrize("cols", [2, 4, 8])
+@pytest.mark.parametrize("cols", [0, 2, 4, 8])
 def test_batch_equals_per_layer_calls(he, cols):
     ctx = he.Context(13, 3, 60)
     ctx.tune(he.TUNE_MAC_COLUMNS, cols)
