@@ -66,6 +66,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(vals, world: int, device="cpu"):
+    """Element-wise maximum of `vals` over all ranks (the job's time is the
+    slowest rank's); identity for one process."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_rank_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job rate: the units every rank processed over the max-over-ranks time."""
+    return units_per_rank_step * steps * world / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -583,13 +600,8 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
-
-    products = S.products * args.steps * world
-    value = products / (ms * 1e-3)
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], world, dev)
+    value = job_throughput(S.products, args.steps, world, ms)
     peaks = load_peaks()
     dom, table, roof = roofline(prof, S, ctx.n, ctx.L, args.steps, peaks, ck)
     roof["probe"] = {"imad32_T_per_s": round(probe["imad32"], 3), "shoup64_T_per_s": round(probe["shoup64"], 3),
@@ -614,7 +626,7 @@ def run_ours(args):
         "kernels": table,
         "clocks": ck,
         "gpu_launches": launches,
-        "e2e": {"value": products / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(S.products, args.steps, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
     }
     if not args.no_extras and world == 1:

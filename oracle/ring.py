@@ -118,3 +118,49 @@ def ring_matmul_dgrad(w, gy, t_bits: int):
 def ring_matmul_wgrad(gy, x, t_bits: int):
     """gW[o, i] = sum_b gy[b, o] x[b, i]."""
     return ring_matmul(np.ascontiguousarray(_u64(x).T), np.ascontiguousarray(_u64(gy).T), t_bits)
+
+
+# ---------------------------------------------------------------------------
+# The same operators evaluated at chosen output elements only (for checks at
+# sizes where the full operator is too slow): each element is its defining sum.
+def ring_conv2d_at(w, x, pad: int, t_bits: int, idx):
+    """y[b, o, i, j] of `ring_conv2d` for each (b, o, i, j) in idx."""
+    w = _u64(w)
+    xp = _pad(_u64(x), pad)
+    s = w.shape[2]
+    out = []
+    with np.errstate(over="ignore"):
+        for b, o, i, j in idx:
+            out.append(int((w[o] * xp[b, :, i:i + s, j:j + s]).sum(dtype=np.uint64)) & ((1 << t_bits) - 1))
+    return out
+
+
+def ring_conv2d_dgrad_at(w, gy, pad: int, t_bits: int, idx):
+    """gx[b, c, i, j] of `ring_conv2d_dgrad` for each (b, c, i, j) in idx."""
+    w = _u64(w)
+    gy = _u64(gy)
+    co, ci, s, _ = w.shape
+    ho, wo = gy.shape[2], gy.shape[3]
+    out = []
+    with np.errstate(over="ignore"):
+        for b, c, i, j in idx:
+            acc = np.uint64(0)
+            for u in range(s):
+                for v in range(s):
+                    r, q = i + pad - u, j + pad - v
+                    if 0 <= r < ho and 0 <= q < wo:
+                        acc += (gy[b, :, r, q] * w[:, c, u, v]).sum(dtype=np.uint64)
+            out.append(int(acc) & ((1 << t_bits) - 1))
+    return out
+
+
+def ring_conv2d_wgrad_at(gy, x, pad: int, s: int, t_bits: int, idx):
+    """gW[o, c, u, v] of `ring_conv2d_wgrad` for each (o, c, u, v) in idx."""
+    gy = _u64(gy)
+    xp = _pad(_u64(x), pad)
+    ho, wo = gy.shape[2], gy.shape[3]
+    out = []
+    with np.errstate(over="ignore"):
+        for o, c, u, v in idx:
+            out.append(int((gy[:, o] * xp[:, c, u:u + ho, v:v + wo]).sum(dtype=np.uint64)) & ((1 << t_bits) - 1))
+    return out

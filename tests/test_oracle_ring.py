@@ -59,3 +59,19 @@ def test_float_equivalence_small_values():
     assert (signed(ring.ring_matmul(wf, xf, T)) == yt.detach().numpy()).all()
     assert (signed(ring.ring_matmul_dgrad(wf, gyf, T)) == xt.grad.numpy()).all()
     assert (signed(ring.ring_matmul_wgrad(gyf, xf, T)) == wt.grad.numpy()).all()
+
+
+def test_sampled_operators_match_full():
+    g = np.random.default_rng(3)
+    x = g.integers(0, 1 << T, size=(3, 4, 7, 6), dtype=np.uint64)
+    w = g.integers(0, 1 << T, size=(5, 4, 3, 3), dtype=np.uint64)
+    gy = g.integers(0, 1 << T, size=(3, 5, 7, 6), dtype=np.uint64)
+    full_y = ring.ring_conv2d(w, x, 1, T)
+    full_gx = ring.ring_conv2d_dgrad(w, gy, 1, T)
+    full_gw = ring.ring_conv2d_wgrad(gy, x, 1, 3, T)
+    idx = [(0, 0, 0, 0), (2, 4, 6, 5), (1, 2, 3, 0), (0, 3, 6, 2)]
+    assert ring.ring_conv2d_at(w, x, 1, T, idx) == [int(full_y[i]) for i in idx]
+    idx_x = [(0, 0, 0, 0), (2, 3, 6, 5), (1, 1, 3, 4)]
+    assert ring.ring_conv2d_dgrad_at(w, gy, 1, T, idx_x) == [int(full_gx[i]) for i in idx_x]
+    idx_w = [(0, 0, 0, 0), (4, 3, 2, 2), (2, 1, 0, 2)]
+    assert ring.ring_conv2d_wgrad_at(gy, x, 1, 3, T, idx_w) == [int(full_gw[i]) for i in idx_w]
