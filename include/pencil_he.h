@@ -74,7 +74,8 @@ int pencil_ctx_destroy(PencilCtx* ctx);
 int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
 /* Tuning knobs of a context (chosen by the autotuner; results never depend on them).
  * PENCIL_TUNE_NTT_LOG_RADIX: log2 of the coefficients each thread holds in the
- * NTT kernels, i.e. the radix of one shared-memory round: 4 or 5.
+ * NTT kernels, i.e. the radix of one shared-memory round: 4 or 5 (default 4
+ * up to N = 8192, where two transforms share an SM; 5 above).
  * PENCIL_TUNE_MAC_COLUMNS: output ciphertexts per thread of the ct x pt
  * multiply-accumulate reading operands straight from L2: 2, 4 or 8; or 0: the
  * shared-memory staged kernel (each CTA stages one input block of 32 slots for

@@ -278,7 +278,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   DevCtx& d = ctx->dev;
   memset(&d, 0, sizeof(d));
   d.log_n = p.log_n;
-  d.ntt_loge = p.log_n <= 12 ? 4 : 5;
+  d.ntt_loge = p.log_n <= 13 ? 4 : 5;   // measured: radix 2^4 (two CTAs per SM) up to N = 8192
   d.n = n;
   d.L = p.num_primes;
   d.t_bits = p.t_bits;
@@ -314,6 +314,8 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     lc.th_lo = (u64)th;
     lc.c60 = (u64)((((u128)1) << 60) % q);
     lc.c64 = (u64)((((u128)1) << 64) % q);
+    lc.nqtil = mulmod(lc.ninv, lc.qtil, q);
+    lc.nqtils = shoup(lc.nqtil, q);
   }
   d.mac_nt = 4;
   d.mac_split = 1;

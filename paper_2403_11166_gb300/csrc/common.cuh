@@ -22,6 +22,7 @@ struct LimbConst {
   u64 qtil, qtils;   // (q_total / q_j)^{-1} mod q_j              (CRT)
   u64 th_hi, th_lo;  // floor(2^(128 + t_bits) / q_j), 128 bits   (t / q_j in 0.128 fixed point)
   u64 c60, c64;      // 2^60 mod q and 2^64 mod q                 (split multiply-accumulate folds)
+  u64 nqtil, nqtils; // N^{-1} qtil mod q_j                       (INTT scaling folded into the CRT factor)
 };
 
 struct DevCtx {
@@ -82,10 +83,9 @@ __device__ __forceinline__ u64 reduce64(u64 x, const LimbConst& c) {
   return csub(x - qt * c.q, c.q);
 }
 
-// (hi * 2^64 + lo) mod q, canonical.
+// (hi * 2^64 + lo) mod q, canonical.  Shoup's product accepts any hi < 2^64.
 __device__ __forceinline__ u64 reduce128(u64 hi, u64 lo, const LimbConst& c) {
-  u64 rh = reduce64(hi, c);
-  u64 t = mul_shoup_lazy(rh, c.r64, c.r64s, c.q);  // [0, 2q)
+  u64 t = mul_shoup_lazy(hi, c.r64, c.r64s, c.q);  // [0, 2q)
   u64 rl = reduce64(lo, c);
   u64 s = t + rl;                                   // [0, 3q)
   s = csub(s, 2 * c.q);

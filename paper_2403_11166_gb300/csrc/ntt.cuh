@@ -140,7 +140,8 @@ struct NttCfg {
   static constexpr int T = N >> LOGE;
   static constexpr int LAST_S0 = ((LOGN - 1) / LOGE) * LOGE;
   static constexpr size_t SMEM = (size_t)N * sizeof(u64);
-  static constexpr int MIN_BLOCKS = T >= 512 ? 1 : 2;   // 512+ threads: one CTA per SM
+  // two CTAs (two transforms) per SM when their threads and shared memory fit
+  static constexpr int MIN_BLOCKS = (T <= 512 && 2 * SMEM <= 227 * 1024) ? 2 : 1;
 };
 
 // Forward transform of (poly, limb) with a fused prologue (Mode::load,
@@ -154,10 +155,23 @@ __device__ __forceinline__ void ntt_fwd_run(const DevCtx& ctx, const typename Mo
   const u64 q = lc.q, q2 = 2 * q;
   const ulonglong2* tw = ctx.tw_fwd + (size_t)limb * C::N;
   u64 v[C::E];
+  if constexpr (Mode::kHeavyLoad) {
+    // Long prologue (gathers, multiplies): a short loop through shared memory
+    // keeps the code small; each thread re-reads only the slots it wrote.
+#pragma unroll 4
+    for (int l = 0; l < C::E; ++l) {
+      const int e = tau + l * C::T;
+      sm[sidx<LOGN>(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+    }
 #pragma unroll
-  for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
+    for (int l = 0; l < C::E; ++l) v[l] = sm[sidx<LOGN>(tau + l * C::T)];
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
+  }
   FwdRounds<LOGN, C::LOGE, 0>::run(v, sm, tw, tau, q, q2);
-#pragma unroll
+#pragma unroll(Mode::kEpilogueUnroll)
   for (int l = 0; l < C::E / 2; ++l) {
     const int e = 2 * (tau + l * C::T);
     const u64 x0 = canon4(sm[sidx<LOGN>(e)], q, q2);
@@ -177,18 +191,16 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   const u64 q = lc.q, q2 = 2 * q;
   const ulonglong2* tw = ctx.tw_inv + (size_t)limb * C::N;
   u64 v[C::E];
-#pragma unroll
+#pragma unroll(Mode::kHeavyLoad ? 4 : C::E)
   for (int l = 0; l < C::E; ++l) {
     const int e = tau + l * C::T;
     sm[sidx<LOGN>(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
   }
   __syncthreads();
   InvRounds<LOGN, C::LOGE, C::LAST_S0>::run(v, sm, tw, tau, q, q2);
+  // v in [0, 2q); the mode applies N^{-1} (possibly folded into its own constant)
 #pragma unroll
-  for (int l = 0; l < C::E; ++l) {
-    const u64 x = mul_shoup(v[l], lc.ninv, lc.ninvs, q);
-    Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, x);
-  }
+  for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
 }
 
 template <int LOGN, int LOGE, class Mode>
@@ -240,6 +252,8 @@ __device__ __forceinline__ size_t ct_off(int poly, int comp, int limb, int L, in
 
 // In-place transform of [count][L][N] polynomials.
 struct ModeRaw {
+  static constexpr bool kHeavyLoad = false;
+  static constexpr int kEpilogueUnroll = 16;
   struct Params {
     u64* polys;
   };
@@ -255,15 +269,17 @@ struct ModeRaw {
     *reinterpret_cast<ulonglong2*>(P.polys + limb_off(poly, limb, c.L, N) + e) = make_ulonglong2(x0, x1);
   }
   template <int N>
-  static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+  static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
-    P.polys[limb_off(poly, limb, c.L, N) + e] = x;
+    P.polys[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.ninv, lc.ninvs, lc.q);
   }
 };
 
 // DO encryption: prologue Delta*m + e (m gathered by the packing), epilogue
 // c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain.
 struct ModeEncrypt {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 1;   // Philox + two reductions per pair
   struct Params {
     Packing pk;
     Accessor ac;
@@ -299,6 +315,8 @@ struct ModeEncrypt {
 
 // MO add_plain (Alg. 1 step 2): out_c0 = ct_in.c0 + NTT(Delta * pi_v(x0)).
 struct ModeAddPlain {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 4;
   struct Params {
     Packing pk;
     Accessor ac;
@@ -323,6 +341,8 @@ struct ModeAddPlain {
 
 // MO plaintext encoding: centred lift of Z_t values, NTT.
 struct ModeEncode {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 4;
   struct Params {
     Packing pk;
     Accessor ac;
@@ -345,6 +365,8 @@ struct ModeEncode {
 
 // MO re-mask (Alg. 1 step 3): ct_out.c0 -= NTT(Delta * s).
 struct ModeMask {
+  static constexpr bool kHeavyLoad = false;
+  static constexpr int kEpilogueUnroll = 4;
   struct Params {
     const u64* mpoly;   // [count][N] Z_t mask coefficients
     u64* ct;            // [count][2][L][N]
@@ -370,6 +392,8 @@ __device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
 
 // DO key generation: ternary s, NTT, stored with Shoup companions.
 struct ModeKeygen {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 1;
   struct Params {
     u64 seed;
     ulonglong2* sk;   // [L][N]
@@ -389,8 +413,11 @@ struct ModeKeygen {
   }
 };
 
-// DO decryption, first half: x = INTT(c0 + c1 * s_hat); stores y = x * qtilde mod q_j.
+// DO decryption, first half: x = INTT(c0 + c1 * s_hat); stores y = x * qtilde mod q_j
+// (the INTT's N^{-1} and qtilde are one constant).
 struct ModeDecrypt {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 16;
   struct Params {
     const u64* ct;          // [count][2][L][N]
     const ulonglong2* sk;   // [L][N]
@@ -408,7 +435,7 @@ struct ModeDecrypt {
   template <int N>
   static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
-    P.out[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.qtil, lc.qtils, lc.q);
+    P.out[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.nqtil, lc.nqtils, lc.q);   // N^{-1} qtil
   }
 };
 
