@@ -215,6 +215,20 @@ int he_linear_forward(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* ct
                       uint64_t mask_seed, uint64_t* ct_out, uint64_t* y0,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* he_linear_forward in two calls, so that the MO's ciphertext-independent work
+ * runs before (or concurrently with) the DO's encryption:
+ * he_linear_forward_prepare draws s, writes y0 and leaves NTT(Delta pi_v(x0))
+ * and NTT(Delta s) in ws; he_linear_forward_apply (same plan, same ws, ordered
+ * after the prepare on the GPU) computes ct_out from ct_in and pt.  ws is read,
+ * not modified, by the apply.  The pair's outputs are bit-identical to
+ * he_linear_forward with the same arguments.  Same argument rules. */
+int he_linear_forward_prepare(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* x0,
+                              const uint64_t* bias, uint64_t mask_seed, uint64_t* y0,
+                              void* ws, size_t ws_bytes, void* stream);
+int he_linear_forward_apply(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* ct_in,
+                            const uint64_t* pt, uint64_t* ct_out,
+                            void* ws, size_t ws_bytes, void* stream);
+
 /* MO: backward pass of one layer (Sec. 3.2.2).
  * Input gradient (plan_dgrad, nullable to skip): Algorithm 1 on the DGRAD plan,
  *   ct_gx = sum_k (ct_gy1_d + Delta pi_v(gy0)) * pt_wt - Delta s_x, gx0 = s_x
@@ -319,7 +333,7 @@ enum {
   PENCIL_K_NTT_RAW = 0, PENCIL_K_INTT_RAW, PENCIL_K_NTT_ENCRYPT, PENCIL_K_NTT_ADDPLAIN, PENCIL_K_NTT_ENCODE,
   PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
   PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_RING,
-  PENCIL_K_BIAS_GRAD, PENCIL_K_COUNT
+  PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_COUNT
 };
 typedef struct {
   int32_t kernel;   /* PENCIL_K_* */

@@ -715,9 +715,10 @@ extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, 
   auto al = [](long long b) { return (b + 255) / 256 * 256; };
   const long long lnb = (long long)ctx->dev.L * n * 8;
   P->ws_encrypt = al(std::max(P->ct_in, P->pt) * (long long)n);
-  P->ws_forward = al(P->ct_in * lnb) + al(P->ct_out * (long long)n * 8);
-  if (role == PENCIL_ROLE_WGRAD)
-    P->ws_backward = al(P->pt * lnb) + al(P->ct_in * lnb) + al(P->ct_out * (long long)n * 8);
+  // Alg. 1: NTT(Delta x0) per input ct, NTT(Delta s) per output ct, s per output ct
+  P->ws_forward = al(P->ct_in * lnb) + al(P->ct_out * lnb) + al(P->ct_out * (long long)n * 8);
+  if (role == PENCIL_ROLE_WGRAD)   // Alg. 2: encoded <gY>_0 and <X>_0, NTT(Delta s), s
+    P->ws_backward = al(P->pt * lnb) + al(P->ct_in * lnb) + al(P->ct_out * lnb) + al(P->ct_out * (long long)n * 8);
   else
     P->ws_backward = P->ws_forward;
   P->ws_decrypt = al(P->ct_out * lnb);
@@ -840,30 +841,67 @@ extern "C" int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const Pe
   return PENCIL_OK;
 }
 
-// Alg. 1 steps 2-3 for a FWD or DGRAD plan (shared by forward and backward).
-static int alg1(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, const u64* pt, const u64* x0, const u64* bias,
-                u64 mask_seed, u64* ct_out, u64* y0, char* ws, cudaStream_t s) {
-  const long long lnw = (long long)ctx->dev.L * ctx->n;
-  u64* c0p = reinterpret_cast<u64*>(ws);
-  u64* mpoly = reinterpret_cast<u64*>(ws + (P->ct_in * lnw * 8 + 255) / 256 * 256);
-  ModeAddPlain::Params A;
-  A.pk = P->pk_v;
-  A.ac = P->acc_v;
-  A.ac.ptr = x0;
-  A.ct_in = ct_in;
-  A.out_c0 = c0p;
+// Workspace regions of Alg. 1 (FWD or DGRAD plan): NTT(Delta x0) [ct_in][L][N],
+// NTT(Delta s) [ct_out][L][N], mask coefficients s [ct_out][N].
+struct Alg1Ws {
+  u64 *p0, *mnt, *mpoly;
+};
+static Alg1Ws alg1_ws(const PencilPlan* P, char* ws) {
+  auto al = [](long long b) { return (b + 255) / 256 * 256; };
+  const long long lnb = (long long)P->ctx->dev.L * P->ctx->n * 8;
+  Alg1Ws w;
+  w.p0 = reinterpret_cast<u64*>(ws);
+  w.mnt = reinterpret_cast<u64*>(ws + al(P->ct_in * lnb));
+  w.mpoly = reinterpret_cast<u64*>(ws + al(P->ct_in * lnb) + al(P->ct_out * lnb));
+  return w;
+}
+
+// MO's ciphertext-independent part of Alg. 1 steps 2-3: the mask s (Z_t
+// coefficients), then NTT(Delta pi_v(x0)) and NTT(Delta s) in one launch, and
+// the MO's share s + b.
+static int alg1_prepare(PencilCtx* ctx, const PencilPlan* P, const u64* x0, const u64* bias, u64 mask_seed, u64* y0,
+                        char* ws, cudaStream_t s) {
+  const Alg1Ws w = alg1_ws(P, ws);
   {
-    PROF(ctx, PENCIL_K_NTT_ADDPLAIN, s);
-    CUDA_TRY((ntt<ModeAddPlain, false>(ctx->dev, A, (int)P->ct_in, s)));
+    PROF(ctx, PENCIL_K_MASK_POLY, s);
+    CUDA_TRY(launch_mask_poly(ctx->dev, P->pk_y, P->acc_y, mask_seed, (int)P->ct_out, w.mpoly, s));
   }
+  ModeMoPrep::Params R;
+  R.pk = P->pk_v;
+  R.ac = P->acc_v;
+  R.ac.ptr = x0;
+  R.mpoly = w.mpoly;
+  R.n_in = (int)P->ct_in;
+  R.out_in = w.p0;
+  R.out_mask = w.mnt;
+  {
+    PROF(ctx, PENCIL_K_NTT_MO_PREP, s);
+    CUDA_TRY((ntt<ModeMoPrep, false>(ctx->dev, R, (int)(P->ct_in + P->ct_out), s)));
+  }
+  {
+    PROF(ctx, PENCIL_K_MO_SHARE, s);
+    CUDA_TRY(launch_mo_share(mask_seed, P->out_elems, ctx->dev.t_mask, bias, P->hw, P->co_out, y0, s));
+  }
+  return PENCIL_OK;
+}
+
+// Alg. 1 steps 2-3 on the received ciphertexts: ct_out[m, n] = sum_k
+// (ct_in[m, k] + NTT(Delta x0)[m, k]) pt[k, n] - NTT(Delta s)[m, n], one launch.
+static int alg1_apply(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, const u64* pt, u64* ct_out, char* ws,
+                      cudaStream_t s) {
+  const Alg1Ws w = alg1_ws(P, ws);
+  const long long lnw = (long long)ctx->dev.L * ctx->n;
   MacParams M;
   memset(&M, 0, sizeof(M));
-  M.a0 = c0p;
-  M.a0_stride = lnw;
+  M.a0 = ct_in;
+  M.a0_stride = 2 * lnw;
+  M.p0 = w.p0;
+  M.p0_stride = lnw;
   M.a1 = ct_in + lnw;
   M.a1_stride = 2 * lnw;
   M.b = pt;
   M.b_stride = lnw;
+  M.mask = w.mnt;
   M.out = ct_out;
   M.M = (int)P->c.M();
   M.K = (int)P->c.K();
@@ -873,35 +911,53 @@ static int alg1(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, const u64
     PROF(ctx, PENCIL_K_MAC, s);
     CUDA_TRY(launch_mac(ctx->dev, M, false, s));
   }
-  Accessor ay = P->acc_y;
-  {
-    PROF(ctx, PENCIL_K_MASK_POLY, s);
-    CUDA_TRY(launch_mask_poly(ctx->dev, P->pk_y, ay, mask_seed, (int)P->ct_out, mpoly, s));
-  }
-  ModeMask::Params K;
-  K.mpoly = mpoly;
-  K.ct = ct_out;
-  {
-    PROF(ctx, PENCIL_K_NTT_MASK, s);
-    CUDA_TRY((ntt<ModeMask, false>(ctx->dev, K, (int)P->ct_out, s)));
-  }
-  {
-    PROF(ctx, PENCIL_K_MO_SHARE, s);
-    CUDA_TRY(launch_mo_share(mask_seed, P->out_elems, ctx->dev.t_mask, bias, P->hw, P->co_out, y0, s));
-  }
+  return PENCIL_OK;
+}
+
+static int alg1(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, const u64* pt, const u64* x0, const u64* bias,
+                u64 mask_seed, u64* ct_out, u64* y0, char* ws, cudaStream_t s) {
+  int rc = alg1_prepare(ctx, P, x0, bias, mask_seed, y0, ws, s);
+  return rc != PENCIL_OK ? rc : alg1_apply(ctx, P, ct_in, pt, ct_out, ws, s);
+}
+
+static int check_fwd_plan(PencilCtx* ctx, const PencilPlan* P, const void* bias, void* ws, size_t ws_bytes) {
+  if (!ctx || !P || !ws || P->ctx != ctx) return PENCIL_E_ARG;
+  if (P->role == PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  if (bias && P->role != PENCIL_ROLE_FWD) return PENCIL_E_ARG;
+  if (!aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_forward) return PENCIL_E_CAPACITY;
   return PENCIL_OK;
 }
 
 extern "C" int he_linear_forward(PencilCtx* ctx, const PencilPlan* P, const uint64_t* ct_in, const uint64_t* pt,
                                  const uint64_t* x0, const uint64_t* bias, uint64_t mask_seed, uint64_t* ct_out,
                                  uint64_t* y0, void* ws, size_t ws_bytes, void* stream) {
-  if (!ctx || !P || !ct_in || !pt || !x0 || !ct_out || !y0 || !ws || P->ctx != ctx) return PENCIL_E_ARG;
-  if (P->role == PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
-  if (bias && P->role != PENCIL_ROLE_FWD) return PENCIL_E_ARG;
-  if (!aligned16(ct_in) || !aligned16(pt) || !aligned16(ct_out) || !aligned16(ws)) return PENCIL_E_ARG;
-  if ((long long)ws_bytes < P->ws_forward) return PENCIL_E_CAPACITY;
+  int rc = check_fwd_plan(ctx, P, bias, ws, ws_bytes);
+  if (rc != PENCIL_OK) return rc;
+  if (!ct_in || !pt || !x0 || !ct_out || !y0) return PENCIL_E_ARG;
+  if (!aligned16(ct_in) || !aligned16(pt) || !aligned16(ct_out)) return PENCIL_E_ARG;
   DeviceGuard guard(ctx->device);
   return alg1(ctx, P, ct_in, pt, x0, bias, mask_seed, ct_out, y0, reinterpret_cast<char*>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int he_linear_forward_prepare(PencilCtx* ctx, const PencilPlan* P, const uint64_t* x0,
+                                         const uint64_t* bias, uint64_t mask_seed, uint64_t* y0, void* ws,
+                                         size_t ws_bytes, void* stream) {
+  int rc = check_fwd_plan(ctx, P, bias, ws, ws_bytes);
+  if (rc != PENCIL_OK) return rc;
+  if (!x0 || !y0) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  return alg1_prepare(ctx, P, x0, bias, mask_seed, y0, reinterpret_cast<char*>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int he_linear_forward_apply(PencilCtx* ctx, const PencilPlan* P, const uint64_t* ct_in, const uint64_t* pt,
+                                       uint64_t* ct_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_fwd_plan(ctx, P, nullptr, ws, ws_bytes);
+  if (rc != PENCIL_OK) return rc;
+  if (!ct_in || !pt || !ct_out) return PENCIL_E_ARG;
+  if (!aligned16(ct_in) || !aligned16(pt) || !aligned16(ct_out)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  return alg1_apply(ctx, P, ct_in, pt, ct_out, reinterpret_cast<char*>(ws), (cudaStream_t)stream);
 }
 
 extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const PencilPlan* Pw,
@@ -935,7 +991,21 @@ extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const Pe
     auto al = [](long long b) { return (b + 255) / 256 * 256; };
     u64* pt_gy0 = reinterpret_cast<u64*>(w);
     u64* pt_x0 = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8));
-    u64* mpoly = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8) + al(Pw->ct_in * lnw * 8));
+    u64* mnt = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8) + al(Pw->ct_in * lnw * 8));
+    u64* mpoly = reinterpret_cast<u64*>(w + al(Pw->pt * lnw * 8) + al(Pw->ct_in * lnw * 8) + al(Pw->ct_out * lnw * 8));
+    {
+      PROF(ctx, PENCIL_K_MASK_POLY, s);
+      CUDA_TRY(launch_mask_poly(ctx->dev, Pw->pk_y, Pw->acc_y, mask_seed_w, (int)Pw->ct_out, mpoly, s));
+    }
+    ModeMoPrep::Params R;
+    memset(&R, 0, sizeof(R));
+    R.mpoly = mpoly;
+    R.n_in = 0;
+    R.out_mask = mnt;
+    {
+      PROF(ctx, PENCIL_K_NTT_MO_PREP, s);
+      CUDA_TRY((ntt<ModeMoPrep, false>(ctx->dev, R, (int)Pw->ct_out, s)));
+    }
     ModeEncode::Params E1;
     E1.pk = Pw->pk_w;
     E1.ac = Pw->acc_w;
@@ -967,6 +1037,7 @@ extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const Pe
     M.cb0 = ct_gy1_w;
     M.cb1 = ct_gy1_w + lnw;
     M.cb_stride = 2 * lnw;
+    M.mask = mnt;
     M.out = ct_gw;
     M.M = (int)Pw->c.M();
     M.K = (int)Pw->c.K();
@@ -975,17 +1046,6 @@ extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const Pe
     {
       PROF(ctx, PENCIL_K_MAC_DUAL, s);
       CUDA_TRY(launch_mac(ctx->dev, M, true, s));
-    }
-    {
-      PROF(ctx, PENCIL_K_MASK_POLY, s);
-      CUDA_TRY(launch_mask_poly(ctx->dev, Pw->pk_y, Pw->acc_y, mask_seed_w, (int)Pw->ct_out, mpoly, s));
-    }
-    ModeMask::Params K;
-    K.mpoly = mpoly;
-    K.ct = ct_gw;
-    {
-      PROF(ctx, PENCIL_K_NTT_MASK, s);
-      CUDA_TRY((ntt<ModeMask, false>(ctx->dev, K, (int)Pw->ct_out, s)));
     }
     {
       PROF(ctx, PENCIL_K_MO_SHARE, s);

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx ctx, MacParams P) {
   const int fold = DUAL ? 64 : 128;   // products per accumulator stay below 2^128
   for (int k = 0; k < P.K; ++k) {
     const size_t mk = (size_t)m * P.K + k;
-    const u64 a0 = __ldg(P.a0 + mk * P.a0_stride + lane);
+    u64 a0 = __ldg(P.a0 + mk * P.a0_stride + lane);
+    if (P.p0) a0 = add_mod(a0, __ldg(P.p0 + mk * P.p0_stride + lane), lc.q);
     const u64 a1 = __ldg(P.a1 + mk * P.a1_stride + lane);
     u64 pa = 0;
     if constexpr (DUAL) pa = __ldg(P.pa + mk * P.pa_stride + lane);
@@ -65,8 +66,10 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx ctx, MacParams P) {
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     if (j < nn) {
-      const size_t o = ((size_t)m * P.NC + n0 + j) * 2 * ln + lane;
-      P.out[o] = reduce128(hi0[j], lo0[j], lc);
+      const size_t mn = (size_t)m * P.NC + n0 + j, o = mn * 2 * ln + lane;
+      u64 v0 = reduce128(hi0[j], lo0[j], lc);
+      if (P.mask) v0 = sub_mod(v0, __ldg(P.mask + mn * ln + lane), lc.q);
+      P.out[o] = v0;
       P.out[o + ln] = reduce128(hi1[j], lo1[j], lc);
     }
   }
@@ -108,17 +111,49 @@ __device__ __forceinline__ void fold3(Acc3& a, u64 c60, u64 c64) {
   a.s0 &= (1ull << 30) - 1;
 }
 
-// canonical value of a folded accumulator: S0 + S1 2^30 (< 2^66) mod q
+// canonical value of an accumulator.  After fold3, S0 < 2^30 and S1 < 2^35, and
+// S0 + S1 2^30 = S0 + (S1 mod 2^30) 2^30 + (S1 >> 30) 2^60 with 2^60 = c60 mod q
+// (c60 < 2^28), a sum below 2^60 + 2^33: one Barrett reduction (any q < 2^60).
 __device__ __forceinline__ u64 acc3_value(Acc3 a, const LimbConst& lc) {
   fold3(a, lc.c60, lc.c64);
-  const u64 lo = a.s0 + (a.s1 << 30);
-  const u64 hi = (a.s1 >> 34) + (lo < a.s0 ? 1ull : 0ull);
-  return reduce128(hi, lo, lc);
+  const u64 v = a.s0 + ((a.s1 & ((1ull << 30) - 1)) << 30) + (u64)(u32)(a.s1 >> 30) * (u32)lc.c60;
+  return reduce64(v, lc);
 }
 
-// Outputs (m, n0 .. n0 + NT - 1) of one slot `lane`.
+__device__ __forceinline__ void cp_async16(u64* smem, const u64* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+__device__ __forceinline__ void cp_async8(u64* smem, const u64* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Per-thread operand ring of the split multiply-accumulate: every thread copies
+// its own operand words of input blocks k + 1 .. k + MAC_RING - 1 into shared
+// memory (8-byte cp.async, no sharing between threads, so no barrier) while it
+// multiplies block k; words are stored [stage][word][thread] (consecutive
+// threads, consecutive banks).
+#define MAC_RING 4
 template <int NT, bool DUAL>
-__device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParams& P, int m, int n0, int lane) {
+struct MacRing {
+  // a0, a1, (Alg. 1: NTT(Delta x0) | Alg. 2: A'), B[NT] (Alg. 2: + B'0[NT], B'1[NT])
+  static constexpr int W = DUAL ? 3 + 3 * NT : 3 + NT;
+  static constexpr size_t bytes(int threads) { return (size_t)MAC_RING * W * threads * sizeof(u64); }
+};
+
+// Outputs (m, n0 .. n0 + NT - 1) of one slot `lane`; `ring` = this CTA's ring
+// (MacRing::bytes(blockDim.x)), `tid` = this thread's column in it.
+template <int NT, bool DUAL>
+__device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParams& P, int m, int n0, int lane,
+                                               u64* ring, int tid) {
+  constexpr int W = MacRing<NT, DUAL>::W;
+  const int T = blockDim.x;
   const int nn = min(NT, P.NC - n0);
   const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
   const u64 c60 = lc.c60, c64 = lc.c64;
@@ -129,48 +164,71 @@ __device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParam
 #pragma unroll
     for (int c = 0; c < 2; ++c) acc[j][c] = Acc3{0, 0, 0};
   constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
-  // operands of step k, loaded one step ahead
-  u64 a0, a1, pa = 0, b[NT], c0[NT], c1[NT];
-  auto load = [&](int k) {
-    const size_t mk = (size_t)m * P.K + k;
-    a0 = __ldg(P.a0 + mk * P.a0_stride + lane);
-    a1 = __ldg(P.a1 + mk * P.a1_stride + lane);
-    if constexpr (DUAL) pa = __ldg(P.pa + mk * P.pa_stride + lane);
+  // operand pointers of the next block to copy (advanced by one block per copy)
+  const size_t mk0 = (size_t)m * P.K;
+  const u64* pa0 = P.a0 + mk0 * P.a0_stride + lane;
+  const u64* pa1 = P.a1 + mk0 * P.a1_stride + lane;
+  const u64* pp0 = DUAL ? P.pa + mk0 * P.pa_stride + lane : (P.p0 ? P.p0 + mk0 * P.p0_stride + lane : nullptr);
+  const i64 p_step = DUAL ? P.pa_stride : P.p0_stride;
+  const u64* pb = P.b + (size_t)n0 * P.b_stride + lane;
+  const u64* pc0 = DUAL ? P.cb0 + (size_t)n0 * P.cb_stride + lane : nullptr;
+  const u64* pc1 = DUAL ? P.cb1 + (size_t)n0 * P.cb_stride + lane : nullptr;
+  const size_t kb = (size_t)P.NC * P.b_stride, kc = (size_t)P.NC * P.cb_stride;
+  u64* mine = ring + tid;
+  auto word = [&](int stage, int w) -> u64* { return mine + (size_t)(stage * W + w) * T; };
+  auto issue = [&](int stage) {
+    cp_async8(word(stage, 0), pa0);
+    cp_async8(word(stage, 1), pa1);
+    if (pp0) cp_async8(word(stage, 2), pp0);
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      const size_t kn = (size_t)k * P.NC + n0 + (j < nn ? j : 0);
-      b[j] = __ldg(P.b + kn * P.b_stride + lane);
+      const int jj = j < nn ? j : 0;
+      cp_async8(word(stage, 3 + j), pb + jj * P.b_stride);
       if constexpr (DUAL) {
-        c0[j] = __ldg(P.cb0 + kn * P.cb_stride + lane);
-        c1[j] = __ldg(P.cb1 + kn * P.cb_stride + lane);
+        cp_async8(word(stage, 3 + NT + j), pc0 + jj * P.cb_stride);
+        cp_async8(word(stage, 3 + 2 * NT + j), pc1 + jj * P.cb_stride);
       }
+    }
+    pa0 += P.a0_stride;
+    pa1 += P.a1_stride;
+    if (pp0) pp0 += p_step;
+    pb += kb;
+    if constexpr (DUAL) {
+      pc0 += kc;
+      pc1 += kc;
     }
   };
-  load(0);
+#pragma unroll
+  for (int st = 0; st < MAC_RING - 1; ++st) {
+    if (st < P.K) issue(st);
+    cp_async_commit();
+  }
   for (int k = 0; k < P.K; ++k) {
+    if (k + MAC_RING - 1 < P.K) issue((k + MAC_RING - 1) % MAC_RING);
+    cp_async_commit();
+    cp_async_wait<MAC_RING - 1>();   // this thread's copies of block k have landed
+    const int st = k % MAC_RING;
+    u64 a0 = *word(st, 0);
+    if (!DUAL && pp0) a0 = add_mod(a0, *word(st, 2), lc.q);   // Alg. 1 step 2: + NTT(Delta x0)
+    const u64 a1 = *word(st, 1);
     const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
     const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
-    const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
-    u32 bL[NT], bH[NT], c0L[NT], c0H[NT], c1L[NT], c1H[NT];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      bL[j] = (u32)b[j] & M30;
-      bH[j] = (u32)(b[j] >> 30);
-      if constexpr (DUAL) {
-        c0L[j] = (u32)c0[j] & M30;
-        c0H[j] = (u32)(c0[j] >> 30);
-        c1L[j] = (u32)c1[j] & M30;
-        c1H[j] = (u32)(c1[j] >> 30);
-      }
+    u32 pL = 0, pH = 0;
+    if constexpr (DUAL) {
+      const u64 pa = *word(st, 2);
+      pL = (u32)pa & M30;
+      pH = (u32)(pa >> 30);
     }
-    if (k + 1 < P.K) load(k + 1);
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      mac_split(acc[j][0], a0L, a0H, bL[j], bH[j]);
-      mac_split(acc[j][1], a1L, a1H, bL[j], bH[j]);
+      const u64 b = *word(st, 3 + j);
+      const u32 bL = (u32)b & M30, bH = (u32)(b >> 30);
+      mac_split(acc[j][0], a0L, a0H, bL, bH);
+      mac_split(acc[j][1], a1L, a1H, bL, bH);
       if constexpr (DUAL) {
-        mac_split(acc[j][0], c0L[j], c0H[j], pL, pH);
-        mac_split(acc[j][1], c1L[j], c1H[j], pL, pH);
+        const u64 c0 = *word(st, 3 + NT + j), c1 = *word(st, 3 + 2 * NT + j);
+        mac_split(acc[j][0], (u32)c0 & M30, (u32)(c0 >> 30), pL, pH);
+        mac_split(acc[j][1], (u32)c1 & M30, (u32)(c1 >> 30), pL, pH);
       }
     }
     if ((k % FOLD) == FOLD - 1) {
@@ -185,21 +243,24 @@ __device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParam
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     if (j < nn) {
-      const size_t o = ((size_t)m * P.NC + n0 + j) * 2 * ln + lane;
-      P.out[o] = acc3_value(acc[j][0], lc);
+      const size_t mn = (size_t)m * P.NC + n0 + j, o = mn * 2 * ln + lane;
+      u64 v0 = acc3_value(acc[j][0], lc);
+      if (P.mask) v0 = sub_mod(v0, __ldg(P.mask + mn * ln + lane), lc.q);
+      P.out[o] = v0;
       P.out[o + ln] = acc3_value(acc[j][1], lc);
     }
   }
 }
 
 template <int NT, bool DUAL>
-__global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
+__global__ void __launch_bounds__(128, (NT == 4 && !DUAL) ? 6 : 0) k_mac_split(DevCtx ctx, MacParams P) {
+  extern __shared__ u64 ring[];
   const int ntiles = (P.NC + NT - 1) / NT;
   const int m = blockIdx.x / ntiles + P.m_base;
   const int n0 = (blockIdx.x % ntiles) * NT;
   const int lane = blockIdx.y * blockDim.x + threadIdx.x;
   if (lane >= P.lanes || m >= P.M) return;
-  mac_split_tile<NT, DUAL>(ctx, P, m, n0, lane);
+  mac_split_tile<NT, DUAL>(ctx, P, m, n0, lane, ring, threadIdx.x);
 }
 
 // ------------------------------------------------------------------ MAC, shared-memory staged
@@ -216,15 +277,6 @@ __global__ void __launch_bounds__(128) k_mac_split(DevCtx ctx, MacParams P) {
 #define MAC_PAIRS 8
 #define MAC_STAGES 4
 
-__device__ __forceinline__ void cp_async16(u64* smem, const u64* gmem, int bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
-}
 
 // Global address of row `row` of stage k (or nullptr when outside the layer).
 // Rows: [0, 2MB) A components; [2MB, 2MB + NB) B; Alg. 2: [.., + MB) A', [.., + 2NB) B' components.
@@ -242,9 +294,11 @@ __device__ __forceinline__ const u64* mac_row(const MacParams& P, int MB, int NB
     return n < P.NC ? P.b + ((size_t)k * P.NC + n) * P.b_stride : nullptr;
   }
   row -= NB;
-  if (row < MB) {
+  if (row < MB) {   // Alg. 2: A'[m, k]; Alg. 1: NTT(Delta x0)[m, k]
     const int m = m0 + row;
-    return m < P.M ? P.pa + ((size_t)m * P.K + k) * P.pa_stride : nullptr;
+    if (m >= P.M) return nullptr;
+    const size_t mk = (size_t)m * P.K + k;
+    return DUAL ? P.pa + mk * P.pa_stride : P.p0 + mk * P.p0_stride;
   }
   row -= MB;
   const int n = n0 + (row >> 1);
@@ -273,7 +327,8 @@ __global__ void __launch_bounds__(256, 2) k_mac_smem(DevCtx ctx, MacParams P, in
   const int m0 = mb * MB + P.m_base, n0 = nb * NB;
   const int tid = threadIdx.x, col = tid & (MAC_LANES - 1), warp = tid >> 5;
   const int lane = lane0 + col;
-  const int W = DUAL ? 3 * (MB + NB) : 2 * MB + NB;
+  const bool add_p0 = !DUAL && P.p0 != nullptr;
+  const int W = DUAL ? 3 * (MB + NB) : 2 * MB + NB + (add_p0 ? MB : 0);
   constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
   constexpr u32 M30 = (1u << 30) - 1;
   const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
@@ -293,6 +348,15 @@ __global__ void __launch_bounds__(256, 2) k_mac_smem(DevCtx ctx, MacParams P, in
     cp_async_commit();
     cp_async_wait<MAC_STAGES - 1>();
     __syncthreads();
+    if (add_p0) {  // Alg. 1 step 2: first components += NTT(Delta x0), before any word is split
+      u64* w = st + (size_t)(k % MAC_STAGES) * W * MAC_LANES;
+      for (int idx = tid; idx < MB * MAC_LANES; idx += blockDim.x) {
+        const int r = idx / MAC_LANES, c = idx % MAC_LANES;
+        const u64 q = ctx.limb[(lane0 + c) >> ctx.log_n].q;
+        w[(2 * r) * MAC_LANES + c] = add_mod(w[(2 * r) * MAC_LANES + c], w[(2 * MB + NB + r) * MAC_LANES + c], q);
+      }
+      __syncthreads();
+    }
     {  // split every staged word once: (low 30 bits) | (high 30 bits) << 32
       u64* w = st + (size_t)(k % MAC_STAGES) * W * MAC_LANES;
       for (int idx = tid; idx < W * MAC_LANES; idx += blockDim.x) {
@@ -334,8 +398,10 @@ __global__ void __launch_bounds__(256, 2) k_mac_smem(DevCtx ctx, MacParams P, in
     const int p = warp * MAC_PAIRS + i;
     const int m = m0 + (p >> lnb), n = n0 + (p & (NB - 1));
     if (m < P.M && n < P.NC) {
-      const size_t o = ((size_t)m * P.NC + n) * 2 * ln + lane;
-      P.out[o] = acc3_value(acc[i][0], lc);
+      const size_t mn = (size_t)m * P.NC + n, o = mn * 2 * ln + lane;
+      u64 v0 = acc3_value(acc[i][0], lc);
+      if (P.mask) v0 = sub_mod(v0, __ldg(P.mask + mn * ln + lane), lc.q);
+      P.out[o] = v0;
       P.out[o + ln] = acc3_value(acc[i][1], lc);
     }
   }
@@ -349,7 +415,7 @@ static cudaError_t launch_mac_smem(const DevCtx& ctx, const MacParams& P0, bool 
     ++lnb;
   }
   const int MB = 64 / NB;
-  const int words = dual ? 3 * (MB + NB) : 2 * MB + NB;
+  const int words = dual ? 3 * (MB + NB) : 2 * MB + NB + (P0.p0 ? MB : 0);
   const size_t smem = (size_t)MAC_STAGES * words * MAC_LANES * sizeof(u64);
   cudaError_t e = dual ? cudaFuncSetAttribute(k_mac_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                        : cudaFuncSetAttribute(k_mac_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -380,14 +446,20 @@ static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool
   const int ntiles = (P.NC + NT - 1) / NT;
   const unsigned gy = (unsigned)((P.lanes + threads - 1) / threads);
   const int mchunk = max(1, 2147483647 / max(1, ntiles));
+  const size_t smem = dual ? MacRing<NT, true>::bytes(threads) : MacRing<NT, false>::bytes(threads);
+  cudaError_t e0 = dual ? cudaFuncSetAttribute(k_mac_split<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)
+                        : cudaFuncSetAttribute(k_mac_split<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+  if (e0 != cudaSuccess) return e0;
   for (int base = 0; base < P0.M; base += mchunk) {
     P.m_base = base;
     const int mc = min(mchunk, P0.M - base);
     dim3 grid((unsigned)(mc * ntiles), gy);
     if (dual)
-      k_mac_split<NT, true><<<grid, threads, 0, s>>>(ctx, P);
+      k_mac_split<NT, true><<<grid, threads, smem, s>>>(ctx, P);
     else
-      k_mac_split<NT, false><<<grid, threads, 0, s>>>(ctx, P);
+      k_mac_split<NT, false><<<grid, threads, smem, s>>>(ctx, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -779,13 +851,14 @@ template <int NT>
 __global__ void __launch_bounds__(128) k_mac_persistent(DevCtx ctx, const MacParams* __restrict__ Ps,
                                                         const int4* __restrict__ items, long long n_items,
                                                         const u64* ready, const u64* step, int* abort_flag) {
+  extern __shared__ u64 ring[];
   const u64 want = (step ? *step : 0ull) + 1;
   for (long long i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int4 it = items[i];   // (layer, m, n0, lane block)
     if (!wait_ready(ready, it.x, want, ctx.status, abort_flag)) return;
     const MacParams& P = Ps[it.x];
     const int lane = it.w * blockDim.x + threadIdx.x;
-    if (lane < P.lanes) mac_split_tile<NT, false>(ctx, P, it.y, it.z, lane);
+    if (lane < P.lanes) mac_split_tile<NT, false>(ctx, P, it.y, it.z, lane, ring, threadIdx.x);
   }
 }
 
@@ -813,13 +886,16 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
     const unsigned grid = (unsigned)std::min<long long>(B.n_mac, (long long)B.mac_blocks);
     switch (B.mac_nt) {
       case 2:
-        k_mac_persistent<2><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+        k_mac_persistent<2><<<grid, 128, MacRing<2, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
+                                                                                B.ready, B.step, B.abort_flag);
         break;
       case 8:
-        k_mac_persistent<8><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+        k_mac_persistent<8><<<grid, 128, MacRing<8, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
+                                                                                B.ready, B.step, B.abort_flag);
         break;
       default:
-        k_mac_persistent<4><<<grid, 128, 0, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step, B.abort_flag);
+        k_mac_persistent<4><<<grid, 128, MacRing<4, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
+                                                                                B.ready, B.step, B.abort_flag);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -853,13 +929,16 @@ cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int* blocks) {
   if (e == cudaSuccess) {
     switch (nt) {
       case 2:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<2>, 128, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<2>, 128,
+                                                        MacRing<2, false>::bytes(128));
         break;
       case 8:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<8>, 128, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<8>, 128,
+                                                        MacRing<8, false>::bytes(128));
         break;
       default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<4>, 128, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<4>, 128,
+                                                        MacRing<4, false>::bytes(128));
     }
   }
   *blocks = std::max(1, sms * std::max(1, per));

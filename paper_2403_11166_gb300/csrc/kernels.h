@@ -20,6 +20,10 @@ struct MacParams {
   const u64* cb0;    // Alg. 2: B'[k, n] ciphertext c0
   const u64* cb1;    //                      and c1
   i64 cb_stride;
+  const u64* p0;     // Alg. 1: NTT(Delta x0)[m, k] added to A's first component on load (or null)
+  i64 p0_stride;
+  const u64* mask;   // Alg. 1 step 3: NTT(Delta s)[m * NC + n] ([lanes] each) subtracted from the
+                     // first output component on store (or null)
   u64* out;          // [M * NC][2][lanes]
   int M, K, NC;
   int lanes;

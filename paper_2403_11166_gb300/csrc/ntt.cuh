@@ -386,6 +386,38 @@ struct ModeMask {
   }
 };
 
+// MO's ciphertext-independent terms of Alg. 1 steps 2-3, one launch for both:
+// polynomials [0, n_in) -> out_in = NTT(Delta * pi_v(x0)) (added to c0 by the
+// multiply-accumulate), [n_in, count) -> out_mask = NTT(Delta * s) of the mask
+// polynomials (subtracted by the multiply-accumulate's store).
+struct ModeMoPrep {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kEpilogueUnroll = 8;
+  struct Params {
+    Packing pk;
+    Accessor ac;
+    const u64* mpoly;   // [count - n_in][N] Z_t mask coefficients
+    int n_in;
+    u64* out_in;        // [n_in][L][N]
+    u64* out_mask;      // [count - n_in][L][N]
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    const u64 m = poly < P.n_in ? gather(P.pk, P.ac, poly, e) & c.t_mask
+                                : P.mpoly[(size_t)(poly - P.n_in) * N + e];
+    return mul_shoup(m, lc.delta, lc.deltas, lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    u64* dst = poly < P.n_in ? P.out_in + limb_off(poly, limb, c.L, N)
+                             : P.out_mask + limb_off(poly - P.n_in, limb, c.L, N);
+    *reinterpret_cast<ulonglong2*>(dst + e) = make_ulonglong2(x0, x1);
+  }
+};
+
 __device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
   return (u64)((((unsigned __int128)w) << 64) / q);
 }
@@ -493,6 +525,7 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeAddPlain, false)  \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMask, false)      \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMoPrep, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
 // Radix 2^4 and 2^5 register blocks for one N.

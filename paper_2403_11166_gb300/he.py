@@ -33,13 +33,13 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune", "pencil_batch_create",
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
-           "pencil_plan_candidates")
+           "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
-                "ring", "bias_grad")
+                "ring", "bias_grad", "ntt_mo_prep")
 
 
 class PencilError(RuntimeError):
@@ -95,6 +95,8 @@ def _load():
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
         "he_linear_forward": [P, P, P, P, P, P, U64, P, P, P, SZ, P],
+        "he_linear_forward_prepare": [P, P, P, P, U64, P, P, SZ, P],
+        "he_linear_forward_apply": [P, P, P, P, P, P, SZ, P],
         "he_linear_backward": [P, P, P, P, P, P, P, P, P, U64, U64, P, P, P, P, P, SZ, P],
         "decrypt_to_share": [P, P, P, P, P, I32, P, SZ, P],
         "pencil_ntt_batch": [P, P, I64, I32, P],
@@ -299,6 +301,18 @@ def he_linear_forward(ctx: Context, plan: Plan, ct_in, pt, x0, bias, mask_seed: 
     w, nb = _ws(ws)
     _check(lib.he_linear_forward(ctx.h, plan.h, _ptr(ct_in), _ptr(pt), _ptr(x0), _ptr(bias), mask_seed,
                                  _ptr(ct_out), _ptr(y0), w, nb, _stream(stream)), "he_linear_forward")
+
+
+def he_linear_forward_prepare(ctx: Context, plan: Plan, x0, bias, mask_seed: int, y0, ws, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.he_linear_forward_prepare(ctx.h, plan.h, _ptr(x0), _ptr(bias), mask_seed, _ptr(y0), w, nb,
+                                         _stream(stream)), "he_linear_forward_prepare")
+
+
+def he_linear_forward_apply(ctx: Context, plan: Plan, ct_in, pt, ct_out, ws, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.he_linear_forward_apply(ctx.h, plan.h, _ptr(ct_in), _ptr(pt), _ptr(ct_out), w, nb, _stream(stream)),
+           "he_linear_forward_apply")
 
 
 def he_linear_backward(ctx: Context, plan_dgrad, plan_wgrad, ct_gy1_d, pt_wt, ct_x1_w, ct_gy1_w, gy0, x0,

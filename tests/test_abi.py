@@ -53,3 +53,11 @@ def test_bad_params_rejected_on_host(lib):
     assert lib.pencil_ctx_create(None, 0, ctypes.byref(h)) == -1
     lib.pencil_sync_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.pencil_sync_status(None, None) == -1
+
+
+def test_binding_status_checks_are_well_formed():
+    """Every status check in the binding passes exactly (code, call name)."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_2403_11166_gb300", "he.py")).read()
+    calls = [n for n in ast.walk(ast.parse(src)) if isinstance(n, ast.Call) and getattr(n.func, "id", None) == "_check"]
+    assert calls and all(len(c.args) == 2 and isinstance(c.args[1], ast.Constant) for c in calls)

@@ -276,3 +276,63 @@ def test_tuning_knobs_do_not_change_results(he, radix, cols):
         outs.append(gpu_forward(he, ctx, sk, L, he.ROLE_FWD, part, W, x1, x0, None, 3, 4)[1:])
     for a, b in zip(*outs):
         assert (a == b).all()
+
+
+@pytest.mark.parametrize("cfg,cols", [((12, 2, 54), None), ((13, 3, 60), 4), ((13, 3, 60), 0)])
+def test_prepare_apply_equals_forward(he, cfg, cols):
+    """he_linear_forward_prepare on one stream, encrypt on another, then
+    he_linear_forward_apply: ciphertexts and shares bit-identical to he_linear_forward
+    (generic, split and shared-memory staged multiply-accumulate)."""
+    L = Layer("conv", B=3, Ci=5, Co=7, h=9, w=8, s=3, pad=1)
+    part = (1, 2, 3, 5, 4, 3, 3)
+    ctx = he.Context(*cfg)
+    if cols is not None:
+        ctx.tune(he.TUNE_MAC_COLUMNS, cols)
+    sk = ctx.keygen(5)
+    g = inputs.rng(8)
+    W = inputs.gaussian_fixed(g, L.w_shape())
+    x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L.x_shape()))
+    bias = inputs.uniform_zt(g, (L.Co,))
+    _, _, _, ct_ref, y0_ref, y1_ref = gpu_forward(he, ctx, sk, L, he.ROLE_FWD, part, W, x1, x0, bias, 3, 4)
+    plan = he.Plan(ctx, _he_layer(he, L), he.ROLE_FWD, part)
+    S = plan.sizes
+    ws_mo = plan.new_ws(S.ws_forward)
+    ws_do = plan.new_ws(max(S.ws_encrypt, S.ws_decrypt))
+    pt, ct_in, ct_out = plan.new_pt(S.pt), plan.new_ct(S.ct_in), plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    y1 = torch.empty_like(y0)
+    Wd, x0d, x1d, bd = to_dev(W), to_dev(x0), to_dev(x1), to_dev(bias)
+    mo, do = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, Wd, pt, stream=mo)
+    he.he_linear_forward_prepare(ctx, plan, x0d, bd, 4, y0, ws_mo, stream=mo)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1d, 3, ct_in, ws_do, stream=do)
+    do.wait_stream(mo)
+    he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct_out, ws_mo, stream=do)
+    he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws_do, stream=do)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    assert (to_np(ct_out) == ct_ref).all()
+    assert (to_np(y0) == y0_ref).all() and (to_np(y1) == y1_ref).all()
+    # the prepared workspace is only read: a second apply gives the same ciphertexts
+    ct2 = plan.new_ct(S.ct_out)
+    he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct2, ws_mo)
+    torch.cuda.synchronize()
+    assert (to_np(ct2) == ct_ref).all()
+
+
+def test_split_calls_validate(he):
+    ctx = he.Context(12, 2, 54)
+    L = Layer("fc", B=2, Ci=10, Co=3)
+    plan = he.Plan(ctx, _he_layer(he, L), he.ROLE_FWD, None)
+    S = plan.sizes
+    small = plan.new_ws(max(1, S.ws_forward // 2))
+    x0 = torch.zeros(L.B * L.Ci, dtype=torch.int64, device="cuda")
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+    with pytest.raises(he.PencilError) as e:
+        he.he_linear_forward_prepare(ctx, plan, x0, None, 1, y0, small)
+    assert e.value.code == -4
+    with pytest.raises(he.PencilError) as e:
+        he.he_linear_forward_apply(ctx, plan, None, plan.new_pt(S.pt), plan.new_ct(S.ct_out),
+                                   plan.new_ws(S.ws_forward))
+    assert e.value.code == -1
