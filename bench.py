@@ -4,10 +4,10 @@
 Workload: the forward homomorphic product of a conv 3x3, 16 -> 16 channels,
 32 x 32 input, pad 1, batch 64 (BFV N = 8192, three 60-bit primes, t = 2^41),
 seeded synthetic Gaussian fixed-point data (12 fractional bits).  One step =
-the whole forward path of Algorithm 1: encode_weights (pi_W + NTT) and
+the whole forward path of Algorithm 1: encode_weights (MO: pi_W + NTT),
 he_linear_forward_prepare (MO: NTT(Delta <X>_0), mask s, NTT(Delta s), share
-s + b) on one stream while encrypt_share (DO: pi_v + BFV encryption) runs on
-another, then he_linear_forward_apply (MO: ct x pt multiply-accumulate with the
+s + b) and encrypt_share (DO: pi_v + BFV encryption) on three streams, then
+he_linear_forward_apply (MO: ct x pt multiply-accumulate with the
 add of <X>_0 and the re-mask fused) and decrypt_to_share (DO).  Metric:
 ct x pt products per second (whole job), plus the per-kernel roofline of the
 dominant kernel, an end-to-end number with host buffers, and the oracle timed
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--ntt-log-radix", type=int, default=0, help="force the NTT radix knob (4 or 5)")
     ap.add_argument("--mac-columns", type=int, default=-1,
                     help="force the MAC knob (0: shared-memory staged; 2, 4, 8: columns per thread)")
+    ap.add_argument("--mac-staging", type=int, default=-1,
+                    help="force the MAC staging knob (0: per-thread cp.async ring, 1: bulk copies by a producer warp)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
     ap.add_argument("--extras-only", action="store_true", help="run only the extra workloads (JSON line)")
     return ap.parse_args()
@@ -507,6 +509,8 @@ def run_ours(args):
         ctx.tune(he.TUNE_NTT_LOG_RADIX, args.ntt_log_radix)
     if args.mac_columns >= 0:
         ctx.tune(he.TUNE_MAC_COLUMNS, args.mac_columns)
+    if args.mac_staging >= 0:
+        ctx.tune(he.TUNE_MAC_STAGING, args.mac_staging)
     sk = ctx.keygen(1234 + rank)
     layer = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
                      LAYER["pad"])
@@ -536,20 +540,24 @@ def run_ours(args):
 
     ws_mo = plan.new_ws(S.ws_forward)
 
-    # The MO encodes its weights and prepares its ciphertext-independent terms
-    # (NTT(Delta <X>_0), the mask s and NTT(Delta s)) while the DO encrypts its
-    # share: independent parties, two streams forked and joined inside every step.
-    mo_stream = torch.cuda.Stream(device=dev)
-    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    # The MO encodes its weights and, independently, prepares its
+    # ciphertext-independent terms (the mask s, NTT(Delta <X>_0), NTT(Delta s))
+    # while the DO encrypts its share: three independent streams of work, forked
+    # from and joined back into the launch stream inside every step.
+    mo_enc, mo_prep = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    fork, join_enc, join_prep = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
 
     def step(i):
         fork.record(stream)
-        mo_stream.wait_event(fork)
-        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt, stream=mo_stream)
-        he.he_linear_forward_prepare(ctx, plan, d["x0"], d["bias"], 5000 + i, y0, ws_mo, stream=mo_stream)
-        join.record(mo_stream)
+        mo_enc.wait_event(fork)
+        mo_prep.wait_event(fork)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt, stream=mo_enc)
+        join_enc.record(mo_enc)
+        he.he_linear_forward_prepare(ctx, plan, d["x0"], d["bias"], 5000 + i, y0, ws_mo, stream=mo_prep)
+        join_prep.record(mo_prep)
         he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 1000 + i, ct_in, ws, stream=stream)
-        stream.wait_event(join)
+        stream.wait_event(join_enc)
+        stream.wait_event(join_prep)
         he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct_out, ws_mo, stream=stream)
         he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws, stream=stream)
 

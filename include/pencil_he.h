@@ -79,8 +79,12 @@ int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
  * PENCIL_TUNE_MAC_COLUMNS: output ciphertexts per thread of the ct x pt
  * multiply-accumulate reading operands straight from L2: 2, 4 or 8; or 0: the
  * shared-memory staged kernel (each CTA stages one input block of 32 slots for
- * a 64-pair output block; each operand word read once per CTA). */
-enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1 };
+ * a 64-pair output block; each operand word read once per CTA).
+ * PENCIL_TUNE_MAC_STAGING (columns 2, 4, 8): 0 = every thread copies its own
+ * operand words a few input blocks ahead (cp.async ring); 1 = one producer
+ * warp per CTA copies whole 1 KB operand rows with bulk asynchronous copies
+ * (cp.async.bulk + mbarrier), the other warps only multiply. */
+enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1, PENCIL_TUNE_MAC_STAGING = 2 };
 int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value);
 int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value);
 

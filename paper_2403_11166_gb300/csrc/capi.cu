@@ -318,6 +318,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     lc.nqtils = shoup(lc.nqtil, q);
   }
   d.mac_nt = 4;
+  d.mac_staging = 1;   // measured: bulk copies by a producer warp, 4 columns per thread
   d.mac_split = 1;
   for (int j = 0; j < d.L; ++j)
     if (qs[j] >= (1ull << 60) || d.limb[j].c60 >= (1ull << 28) || d.limb[j].c64 >= (1ull << 28)) d.mac_split = 0;
@@ -377,6 +378,11 @@ extern "C" int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value) {
     ctx->dev.mac_nt = value;
     return PENCIL_OK;
   }
+  if (knob == PENCIL_TUNE_MAC_STAGING) {
+    if (value != 0 && value != 1) return PENCIL_E_ARG;
+    ctx->dev.mac_staging = value;
+    return PENCIL_OK;
+  }
   return PENCIL_E_ARG;
 }
 
@@ -388,6 +394,10 @@ extern "C" int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* 
   }
   if (knob == PENCIL_TUNE_MAC_COLUMNS) {
     *value = ctx->dev.mac_nt;
+    return PENCIL_OK;
+  }
+  if (knob == PENCIL_TUNE_MAC_STAGING) {
+    *value = ctx->dev.mac_staging;
     return PENCIL_OK;
   }
   return PENCIL_E_ARG;

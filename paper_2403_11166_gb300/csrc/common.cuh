@@ -38,6 +38,7 @@ struct DevCtx {
   int* status;               // device status word (atomicOr of error bits)
   int mac_split;             // 1: every q_j < 2^60 with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
   int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
+  int mac_staging;           // operand staging of the split MAC: 0 per-thread cp.async ring, 1 bulk copies
 };
 
 // A strided view of a user tensor seen as (a, b, r, s) with spatial zero

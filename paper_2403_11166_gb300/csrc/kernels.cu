@@ -90,15 +90,15 @@ struct Acc3 {
   u64 s0, s1, s2;
 };
 
-// Four 32x32->64 multiply-adds with the 64-bit accumulate fused into each
-// multiply (mad.wide.u32), so no separate 64-bit additions are issued.
+// Four 32x32->64 multiply-adds, each with its 64-bit accumulate fused into the
+// multiply (one mad.wide.u32 each).  Written as plain expressions so that the
+// compiler interleaves the partial products of different accumulators (the two
+// S1 terms of one product depend on each other).
 __device__ __forceinline__ void mac_split(Acc3& a, u32 aL, u32 aH, u32 bL, u32 bH) {
-  asm("mad.wide.u32 %0, %3, %5, %0;\n\t"
-      "mad.wide.u32 %1, %4, %5, %1;\n\t"
-      "mad.wide.u32 %1, %3, %6, %1;\n\t"
-      "mad.wide.u32 %2, %4, %6, %2;"
-      : "+l"(a.s0), "+l"(a.s1), "+l"(a.s2)
-      : "r"(aL), "r"(aH), "r"(bL), "r"(bH));
+  a.s0 += (u64)aL * bL;
+  a.s1 += (u64)aH * bL;
+  a.s2 += (u64)aH * bH;
+  a.s1 += (u64)aL * bH;
 }
 
 __device__ __forceinline__ void fold3(Acc3& a, u64 c60, u64 c64) {
@@ -253,7 +253,7 @@ __device__ __forceinline__ void mac_split_tile(const DevCtx& ctx, const MacParam
 }
 
 template <int NT, bool DUAL>
-__global__ void __launch_bounds__(128, (NT == 4 && !DUAL) ? 6 : 0) k_mac_split(DevCtx ctx, MacParams P) {
+__global__ void __launch_bounds__(128, (NT == 4 && !DUAL) ? 6 : 0) k_mac_ring(DevCtx ctx, MacParams P) {
   extern __shared__ u64 ring[];
   const int ntiles = (P.NC + NT - 1) / NT;
   const int m = blockIdx.x / ntiles + P.m_base;
@@ -261,6 +261,182 @@ __global__ void __launch_bounds__(128, (NT == 4 && !DUAL) ? 6 : 0) k_mac_split(D
   const int lane = blockIdx.y * blockDim.x + threadIdx.x;
   if (lane >= P.lanes || m >= P.M) return;
   mac_split_tile<NT, DUAL>(ctx, P, m, n0, lane, ring, threadIdx.x);
+}
+
+// ------------------------------------------------------------------ MAC, bulk-copy staged
+// CTA = MAC_BT consecutive slots of one output tile (m, n0 .. n0 + NT - 1).  For
+// every input block k, thread 0 copies the tile's operand rows (a0, a1, then
+// NTT(Delta x0) for Alg. 1 or A' for Alg. 2, B[NT], Alg. 2: B'0[NT], B'1[NT];
+// MAC_BT words = 1 KB each) from global memory into a ring of MAC_BSTAGES
+// shared-memory stages with bulk asynchronous copies (cp.async.bulk, completion
+// counted in bytes on one mbarrier per stage), MAC_BSTAGES - 1 blocks ahead of
+// the multiply; every thread then reads its own slot's words.  The barrier of
+// block k also frees the stage read in block k - 1 for the next copy.  A wait on
+// an mbarrier gives up after MAC_WAIT_LIMIT polls: the CTA then sets the timeout
+// bit of the status word, lets its issued copies land (bounded the same way) and
+// returns.
+#define MAC_BT 128
+#define MAC_BSTAGES 4
+#define MAC_WAIT_LIMIT (1 << 22)
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u32 bar, u32 parity) {
+  u32 done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(u32 bar, u32 parity) {
+  for (int i = 0; i < MAC_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// 16-byte aligned global source and shared destination, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(u32 dst, const void* src, u32 bytes, u32 bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u32 bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-specialised: warps 0 .. MAC_BT/32 - 1 multiply (thread = slot), the last
+// warp's lane 0 produces.  full[s] completes when stage s holds its block (byte
+// count), empty[s] when the MAC_BT/32 consumer warps have finished reading it.
+template <int NT, bool DUAL>
+__global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams P) {
+  constexpr int W = MacRing<NT, DUAL>::W;   // rows per stage
+  constexpr u32 ROW = MAC_BT * sizeof(u64);
+  constexpr int CONSUMER_WARPS = MAC_BT / 32;
+  extern __shared__ __align__(128) u64 ring[];   // [MAC_BSTAGES][W][MAC_BT]
+  __shared__ __align__(8) u64 full[MAC_BSTAGES], empty[MAC_BSTAGES];
+  const int ntiles = (P.NC + NT - 1) / NT;
+  const int m = blockIdx.x / ntiles + P.m_base;
+  const int n0 = (blockIdx.x % ntiles) * NT;
+  const int lane0 = blockIdx.y * MAC_BT;
+  const int tid = threadIdx.x;
+  if (m >= P.M) return;   // whole CTA
+  const int nn = min(NT, P.NC - n0);
+  if (tid == 0) {
+#pragma unroll
+    for (int st = 0; st < MAC_BSTAGES; ++st) {
+      mbar_init(smem_u32(&full[st]), 1);
+      mbar_init(smem_u32(&empty[st]), CONSUMER_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid >= MAC_BT) {   // producer warp
+    if (tid != MAC_BT) return;
+    const bool has_p = DUAL || P.p0 != nullptr;
+    const u32 stage_bytes = (u32)(has_p ? W : W - 1) * ROW;
+    int k = 0;
+    for (; k < P.K; ++k) {
+      const int st = k % MAC_BSTAGES;
+      if (k >= MAC_BSTAGES && !mbar_wait_bounded(smem_u32(&empty[st]), (u32)(k / MAC_BSTAGES - 1) & 1u)) break;
+      const u32 bar = smem_u32(&full[st]);
+      const u32 dst = smem_u32(ring + (size_t)st * W * MAC_BT);
+      mbar_expect_tx(bar, stage_bytes);
+      const size_t mk = (size_t)m * P.K + k;
+      bulk_g2s(dst, P.a0 + mk * P.a0_stride + lane0, ROW, bar);
+      bulk_g2s(dst + ROW, P.a1 + mk * P.a1_stride + lane0, ROW, bar);
+      if (DUAL)
+        bulk_g2s(dst + 2 * ROW, P.pa + mk * P.pa_stride + lane0, ROW, bar);
+      else if (P.p0)
+        bulk_g2s(dst + 2 * ROW, P.p0 + mk * P.p0_stride + lane0, ROW, bar);
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const size_t kn = (size_t)k * P.NC + n0 + (j < nn ? j : 0);
+        bulk_g2s(dst + (3 + j) * ROW, P.b + kn * P.b_stride + lane0, ROW, bar);
+        if (DUAL) {
+          bulk_g2s(dst + (3 + NT + j) * ROW, P.cb0 + kn * P.cb_stride + lane0, ROW, bar);
+          bulk_g2s(dst + (3 + 2 * NT + j) * ROW, P.cb1 + kn * P.cb_stride + lane0, ROW, bar);
+        }
+      }
+    }
+    if (k < P.K) {   // consumers stopped releasing stages: record it, let the issued copies land
+      atomicOr(ctx.status, 2);
+      for (int kk = max(0, k - MAC_BSTAGES); kk < k; ++kk)
+        mbar_wait_bounded(smem_u32(&full[kk % MAC_BSTAGES]), (u32)(kk / MAC_BSTAGES) & 1u);
+    }
+    return;
+  }
+  const int lane = lane0 + tid;
+  const LimbConst& lc = ctx.limb[lane >> ctx.log_n];
+  const u64 c60 = lc.c60, c64 = lc.c64;
+  constexpr u32 M30 = (1u << 30) - 1;
+  constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
+  Acc3 acc[NT][2];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = Acc3{0, 0, 0};
+  for (int k = 0; k < P.K; ++k) {
+    const int st = k % MAC_BSTAGES;
+    const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u32)(k / MAC_BSTAGES) & 1u);
+    if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform give-up
+      if ((tid & 31) == 0) atomicOr(ctx.status, 2);   // the producer then times out on this warp's stages
+      return;
+    }
+    const u64* cur = ring + (size_t)st * W * MAC_BT + tid;
+    u64 a0 = cur[0];
+    if (!DUAL && P.p0) a0 = add_mod(a0, cur[2 * MAC_BT], lc.q);   // Alg. 1 step 2: + NTT(Delta x0)
+    const u64 a1 = cur[MAC_BT];
+    u64 pa = 0, bw[NT], c0w[DUAL ? NT : 1], c1w[DUAL ? NT : 1];
+    if constexpr (DUAL) pa = cur[2 * MAC_BT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      bw[j] = cur[(3 + j) * MAC_BT];
+      if constexpr (DUAL) {
+        c0w[j] = cur[(3 + NT + j) * MAC_BT];
+        c1w[j] = cur[(3 + 2 * NT + j) * MAC_BT];
+      }
+    }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
+    const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
+    const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
+    const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const u32 bL = (u32)bw[j] & M30, bH = (u32)(bw[j] >> 30);
+      mac_split(acc[j][0], a0L, a0H, bL, bH);
+      mac_split(acc[j][1], a1L, a1H, bL, bH);
+      if constexpr (DUAL) {
+        mac_split(acc[j][0], (u32)c0w[j] & M30, (u32)(c0w[j] >> 30), pL, pH);
+        mac_split(acc[j][1], (u32)c1w[j] & M30, (u32)(c1w[j] >> 30), pL, pH);
+      }
+    }
+    if ((k % FOLD) == FOLD - 1) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        fold3(acc[j][0], c60, c64);
+        fold3(acc[j][1], c60, c64);
+      }
+    }
+  }
+  const size_t ln = (size_t)P.lanes;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (j < nn) {
+      const size_t mn = (size_t)m * P.NC + n0 + j, o = mn * 2 * ln + lane;
+      u64 v0 = acc3_value(acc[j][0], lc);
+      if (P.mask) v0 = sub_mod(v0, __ldg(P.mask + mn * ln + lane), lc.q);
+      P.out[o] = v0;
+      P.out[o + ln] = acc3_value(acc[j][1], lc);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ MAC, shared-memory staged
@@ -440,16 +616,16 @@ static cudaError_t launch_mac_smem(const DevCtx& ctx, const MacParams& P0, bool 
 }
 
 template <int NT>
-static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+static cudaError_t launch_mac_ring(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
   const int threads = 128;
   MacParams P = P0;
   const int ntiles = (P.NC + NT - 1) / NT;
   const unsigned gy = (unsigned)((P.lanes + threads - 1) / threads);
   const int mchunk = max(1, 2147483647 / max(1, ntiles));
   const size_t smem = dual ? MacRing<NT, true>::bytes(threads) : MacRing<NT, false>::bytes(threads);
-  cudaError_t e0 = dual ? cudaFuncSetAttribute(k_mac_split<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e0 = dual ? cudaFuncSetAttribute(k_mac_ring<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem)
-                        : cudaFuncSetAttribute(k_mac_split<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                        : cudaFuncSetAttribute(k_mac_ring<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
   if (e0 != cudaSuccess) return e0;
   for (int base = 0; base < P0.M; base += mchunk) {
@@ -457,25 +633,60 @@ static cudaError_t launch_mac_split(const DevCtx& ctx, const MacParams& P0, bool
     const int mc = min(mchunk, P0.M - base);
     dim3 grid((unsigned)(mc * ntiles), gy);
     if (dual)
-      k_mac_split<NT, true><<<grid, threads, smem, s>>>(ctx, P);
+      k_mac_ring<NT, true><<<grid, threads, smem, s>>>(ctx, P);
     else
-      k_mac_split<NT, false><<<grid, threads, smem, s>>>(ctx, P);
+      k_mac_ring<NT, false><<<grid, threads, smem, s>>>(ctx, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+template <int NT>
+static cudaError_t launch_mac_bulk(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
+  if (P0.lanes % MAC_BT) return cudaErrorInvalidValue;   // L N is a multiple of 4096
+  MacParams P = P0;
+  const int ntiles = (P.NC + NT - 1) / NT;
+  const unsigned gy = (unsigned)(P.lanes / MAC_BT);
+  const int mchunk = max(1, 2147483647 / max(1, ntiles));
+  const size_t smem = (size_t)MAC_BSTAGES * (dual ? MacRing<NT, true>::W : MacRing<NT, false>::W) * MAC_BT *
+                      sizeof(u64);
+  const void* fn = dual ? (const void*)k_mac_bulk<NT, true> : (const void*)k_mac_bulk<NT, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int base = 0; base < P0.M; base += mchunk) {
+    P.m_base = base;
+    const int mc = min(mchunk, P0.M - base);
+    dim3 grid((unsigned)(mc * ntiles), gy);
+    if (dual)
+      k_mac_bulk<NT, true><<<grid, MAC_BT + 32, smem, s>>>(ctx, P);
+    else
+      k_mac_bulk<NT, false><<<grid, MAC_BT + 32, smem, s>>>(ctx, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaStream_t s) {
   if (ctx.mac_split && ctx.mac_nt == 0) return launch_mac_smem(ctx, P0, dual, s);
+  if (ctx.mac_split && ctx.mac_staging == 1) {
+    switch (ctx.mac_nt) {
+      case 2:
+        return launch_mac_bulk<2>(ctx, P0, dual, s);
+      case 8:
+        return launch_mac_bulk<8>(ctx, P0, dual, s);
+      default:
+        return launch_mac_bulk<4>(ctx, P0, dual, s);
+    }
+  }
   if (ctx.mac_split) {
     switch (ctx.mac_nt) {
       case 2:
-        return launch_mac_split<2>(ctx, P0, dual, s);
+        return launch_mac_ring<2>(ctx, P0, dual, s);
       case 8:
-        return launch_mac_split<8>(ctx, P0, dual, s);
+        return launch_mac_ring<8>(ctx, P0, dual, s);
       default:
-        return launch_mac_split<4>(ctx, P0, dual, s);
+        return launch_mac_ring<4>(ctx, P0, dual, s);
     }
   }
   constexpr int NT = 8;

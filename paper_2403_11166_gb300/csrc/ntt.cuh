@@ -156,9 +156,10 @@ __device__ __forceinline__ void ntt_fwd_run(const DevCtx& ctx, const typename Mo
   const ulonglong2* tw = ctx.tw_fwd + (size_t)limb * C::N;
   u64 v[C::E];
   if constexpr (Mode::kHeavyLoad) {
-    // Long prologue (gathers, multiplies): a short loop through shared memory
-    // keeps the code small; each thread re-reads only the slots it wrote.
-#pragma unroll 4
+    // Long prologue (gathers, multiplies): a loop through shared memory bounds
+    // the code size (kLoadUnroll iterations in flight); each thread re-reads
+    // only the slots it wrote.
+#pragma unroll(Mode::kLoadUnroll)
     for (int l = 0; l < C::E; ++l) {
       const int e = tau + l * C::T;
       sm[sidx<LOGN>(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
@@ -191,7 +192,7 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   const u64 q = lc.q, q2 = 2 * q;
   const ulonglong2* tw = ctx.tw_inv + (size_t)limb * C::N;
   u64 v[C::E];
-#pragma unroll(Mode::kHeavyLoad ? 4 : C::E)
+#pragma unroll(Mode::kLoadUnroll)
   for (int l = 0; l < C::E; ++l) {
     const int e = tau + l * C::T;
     sm[sidx<LOGN>(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
@@ -253,6 +254,7 @@ __device__ __forceinline__ size_t ct_off(int poly, int comp, int limb, int L, in
 // In-place transform of [count][L][N] polynomials.
 struct ModeRaw {
   static constexpr bool kHeavyLoad = false;
+  static constexpr int kLoadUnroll = 32;
   static constexpr int kEpilogueUnroll = 16;
   struct Params {
     u64* polys;
@@ -279,6 +281,7 @@ struct ModeRaw {
 // c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain.
 struct ModeEncrypt {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 8;
   static constexpr int kEpilogueUnroll = 1;   // Philox + two reductions per pair
   struct Params {
     Packing pk;
@@ -316,6 +319,7 @@ struct ModeEncrypt {
 // MO add_plain (Alg. 1 step 2): out_c0 = ct_in.c0 + NTT(Delta * pi_v(x0)).
 struct ModeAddPlain {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
     Packing pk;
@@ -342,6 +346,7 @@ struct ModeAddPlain {
 // MO plaintext encoding: centred lift of Z_t values, NTT.
 struct ModeEncode {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
     Packing pk;
@@ -366,6 +371,7 @@ struct ModeEncode {
 // MO re-mask (Alg. 1 step 3): ct_out.c0 -= NTT(Delta * s).
 struct ModeMask {
   static constexpr bool kHeavyLoad = false;
+  static constexpr int kLoadUnroll = 32;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
     const u64* mpoly;   // [count][N] Z_t mask coefficients
@@ -392,6 +398,7 @@ struct ModeMask {
 // polynomials (subtracted by the multiply-accumulate's store).
 struct ModeMoPrep {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 8;
   struct Params {
     Packing pk;
@@ -425,6 +432,7 @@ __device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
 // DO key generation: ternary s, NTT, stored with Shoup companions.
 struct ModeKeygen {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 4;
   static constexpr int kEpilogueUnroll = 1;
   struct Params {
     u64 seed;
@@ -449,6 +457,7 @@ struct ModeKeygen {
 // (the INTT's N^{-1} and qtilde are one constant).
 struct ModeDecrypt {
   static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 8;
   static constexpr int kEpilogueUnroll = 16;
   struct Params {
     const u64* ct;          // [count][2][L][N]

@@ -148,13 +148,19 @@ def test_dgrad_small(he, L, part, cfg):
     check_forward(he, cfg, L, DGRAD, part, 11, sample_in=[1], sample_pt=[1], sample_out=[0, 1], with_bias=False)
 
 
-@pytest.mark.parametrize("L,part", [
-    (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (2, 1, 3, 3, 3, 3, 2)),
-    (Layer("fc", B=5, Ci=20, Co=7), (3, 2, 4, 1, 1, 1, 1)),
+@pytest.mark.parametrize("L,part,knobs", [
+    (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (2, 1, 3, 3, 3, 3, 2), None),
+    (Layer("fc", B=5, Ci=20, Co=7), (3, 2, 4, 1, 1, 1, 1), None),
+    (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (2, 1, 3, 3, 3, 3, 2), (8, 1)),
+    (Layer("fc", B=5, Ci=20, Co=7), (3, 2, 4, 1, 1, 1, 1), (4, 1)),
+    (Layer("fc", B=5, Ci=20, Co=7), (3, 2, 4, 1, 1, 1, 1), (0, 0)),
 ])
-def test_wgrad_small(he, L, part):
+def test_wgrad_small(he, L, part, knobs):
     cfg = (12, 3, 60)
     ctx = he.Context(*cfg)
+    if knobs is not None:   # (MAC columns, staging): the other multiply-accumulate forms of Alg. 2
+        ctx.tune(he.TUNE_MAC_COLUMNS, knobs[0])
+        ctx.tune(he.TUNE_MAC_STAGING, knobs[1])
     p = BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2])
     sk = ctx.keygen(5)
     osk = bfv.keygen(p, 5)
@@ -255,20 +261,23 @@ def test_host_validation(he):
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("radix,cols", [(4, 2), (5, 4), (4, 8), (5, 8), (5, 0), (4, 0)])
-def test_tuning_knobs_do_not_change_results(he, radix, cols):
+@pytest.mark.parametrize("radix,cols,staging", [(4, 2, 0), (5, 4, 0), (4, 8, 0), (5, 8, 0), (5, 0, 0), (4, 0, 0),
+                                                (4, 2, 1), (5, 4, 1), (4, 8, 1)])
+def test_tuning_knobs_do_not_change_results(he, radix, cols, staging):
     """Every NTT radix / MAC column setting gives bit-identical ciphertexts and shares
     (the default setting is checked against the oracle above)."""
     cfg = (13, 3, 60)
     L = Layer("conv", B=3, Ci=5, Co=7, h=9, w=8, s=3, pad=1)
     part = (1, 2, 3, 5, 4, 3, 3)
     outs = []
-    for setting in (None, (radix, cols)):
+    for setting in (None, (radix, cols, staging)):
         ctx = he.Context(*cfg)
         if setting:
             ctx.tune(he.TUNE_NTT_LOG_RADIX, setting[0])
             ctx.tune(he.TUNE_MAC_COLUMNS, setting[1])
+            ctx.tune(he.TUNE_MAC_STAGING, setting[2])
             assert ctx.get_tune(he.TUNE_MAC_COLUMNS) == setting[1]
+            assert ctx.get_tune(he.TUNE_MAC_STAGING) == setting[2]
         sk = ctx.keygen(5)
         g = inputs.rng(8)
         W = inputs.gaussian_fixed(g, L.w_shape())
@@ -278,8 +287,9 @@ def test_tuning_knobs_do_not_change_results(he, radix, cols):
         assert (a == b).all()
 
 
-@pytest.mark.parametrize("cfg,cols", [((12, 2, 54), None), ((13, 3, 60), 4), ((13, 3, 60), 0)])
-def test_prepare_apply_equals_forward(he, cfg, cols):
+@pytest.mark.parametrize("cfg,cols,staging", [((12, 2, 54), None, 0), ((13, 3, 60), 4, 0), ((13, 3, 60), 0, 0),
+                                              ((13, 3, 60), 8, 1)])
+def test_prepare_apply_equals_forward(he, cfg, cols, staging):
     """he_linear_forward_prepare on one stream, encrypt on another, then
     he_linear_forward_apply: ciphertexts and shares bit-identical to he_linear_forward
     (generic, split and shared-memory staged multiply-accumulate)."""
@@ -288,6 +298,7 @@ def test_prepare_apply_equals_forward(he, cfg, cols):
     ctx = he.Context(*cfg)
     if cols is not None:
         ctx.tune(he.TUNE_MAC_COLUMNS, cols)
+    ctx.tune(he.TUNE_MAC_STAGING, staging)
     sk = ctx.keygen(5)
     g = inputs.rng(8)
     W = inputs.gaussian_fixed(g, L.w_shape())
