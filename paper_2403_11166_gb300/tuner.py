@@ -1,7 +1,8 @@
 """Autotuner of the batched HE linear layers (measurement-driven).
 
-Search space: the two context knobs (NTT register-block radix 2^4 / 2^5 and
-output columns per thread of the multiply-accumulate: 2, 4, 8) and, per
+Search space: the context knobs (NTT register-block radix 2^4 / 2^5, output
+columns per thread of the multiply-accumulate: 2, 4, 8, and its operand
+staging: per-thread cp.async ring or producer-warp bulk copies) and, per
 distinct layer shape, the planner's cheapest-first partitions (tile shapes:
 batch / channel blocks and spatial tiles).  For every knob setting each shape's
 candidates are timed as a single layer (per-layer calls, CUDA events on the
@@ -114,34 +115,36 @@ class GraphBatch:
 
 
 def tune_batch(ctx: he.Context, sk: he.SecretKey, layers: List[he.Layer], topk: int = 3, reps: int = 3,
-               radices=(4, 5), columns=(2, 4, 8)) -> Dict:
-    """Returns {"ntt_log_radix", "mac_columns", "partitions" (per layer), "ms", "table"} and leaves
-    the context tuned to the winner."""
+               radices=(4, 5), columns=(2, 4, 8), stagings=(0, 1)) -> Dict:
+    """Returns {"ntt_log_radix", "mac_columns", "mac_staging", "partitions" (per layer), "ms", "table"}
+    and leaves the context tuned to the winner."""
     shapes: Dict[Tuple, he.Layer] = {}
     for L in layers:
         shapes.setdefault(_shape_key(L), L)
     table = []
     best = None
-    for radix, cols in itertools.product(radices, columns):
+    for radix, cols, staging in itertools.product(radices, columns, stagings):
         ctx.tune(he.TUNE_NTT_LOG_RADIX, radix)
         ctx.tune(he.TUNE_MAC_COLUMNS, cols)
+        ctx.tune(he.TUNE_MAC_STAGING, staging)
         chosen = {}
         for key, L in shapes.items():
             cands = he.plan_candidates(ctx, L, he.ROLE_FWD, topk)
             timed = [(time_layer(ctx, sk, L, c, reps), c) for c in cands]
             timed.sort()
             chosen[key] = timed[0][1]
-            table.append({"radix": radix, "columns": cols, "shape": key,
+            table.append({"radix": radix, "columns": cols, "staging": staging, "shape": key,
                           "candidates": [{"partition": c, "ms": round(t, 4)} for t, c in timed]})
         gb = GraphBatch(ctx, sk, layers, [chosen[_shape_key(L)] for L in layers])
         ms = gb.time(reps)
         del gb
         torch.cuda.empty_cache()
-        table.append({"radix": radix, "columns": cols, "batch_graph_ms": round(ms, 4)})
+        table.append({"radix": radix, "columns": cols, "staging": staging, "batch_graph_ms": round(ms, 4)})
         if best is None or ms < best["ms"]:
-            best = {"ntt_log_radix": radix, "mac_columns": cols,
+            best = {"ntt_log_radix": radix, "mac_columns": cols, "mac_staging": staging,
                     "partitions": [chosen[_shape_key(L)] for L in layers], "ms": ms}
     ctx.tune(he.TUNE_NTT_LOG_RADIX, best["ntt_log_radix"])
     ctx.tune(he.TUNE_MAC_COLUMNS, best["mac_columns"])
+    ctx.tune(he.TUNE_MAC_STAGING, best["mac_staging"])
     best["table"] = table
     return best

@@ -139,8 +139,9 @@ def test_autotuner_choice_keeps_results(he):
     ctx = he.Context(13, 3, 60)
     sk = ctx.keygen(6)
     layers = [he.Layer(he.FC, 8, 96, 12), he.Layer(he.CONV, 2, 8, 6, 6, 6, 3, 1)]
-    best = tuner.tune_batch(ctx, sk, layers, topk=2, reps=1, radices=(4, 5), columns=(2, 8))
-    assert best["ntt_log_radix"] in (4, 5) and best["mac_columns"] in (2, 8)
+    best = tuner.tune_batch(ctx, sk, layers, topk=2, reps=1, radices=(4, 5), columns=(2, 8), stagings=(0, 1))
+    assert best["ntt_log_radix"] in (4, 5) and best["mac_columns"] in (2, 8) and best["mac_staging"] in (0, 1)
+    assert ctx.get_tune(he.TUNE_MAC_STAGING) == best["mac_staging"]
     assert ctx.get_tune(he.TUNE_MAC_COLUMNS) == best["mac_columns"]
     gb = tuner.GraphBatch(ctx, sk, layers, best["partitions"], capture=False)
     gb.batch.set_step(0)
