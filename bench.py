@@ -4,11 +4,12 @@
 Workload: the forward homomorphic product of a conv 3x3, 16 -> 16 channels,
 32 x 32 input, pad 1, batch 64 (BFV N = 8192, three 60-bit primes, t = 2^41),
 seeded synthetic Gaussian fixed-point data (12 fractional bits).  One step =
-the whole forward path of Algorithm 1: encode_weights (MO: pi_W + NTT),
+the whole forward path of Algorithm 1: encode_weights (MO: pi_W + NTT) and
 he_linear_forward_prepare (MO: NTT(Delta <X>_0), mask s, NTT(Delta s), share
-s + b) and encrypt_share (DO: pi_v + BFV encryption) on three streams, then
-he_linear_forward_apply (MO: ct x pt multiply-accumulate with the
-add of <X>_0 and the re-mask fused) and decrypt_to_share (DO).  Metric:
+s + b) on their own streams, and the layer streamed in row slices through
+encrypt_share (DO: pi_v + BFV encryption), he_linear_forward_apply (MO: ct x pt
+multiply-accumulate with the add of <X>_0 and the re-mask fused) and
+decrypt_to_share (DO), each slice's stages overlapping the neighbours'.  Metric:
 ct x pt products per second (whole job), plus the per-kernel roofline of the
 dominant kernel, an end-to-end number with host buffers, and the oracle timed
 on the host cores.
@@ -58,6 +59,8 @@ def parse():
                     help="force the MAC knob (0: shared-memory staged; 2, 4, 8: columns per thread)")
     ap.add_argument("--mac-staging", type=int, default=-1,
                     help="force the MAC staging knob (0: per-thread cp.async ring, 1: bulk copies by a producer warp)")
+    ap.add_argument("--chunks", type=int, default=1,
+                    help="stream the layer through encrypt / multiply-accumulate / decrypt in this many row slices")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
     ap.add_argument("--extras-only", action="store_true", help="run only the extra workloads (JSON line)")
     return ap.parse_args()
@@ -563,13 +566,21 @@ def run_ours(args):
 
     host = {"W": to_i64(W).pin_memory(), "x0": to_i64(x0).pin_memory(), "x1": to_i64(x1).pin_memory(),
             "bias": to_i64(bias.astype(np.uint64) & np.uint64((1 << T_BITS) - 1)).pin_memory()}
-    d = {k: v.to(dev) for k, v in host.items()}
+    # two sets of per-step inputs and outputs: the end-to-end loop copies the next
+    # step's inputs in and the previous step's shares out while a step computes
+    sets = []
+    for _ in range(2):
+        b = {k: v.to(dev) for k, v in host.items()}
+        b["y0"] = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
+        b["y1"] = torch.empty_like(b["y0"])
+        sets.append(b)
+    d = sets[0]
+    y0, y1 = d["y0"], d["y1"]
     pt = plan.new_pt(S.pt)
     ct_in = plan.new_ct(S.ct_in)
     ct_out = plan.new_ct(S.ct_out)
-    y0 = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
-    y1 = torch.empty_like(y0)
-    ws = plan.new_ws(max(S.ws_encrypt, S.ws_decrypt))
+    ws = plan.new_ws(S.ws_encrypt)
+    ws_dec = plan.new_ws(S.ws_decrypt)
     hy0 = torch.empty(S.out_elems, dtype=torch.int64).pin_memory()
     hy1 = torch.empty_like(hy0).pin_memory()
 
@@ -577,24 +588,45 @@ def run_ours(args):
 
     # The MO encodes its weights and, independently, prepares its
     # ciphertext-independent terms (the mask s, NTT(Delta <X>_0), NTT(Delta s))
-    # while the DO encrypts its share: three independent streams of work, forked
-    # from and joined back into the launch stream inside every step.
-    mo_enc, mo_prep = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    # while the DO encrypts its share.  The layer then streams through the rest
+    # of the protocol in `chunks` slices of its output rows (batch blocks): the
+    # MO's multiply-accumulate of slice c overlaps the DO's encryption of slice
+    # c + 1 and the DO's decryption of slice c - 1.  Streams fork from and join
+    # back into the launch stream inside every step.
+    M_rows = plan.rows
+    nch = max(1, min(args.chunks, M_rows))
+    bounds = [M_rows * c // nch for c in range(nch + 1)]
+    slices = [plan.slice(bounds[c], bounds[c + 1] - bounds[c]) for c in range(nch)] if nch > 1 else [plan]
+    mo_enc, mo_prep, mo_app = (torch.cuda.Stream(device=dev) for _ in range(3))
+    do_dec = torch.cuda.Stream(device=dev)
     fork, join_enc, join_prep = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    ev_ct = [torch.cuda.Event() for _ in slices]
+    ev_out = [torch.cuda.Event() for _ in slices]
+    join_app, join_dec = torch.cuda.Event(), torch.cuda.Event()
 
-    def step(i):
+    def step(i, b=None):
+        b = d if b is None else b
         fork.record(stream)
-        mo_enc.wait_event(fork)
-        mo_prep.wait_event(fork)
-        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, d["W"], pt, stream=mo_enc)
+        for st in (mo_enc, mo_prep, mo_app, do_dec):
+            st.wait_event(fork)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, b["W"], pt, stream=mo_enc)
         join_enc.record(mo_enc)
-        he.he_linear_forward_prepare(ctx, plan, d["x0"], d["bias"], 5000 + i, y0, ws_mo, stream=mo_prep)
+        he.he_linear_forward_prepare(ctx, plan, b["x0"], b["bias"], 5000 + i, b["y0"], ws_mo, stream=mo_prep)
         join_prep.record(mo_prep)
-        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 1000 + i, ct_in, ws, stream=stream)
-        stream.wait_event(join_enc)
-        stream.wait_event(join_prep)
-        he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct_out, ws_mo, stream=stream)
-        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws, stream=stream)
+        for c, sl in enumerate(slices):            # DO: encrypt slice by slice
+            he.encrypt_share(ctx, sk, sl, he.OPERAND_INPUT, b["x1"], 1000 + i, ct_in, ws, stream=stream)
+            ev_ct[c].record(stream)
+        mo_app.wait_event(join_enc)
+        mo_app.wait_event(join_prep)
+        for c, sl in enumerate(slices):            # MO: multiply-accumulate each slice as it arrives
+            mo_app.wait_event(ev_ct[c])
+            he.he_linear_forward_apply(ctx, sl, ct_in, pt, ct_out, ws_mo, stream=mo_app)
+            ev_out[c].record(mo_app)
+        for c, sl in enumerate(slices):            # DO: decrypt each slice as it comes back
+            do_dec.wait_event(ev_out[c])
+            he.decrypt_to_share(ctx, sk, sl, ct_out, b["y1"], False, ws_dec, stream=do_dec)
+        join_dec.record(do_dec)
+        stream.wait_event(join_dec)
 
     for i in range(args.warmup):
         step(i)
@@ -643,22 +675,47 @@ def run_ours(args):
         he.he_linear_forward_prepare(ctx, plan, d["x0"], d["bias"], 7000 + i, y0, ws_mo, stream=stream)
         he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, d["x1"], 3000 + i, ct_in, ws, stream=stream)
         he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct_out, ws_mo, stream=stream)
-        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws, stream=stream)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws_dec, stream=stream)
     torch.cuda.synchronize()
     ctx.profile(False)
     serial = ctx.profile_read()
-    # ---- end to end: host buffers, H2D of the step's inputs and D2H of the shares inside the region
+    # ---- end to end: host buffers; every step's inputs are copied in from pinned
+    # host memory and both shares copied back inside the region, on a copy stream
+    # (double-buffered: step i + 1's inputs go in and step i - 1's shares come out
+    # while step i computes)
     h2d = sum(v.numel() * 8 for v in host.values())
     d2h = 2 * S.out_elems * 8
+    copy = torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_copied = torch.cuda.Event()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
+    copy.wait_event(f0)
+
+    def h2d_into(b):
+        with torch.cuda.stream(copy):
+            for k in host:
+                sets[b][k].copy_(host[k], non_blocking=True)
+        ev_in[b].record(copy)
+
+    h2d_into(0)
     for i in range(args.steps):
-        for k in host:
-            d[k].copy_(host[k], non_blocking=True)
-        step(10_000 + i)
-        hy0.copy_(y0, non_blocking=True)
-        hy1.copy_(y1, non_blocking=True)
+        b = i % 2
+        if i + 1 < args.steps:
+            if i >= 1:
+                copy.wait_event(ev_done[1 - b])   # step i - 1 has finished with that set
+            h2d_into(1 - b)
+        stream.wait_event(ev_in[b])
+        step(10_000 + i, sets[b])
+        ev_done[b].record(stream)
+        copy.wait_event(ev_done[b])
+        with torch.cuda.stream(copy):
+            hy0.copy_(sets[b]["y0"], non_blocking=True)
+            hy1.copy_(sets[b]["y1"], non_blocking=True)
+    ev_copied.record(copy)
+    stream.wait_event(ev_copied)
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
@@ -682,7 +739,8 @@ def run_ours(args):
                                                             plan.part)),
                    "ct_in": S.ct_in, "pt": S.pt, "ct_out": S.ct_out, "products_per_step": S.products,
                    "l2": "inputs larger than L2 (ct_in %.0f MB per step)" % (S.ct_in * S.ct_words * 8 / 1e6),
-                   "parallelism": f"replicas x{world} (independent layers, no collective)"},
+                   "parallelism": f"replicas x{world} (independent layers, no collective)",
+                   "streamed_slices": nch},
         "parity_selfcheck": parity_ok,
         "roofline": roof,
         "kernels": table,

@@ -152,6 +152,28 @@ typedef struct {
 int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, int32_t role,
                        const PencilPartition* part, PencilPlan** out);
 int pencil_plan_destroy(PencilPlan* plan);
+
+/* A slice of a FWD or DGRAD plan over the output rows m in [m_first, m_first +
+ * m_count) of its partition (m = batch block x spatial tile, the row index of
+ * ct_in[m * K + k] and ct_out[m * NC + n]), for streaming a layer through the
+ * protocol block by block (no counterpart in the paper, which describes whole
+ * layers).  A slice shares its parent's tables (destroy it before the parent)
+ * and takes the parent's full-size buffers and workspaces (pencil_plan_sizes
+ * reports the parent's sizes); with it, encrypt_share (INPUT) and
+ * encode_weights (INPUT) touch only input polynomials [m_first K, (m_first +
+ * m_count) K), he_linear_forward_apply only output polynomials [m_first NC,
+ * (m_first + m_count) NC), decrypt_to_share only those outputs (and the share
+ * elements they carry); he_linear_forward_prepare always prepares the whole
+ * layer.  Every polynomial is bit-identical to the whole-plan call's.  Calls on
+ * disjoint slices may run concurrently on different streams: concurrent
+ * encryptions may share one workspace, concurrent decryptions another, but an
+ * encryption and a decryption that may overlap need separate workspaces (both
+ * use theirs from offset 0).
+ * encrypt_share (KERNEL), encrypt_share_noalloc, he_linear_backward and the
+ * batch API take whole plans only (PENCIL_E_ARG).  Errors: PENCIL_E_ARG for a
+ * WGRAD plan or a slice of a slice, PENCIL_E_SHAPE for an empty or
+ * out-of-range row range. */
+int pencil_plan_slice(const PencilPlan* plan, int32_t m_first, int32_t m_count, PencilPlan** out);
 /* Up to max_count distinct partitions of `role` of `layer`, cheapest first by
  * the planner's cost model (the first is the planner's own choice); the
  * autotuner times them.  Host only. */

@@ -192,6 +192,15 @@ struct PencilPlan {
   int4* d_org = nullptr;         // origins: v [ct_in], w [pt], y [ct_out]
   Packing pk_v, pk_w, pk_y;
   long long ws_encrypt, ws_forward, ws_backward, ws_decrypt;
+  // A slice (pencil_plan_slice) covers output rows m in [m_first, m_first + m_count)
+  // of its parent and shares the parent's tables; a full plan covers [0, M).
+  long long m_first = 0, m_count = 0;
+  const PencilPlan* parent = nullptr;
+  // input polynomials [in_first, in_first + in_count), output [out_first, out_first + out_count)
+  long long in_first() const { return m_first * c.K(); }
+  long long in_count() const { return m_count * c.K(); }
+  long long out_first() const { return m_first * c.NC; }
+  long long out_count() const { return m_count * c.NC; }
 };
 
 static int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -732,7 +741,23 @@ extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, 
   else
     P->ws_backward = P->ws_forward;
   P->ws_decrypt = al(P->ct_out * lnb);
+  P->m_first = 0;
+  P->m_count = P->c.M();
   *out = P;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_plan_slice(const PencilPlan* plan, int32_t m_first, int32_t m_count, PencilPlan** out) {
+  if (!plan || !out) return PENCIL_E_ARG;
+  *out = nullptr;
+  if (plan->parent || plan->role == PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  if (m_first < 0 || m_count < 1 || (long long)m_first + m_count > plan->c.M()) return PENCIL_E_SHAPE;
+  PencilPlan* S = new (std::nothrow) PencilPlan(*plan);
+  if (!S) return PENCIL_E_CUDA;
+  S->parent = plan;
+  S->m_first = m_first;
+  S->m_count = m_count;
+  *out = S;
   return PENCIL_OK;
 }
 
@@ -777,9 +802,11 @@ extern "C" int pencil_plan_candidates(PencilCtx* ctx, const PencilLayerDesc* lay
 
 extern "C" int pencil_plan_destroy(PencilPlan* P) {
   if (!P) return PENCIL_E_ARG;
-  DeviceGuard guard(P->ctx->device);
-  cudaFree(P->d_tab);
-  cudaFree(P->d_org);
+  if (!P->parent) {   // a slice does not own the tables
+    DeviceGuard guard(P->ctx->device);
+    cudaFree(P->d_tab);
+    cudaFree(P->d_org);
+  }
   delete P;
   return PENCIL_OK;
 }
@@ -813,10 +840,11 @@ extern "C" int encode_weights(PencilCtx* ctx, const PencilPlan* P, int32_t opera
   M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
   M.ac.ptr = reinterpret_cast<const u64*>(values);
   M.pt = pt;
-  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
+  const long long first = operand == PENCIL_OPERAND_KERNEL ? 0 : P->in_first();
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->in_count();
   {
     PROF(ctx, PENCIL_K_NTT_ENCODE, (cudaStream_t)stream);
-    CUDA_TRY((ntt<ModeEncode, false>(ctx->dev, M, (int)count, (cudaStream_t)stream)));
+    CUDA_TRY((ntt<ModeEncode, false>(ctx->dev, M, (int)count, (cudaStream_t)stream, (int)first)));
   }
   return PENCIL_OK;
 }
@@ -830,11 +858,13 @@ extern "C" int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const Pe
   if ((long long)ws_bytes < P->ws_encrypt) return PENCIL_E_CAPACITY;
   DeviceGuard guard(ctx->device);
   const cudaStream_t s = (cudaStream_t)stream;
-  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
+  if (operand == PENCIL_OPERAND_KERNEL && P->parent) return PENCIL_E_ARG;   // slices cover input / output rows
+  const long long first = operand == PENCIL_OPERAND_KERNEL ? 0 : P->in_first();
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->in_count();
   int8_t* err = reinterpret_cast<int8_t*>(ws);
   {
     PROF(ctx, PENCIL_K_SAMPLE_ERR, s);
-    CUDA_TRY(launch_sample_err(seed, (int)count, ctx->n, err, s));
+    CUDA_TRY(launch_sample_err(seed, (int)first, (int)count, ctx->n, err, s));
   }
   ModeEncrypt::Params M;
   M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
@@ -846,7 +876,7 @@ extern "C" int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const Pe
   M.seed = seed;
   {
     PROF(ctx, PENCIL_K_NTT_ENCRYPT, s);
-    CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+    CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s, (int)first)));
   }
   return PENCIL_OK;
 }
@@ -913,7 +943,8 @@ static int alg1_apply(PencilCtx* ctx, const PencilPlan* P, const u64* ct_in, con
   M.b_stride = lnw;
   M.mask = w.mnt;
   M.out = ct_out;
-  M.M = (int)P->c.M();
+  M.m_base = (int)P->m_first;   // output rows [m_first, m_first + m_count)
+  M.M = (int)(P->m_first + P->m_count);
   M.K = (int)P->c.K();
   M.NC = P->c.NC;
   M.lanes = (int)lnw;
@@ -976,6 +1007,7 @@ extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const Pe
                                   uint64_t mask_seed_x, uint64_t mask_seed_w, uint64_t* ct_gx, uint64_t* gx0,
                                   uint64_t* ct_gw, uint64_t* gw_mask, void* ws, size_t ws_bytes, void* stream) {
   if (!ctx || (!Pd && !Pw) || !ws || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((Pd && Pd->parent) || (Pw && Pw->parent)) return PENCIL_E_ARG;   // whole plans only
   if (Pd && (Pd->ctx != ctx || Pd->role != PENCIL_ROLE_DGRAD || !ct_gy1_d || !pt_wt || !gy0 || !ct_gx || !gx0 ||
              !aligned16(ct_gy1_d) || !aligned16(pt_wt) || !aligned16(ct_gx)))
     return PENCIL_E_ARG;
@@ -1079,11 +1111,12 @@ extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const
   D.out = reinterpret_cast<u64*>(ws);
   {
     PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
-    CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->ct_out, s)));
+    CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->out_count(), s, (int)P->out_first())));
   }
   {
     PROF(ctx, PENCIL_K_DECRYPT_COMBINE, s);
-    CUDA_TRY(launch_decrypt_combine(ctx->dev, P->pk_y, P->acc_y, D.out, (int)P->ct_out, check_noise ? 1 : 0, y1, s));
+    CUDA_TRY(launch_decrypt_combine(ctx->dev, P->pk_y, P->acc_y, D.out, (int)P->out_first(), (int)P->out_count(),
+                                    check_noise ? 1 : 0, y1, s));
   }
   return PENCIL_OK;
 }
@@ -1240,7 +1273,7 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
                                      const uint64_t* share, uint64_t seed, uint64_t* ct, void* stream) {
   if (!ctx || !sk || !P || !share || !ct || P->ctx != ctx || sk->ctx != ctx) return PENCIL_E_ARG;
   if (operand != PENCIL_OPERAND_INPUT && operand != PENCIL_OPERAND_KERNEL) return PENCIL_E_ARG;
-  if (!aligned16(ct)) return PENCIL_E_ARG;
+  if (!aligned16(ct) || P->parent) return PENCIL_E_ARG;   // whole plans only
   const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->ct_in;
   const unsigned long long need = (unsigned long long)count * (unsigned long long)ctx->n;
   if (need > PENCIL_NOALLOC_SCRATCH_BYTES) {
@@ -1255,7 +1288,7 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
   const int rc = noalloc_scratch(ctx->device, &err);
   if (rc != PENCIL_OK) return rc;
   const cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_sample_err(seed, (int)count, ctx->n, err, s));
+  CUDA_TRY(launch_sample_err(seed, 0, (int)count, ctx->n, err, s));
   ModeEncrypt::Params M;
   M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
   M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
@@ -1295,7 +1328,7 @@ extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plan
   if (!ctx || !plans || !out || count < 1) return PENCIL_E_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i)
-    if (!plans[i] || plans[i]->ctx != ctx || plans[i]->role != PENCIL_ROLE_FWD) return PENCIL_E_ARG;
+    if (!plans[i] || plans[i]->ctx != ctx || plans[i]->role != PENCIL_ROLE_FWD || plans[i]->parent) return PENCIL_E_ARG;
   PencilBatch* B = new (std::nothrow) PencilBatch();
   if (!B) return PENCIL_E_CUDA;
   B->ctx = ctx;

@@ -4,6 +4,7 @@
 // and the RNS scale-and-round of decryption (Alg. 1 step 4).
 #include "cdt_table.h"
 #include <algorithm>
+#include <cstdio>
 
 #include "kernels.h"
 
@@ -600,10 +601,10 @@ static cudaError_t launch_mac_smem(const DevCtx& ctx, const MacParams& P0, bool 
   MacParams P = P0;
   const unsigned gx = (unsigned)((P.lanes + MAC_LANES - 1) / MAC_LANES);
   const int mchunk_blocks = std::max(1, 65535 / nblocks);
-  const int mblocks_total = (P0.M + MB - 1) / MB;
+  const int mblocks_total = (P0.M - P0.m_base + MB - 1) / MB;   // output rows m in [m_base, M)
   for (int mbase = 0; mbase < mblocks_total; mbase += mchunk_blocks) {
     const int mblocks = std::min(mchunk_blocks, mblocks_total - mbase);
-    P.m_base = mbase * MB;
+    P.m_base = P0.m_base + mbase * MB;
     dim3 grid(gx, (unsigned)(mblocks * nblocks));
     if (dual)
       k_mac_smem<true><<<grid, 256, smem, s>>>(ctx, P, MB, lnb, mblocks);
@@ -628,9 +629,9 @@ static cudaError_t launch_mac_ring(const DevCtx& ctx, const MacParams& P0, bool 
                         : cudaFuncSetAttribute(k_mac_ring<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
   if (e0 != cudaSuccess) return e0;
-  for (int base = 0; base < P0.M; base += mchunk) {
-    P.m_base = base;
-    const int mc = min(mchunk, P0.M - base);
+  for (long long base = P0.m_base; base < P0.M; base += mchunk) {   // output rows m in [m_base, M)
+    P.m_base = (int)base;
+    const int mc = (int)std::min<long long>(mchunk, P0.M - base);
     dim3 grid((unsigned)(mc * ntiles), gy);
     if (dual)
       k_mac_ring<NT, true><<<grid, threads, smem, s>>>(ctx, P);
@@ -654,15 +655,19 @@ static cudaError_t launch_mac_bulk(const DevCtx& ctx, const MacParams& P0, bool 
   const void* fn = dual ? (const void*)k_mac_bulk<NT, true> : (const void*)k_mac_bulk<NT, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  for (int base = 0; base < P0.M; base += mchunk) {
-    P.m_base = base;
-    const int mc = min(mchunk, P0.M - base);
+  for (long long base = P0.m_base; base < P0.M; base += mchunk) {   // output rows m in [m_base, M)
+    P.m_base = (int)base;
+    const int mc = (int)std::min<long long>(mchunk, P0.M - base);
     dim3 grid((unsigned)(mc * ntiles), gy);
     if (dual)
       k_mac_bulk<NT, true><<<grid, MAC_BT + 32, smem, s>>>(ctx, P);
     else
       k_mac_bulk<NT, false><<<grid, MAC_BT + 32, smem, s>>>(ctx, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      fprintf(stderr, "pencil: k_mac_bulk<%d> launch (grid %u x %u, %d threads, %zu B shared, rows [%d, %d)): %s\n", NT,
+              grid.x, grid.y, MAC_BT + 32, smem, (int)base, P0.M, cudaGetErrorString(e));
+      return e;
+    }
   }
   return cudaSuccess;
 }
@@ -694,7 +699,7 @@ cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P0, bool dual, cudaSt
   MacParams P = P0;
   const unsigned gx = (unsigned)((P.lanes + threads - 1) / threads);
   const unsigned gy = (unsigned)((P.NC + NT - 1) / NT);
-  for (int base = 0; base < P0.M; base += 65535) {
+  for (int base = P0.m_base; base < P0.M; base += 65535) {
     P.m_base = base;
     dim3 grid(gx, gy, (unsigned)min(65535, P0.M - base));
     if (dual)
@@ -718,21 +723,21 @@ __device__ __forceinline__ int8_t cdt_sample(u64 w) {
   return (int8_t)((w >> 63) ? -mag : mag);
 }
 
-__global__ void k_sample_err(u64 seed, int count, int n, int8_t* out) {
+__global__ void k_sample_err(u64 seed, int first, int count, int n, int8_t* out) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int per = n >> 2;
   if (id >= (long long)count * per) return;
-  const int ct = (int)(id / per);
+  const int ct = first + (int)(id / per);
   const int blk = (int)(id % per);
   const Philox4 w = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_E);
   reinterpret_cast<char4*>(out + (size_t)ct * n)[blk] =
       make_char4(cdt_sample(w.v[0]), cdt_sample(w.v[1]), cdt_sample(w.v[2]), cdt_sample(w.v[3]));
 }
 
-cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStream_t s) {
+cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s) {
   const long long total = (long long)count * (n >> 2);
   if (total == 0) return cudaSuccess;
-  k_sample_err<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, count, n, out);
+  k_sample_err<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, first, count, n, out);
   return cudaGetLastError();
 }
 
@@ -740,17 +745,37 @@ cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStrea
 // element `flat`, Philox(key (seed, 4), counter (flat/4, 0, 0, 0)) word flat%4;
 // elsewhere Philox(key (seed, 5), counter (i/4, ct, 0, 0)) word i%4; mod t.
 // Coefficients 4 blk .. 4 blk + 3 of the mask polynomial of output ciphertext ct.
+__device__ __forceinline__ u64 philox_word(const Philox4& w, int i) {
+  return i == 0 ? w.v[0] : i == 1 ? w.v[1] : i == 2 ? w.v[2] : w.v[3];
+}
+
+// Coefficients 4 blk .. 4 blk + 3 of output polynomial ct.  Consecutive
+// coefficients usually carry consecutive outputs, so one Philox block of the
+// element stream is reused while flat / 4 stays the same; the padding stream
+// is drawn only if some coefficient carries no output.
 __device__ __forceinline__ void mask_poly_block(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed,
                                                 int ct, int blk, u64* out_ct) {
-  const Philox4 pad = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_MASK_PAD);
+  i64 flat[4];
+  bool any_pad = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    flat[i] = out_index(pk, ac, ct, 4 * blk + i);
+    any_pad |= flat[i] < 0;
+  }
+  Philox4 pad = {{0, 0, 0, 0}};
+  if (any_pad) pad = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_MASK_PAD);
+  Philox4 el = {{0, 0, 0, 0}};
+  i64 cur = -1;
   u64 r[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const i64 flat = out_index(pk, ac, ct, 4 * blk + i);
-    u64 w = pad.v[i];
-    if (flat >= 0) {
-      const Philox4 el = philox4x64((u64)(flat >> 2), 0ull, 0ull, 0ull, seed, PENCIL_DOM_MASK);
-      w = el.v[flat & 3];
+    u64 w = philox_word(pad, i);
+    if (flat[i] >= 0) {
+      if ((flat[i] >> 2) != cur) {
+        cur = flat[i] >> 2;
+        el = philox4x64((u64)cur, 0ull, 0ull, 0ull, seed, PENCIL_DOM_MASK);
+      }
+      w = philox_word(el, (int)(flat[i] & 3));
     }
     r[i] = w & ctx.t_mask;
   }
@@ -839,19 +864,19 @@ __device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Pac
   y1[flat] = r_hi & ctx.t_mask;
 }
 
-__global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int count, int check,
-                                  u64* y1) {
+__global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int first, int count,
+                                  int check, u64* y1) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int n = ctx.n;
   if (id >= (long long)count * n) return;
-  decrypt_combine_one(ctx, pk, ac, yres, (int)(id / n), (int)(id % n), check, y1);
+  decrypt_combine_one(ctx, pk, ac, yres, first + (int)(id / n), (int)(id % n), check, y1);
 }
 
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
-                                   int count, int check, u64* y1, cudaStream_t s) {
+                                   int first, int count, int check, u64* y1, cudaStream_t s) {
   const long long total = (long long)count * ctx.n;
   if (total == 0) return cudaSuccess;
-  k_decrypt_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, yres, count, check, y1);
+  k_decrypt_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, yres, first, count, check, y1);
   return cudaGetLastError();
 }
 

@@ -32,13 +32,13 @@ struct MacParams {
 
 cudaError_t upload_cdt();
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P, bool dual, cudaStream_t s);
-cudaError_t launch_sample_err(u64 seed, int count, int n, int8_t* out, cudaStream_t s);
+cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s);
 cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed, int count, u64* out,
                              cudaStream_t s);
 cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,
                             cudaStream_t s);
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
-                                   int count, int check, u64* y1, cudaStream_t s);
+                                   int first, int count, int check, u64* y1, cudaStream_t s);
 
 // Plaintext correlation over Z_t of one plan role (see k_ring_* in kernels.cu).
 struct RingParams {
@@ -139,16 +139,20 @@ cudaError_t ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const 
   }
 }
 
+// Transforms polynomials [first, first + count) of the mode's arrays.
 template <class Mode, bool INV>
-cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
+cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s, int first = 0) {
   const bool r4 = ctx.ntt_loge == 4;
   switch (ctx.log_n) {
     case 12:
-      return r4 ? launch_ntt<12, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<12, 5, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<12, 4, Mode, INV>(ctx, P, first, count, s)
+                : launch_ntt<12, 5, Mode, INV>(ctx, P, first, count, s);
     case 13:
-      return r4 ? launch_ntt<13, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<13, 5, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<13, 4, Mode, INV>(ctx, P, first, count, s)
+                : launch_ntt<13, 5, Mode, INV>(ctx, P, first, count, s);
     case 14:
-      return r4 ? launch_ntt<14, 4, Mode, INV>(ctx, P, count, s) : launch_ntt<14, 5, Mode, INV>(ctx, P, count, s);
+      return r4 ? launch_ntt<14, 4, Mode, INV>(ctx, P, first, count, s)
+                : launch_ntt<14, 5, Mode, INV>(ctx, P, first, count, s);
     default:
       return cudaErrorInvalidValue;
   }

@@ -204,18 +204,19 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
 }
 
+// CTA (x, limb) transforms polynomial first + x.
 template <int LOGN, int LOGE, class Mode>
 __global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
-    k_ntt_fwd(DevCtx ctx, typename Mode::Params P) {
+    k_ntt_fwd(DevCtx ctx, typename Mode::Params P, int first) {
   extern __shared__ u64 sm[];
-  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, blockIdx.x, blockIdx.y, sm);
+  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
 }
 
 template <int LOGN, int LOGE, class Mode>
 __global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
-    k_ntt_inv(DevCtx ctx, typename Mode::Params P) {
+    k_ntt_inv(DevCtx ctx, typename Mode::Params P, int first) {
   extern __shared__ u64 sm[];
-  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, blockIdx.x, blockIdx.y, sm);
+  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
 }
 
 // Multi-plan variants: CTA (blockIdx.x, limb) transforms polynomial items[x].y
@@ -482,7 +483,7 @@ struct ModeDecrypt {
 
 // Host-side launcher; explicitly instantiated per LOGN in ntt12.cu / ntt13.cu / ntt14.cu.
 template <int LOGN, int LOGE, class Mode, bool INV>
-cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s) {
+cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int first, int count, cudaStream_t s) {
   using C = NttCfg<LOGN, LOGE>;
   if (count <= 0) return cudaSuccess;
   cudaError_t err;
@@ -491,12 +492,12 @@ cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int co
     err = cudaFuncSetAttribute(k_ntt_inv<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_inv<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+    k_ntt_inv<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
   } else {
     err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_fwd<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P);
+    k_ntt_fwd<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
   }
   return cudaGetLastError();
 }
@@ -524,7 +525,8 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
 }
 
 #define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV)                                                          \
-  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, cudaStream_t); \
+  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, int,      \
+                                                              cudaStream_t);                                   \
   SPEC template cudaError_t launch_ntt_multi<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params*, const int2*, \
                                                                     long long, const u64*, cudaStream_t);
 #define PENCIL_NTT_INST_E(SPEC, LOGN, LOGE)                \

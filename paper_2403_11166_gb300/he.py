@@ -9,6 +9,7 @@ built: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from dataclasses import dataclass
 
@@ -33,7 +34,7 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune", "pencil_batch_create",
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
-           "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply")
+           "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
@@ -92,6 +93,7 @@ def _load():
         "pencil_sk_destroy": [P],
         "pencil_plan_linear": [P, ctypes.POINTER(LayerDesc), I32, ctypes.POINTER(Partition), ctypes.POINTER(P)],
         "pencil_plan_destroy": [P],
+        "pencil_plan_slice": [P, I32, I32, ctypes.POINTER(P)],
         "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
@@ -264,6 +266,24 @@ class Plan:
         _check(lib.pencil_plan_sizes(h, ctypes.byref(s)), "pencil_plan_sizes")
         self.sizes = s
         self.part = s.part.astuple()
+        self.parent = None
+        self.row_range = None
+
+    @property
+    def rows(self) -> int:
+        """M, the output rows of the partition (ct_in = M K, pt = K NC, ct_out = M NC)."""
+        S = self.sizes
+        return math.isqrt(S.ct_in * S.ct_out // S.pt)
+
+    def slice(self, m_first: int, m_count: int) -> "Plan":
+        """pencil_plan_slice: the output rows [m_first, m_first + m_count) of this plan (same
+        buffers and workspaces; keeps this plan alive)."""
+        h = ctypes.c_void_p()
+        _check(lib.pencil_plan_slice(self.h, m_first, m_count, ctypes.byref(h)), "pencil_plan_slice")
+        sl = Plan.__new__(Plan)
+        sl.ctx, sl.layer, sl.role, sl.h = self.ctx, self.layer, self.role, h
+        sl.sizes, sl.part, sl.parent, sl.row_range = self.sizes, self.part, self, (m_first, m_count)
+        return sl
 
     def new_ct(self, count: int) -> torch.Tensor:
         return torch.empty((count, 2, self.ctx.L, self.ctx.n), dtype=torch.int64, device=f"cuda:{self.ctx.device}")

@@ -347,3 +347,83 @@ def test_split_calls_validate(he):
         he.he_linear_forward_apply(ctx, plan, None, plan.new_pt(S.pt), plan.new_ct(S.ct_out),
                                    plan.new_ws(S.ws_forward))
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("role,cfg,chunks", [("fwd", (13, 3, 60), [(0, 1), (1, 2), (3, None)]),
+                                             ("fwd", (12, 2, 54), [(0, 2), (2, None)]),
+                                             ("dgrad", (13, 3, 60), [(0, 3), (3, None)])])
+def test_slices_stream_equals_whole(he, role, cfg, chunks):
+    """A layer streamed through the protocol slice by slice (encrypt / apply /
+    decrypt of disjoint output-row ranges on two alternating streams) gives the
+    whole-plan ciphertexts and shares bit for bit."""
+    L = Layer("conv", B=7, Ci=5, Co=6, h=9, w=8, s=3, pad=1)
+    part = (2, 2, 3, 5, 4, 3, 3)
+    ctx = he.Context(*cfg)
+    sk = ctx.keygen(5)
+    g = inputs.rng(41)
+    W = inputs.gaussian_fixed(g, L.w_shape())
+    xs = inputs.gaussian_fixed(g, L.x_shape() if role == "fwd" else L.y_shape())
+    x0, x1 = inputs.split_shares(g, xs)
+    hrole = he.ROLE_FWD if role == "fwd" else he.ROLE_DGRAD
+    plan = he.Plan(ctx, _he_layer(he, L), hrole, part)
+    S = plan.sizes
+    M = plan.rows
+    assert M >= 4 and S.ct_in % M == 0 and S.ct_out % M == 0
+    Wd, x0d, x1d = to_dev(W), to_dev(x0), to_dev(x1)
+
+    def buffers():   # encryption and decryption of different slices overlap: one workspace each
+        return (plan.new_pt(S.pt), plan.new_ct(S.ct_in), plan.new_ct(S.ct_out),
+                torch.empty(S.out_elems, dtype=torch.int64, device="cuda"),
+                torch.empty(S.out_elems, dtype=torch.int64, device="cuda"),
+                plan.new_ws(S.ws_forward), plan.new_ws(S.ws_encrypt), plan.new_ws(S.ws_decrypt))
+    # whole plan
+    pt, ct_in, ct_out, y0, y1, ws_mo, ws_enc, ws_dec = buffers()
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, Wd, pt)
+    he.he_linear_forward_prepare(ctx, plan, x0d, None, 4, y0, ws_mo)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1d, 3, ct_in, ws_enc)
+    he.he_linear_forward_apply(ctx, plan, ct_in, pt, ct_out, ws_mo)
+    he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws_dec)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    want = [to_np(t) for t in (ct_in, ct_out, y0, y1)]
+    # streamed by slices
+    pt, ct_in, ct_out, y0, y1, ws_mo, ws_enc, ws_dec = buffers()
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, Wd, pt)
+    he.he_linear_forward_prepare(ctx, plan, x0d, None, 4, y0, ws_mo)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    slices = [plan.slice(a, (M - a) if c is None else c) for a, c in chunks]
+    for i, sl in enumerate(slices):
+        st = streams[i % 2]
+        he.encrypt_share(ctx, sk, sl, he.OPERAND_INPUT, x1d, 3, ct_in, ws_enc, stream=st)
+        he.he_linear_forward_apply(ctx, sl, ct_in, pt, ct_out, ws_mo, stream=st)
+        he.decrypt_to_share(ctx, sk, sl, ct_out, y1, True, ws_dec, stream=st)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    for a, b in zip(want, (to_np(t) for t in (ct_in, ct_out, y0, y1))):
+        assert (a == b).all()
+
+
+def test_slice_validation(he):
+    ctx = he.Context(12, 2, 54)
+    L = Layer("conv", B=7, Ci=5, Co=6, h=9, w=8, s=3, pad=1)
+    plan = he.Plan(ctx, _he_layer(he, L), he.ROLE_FWD, (2, 2, 3, 5, 4, 3, 3))
+    M = plan.rows
+    for a, c, code in [(0, 0, -2), (-1, 2, -2), (M - 1, 2, -2), (M, 1, -2)]:
+        with pytest.raises(he.PencilError) as e:
+            plan.slice(a, c)
+        assert e.value.code == code
+    sl = plan.slice(1, 2)
+    with pytest.raises(he.PencilError) as e:
+        sl.slice(0, 1)
+    assert e.value.code == -1
+    sk = ctx.keygen(1)
+    S = plan.sizes
+    with pytest.raises(he.PencilError) as e:   # the kernel operand is not sliced
+        he.encrypt_share(ctx, sk, sl, he.OPERAND_KERNEL, torch.zeros(6 * 5 * 9, dtype=torch.int64, device="cuda"), 1,
+                         plan.new_ct(S.pt), plan.new_ws(S.ws_encrypt))
+    assert e.value.code == -1
+    pw = he.Plan(ctx, _he_layer(he, L), he.ROLE_WGRAD, None)
+    with pytest.raises(he.PencilError) as e:
+        pw.slice(0, 1)
+    assert e.value.code == -1
