@@ -658,8 +658,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    t_issue = time.perf_counter()
     for i in range(args.steps):
         step(args.warmup + i)
+    t_issue = time.perf_counter() - t_issue   # host time to issue the steps (the GPU runs behind it)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -742,6 +744,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (independent layers, no collective)",
                    "streamed_slices": nch},
         "parity_selfcheck": parity_ok,
+        "host_issue_ms_per_step": round(t_issue * 1e3 / args.steps, 4),
         "roofline": roof,
         "kernels": table,
         "clocks": ck,

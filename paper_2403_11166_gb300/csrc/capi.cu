@@ -1312,7 +1312,7 @@ struct PencilBatch {
     bool bound = false;
   };
   struct Off {
-    long long pt, ct_in, ct_out, err, c0p, mpoly, yres;
+    long long pt, ct_in, ct_out, err, p0, mnt, mpoly, yres;
   };
   std::vector<User> user;
   std::vector<Off> off;
@@ -1348,8 +1348,10 @@ extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plan
     o += al(P->ct_out * 2 * lnb);
     f.err = o;
     o += al(P->ct_in * n);
-    f.c0p = o;
+    f.p0 = o;
     o += al(P->ct_in * lnb);
+    f.mnt = o;
+    o += al(P->ct_out * lnb);
     f.mpoly = o;
     o += al(P->ct_out * n * 8);
     f.yres = o;
@@ -1410,15 +1412,14 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   const int nt = ctx->dev.mac_nt == 0 ? 4 : ctx->dev.mac_nt;
   std::vector<ModeEncode::Params> enc(nl);
   std::vector<ModeEncrypt::Params> encr(nl);
-  std::vector<ModeAddPlain::Params> addp(nl);
-  std::vector<ModeMask::Params> mask(nl);
+  std::vector<ModeMoPrep::Params> prep(nl);
   std::vector<ModeDecrypt::Params> dec(nl);
   std::vector<SampleP> samp(nl);
   std::vector<MaskPolyP> mpol(nl);
   std::vector<MoShareP> mosh(nl);
   std::vector<CombineP> comb(nl);
   std::vector<MacParams> mac(nl);
-  std::vector<int2> it_pt, it_in, it_out, it_sh;
+  std::vector<int2> it_pt, it_in, it_out, it_sh, it_prep;
   std::vector<int4> it_mac;
   for (int l = 0; l < nl; ++l) {
     const PencilPlan* P = B->plans[l];
@@ -1428,7 +1429,8 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     u64* ct_in = reinterpret_cast<u64*>(w + f.ct_in);
     u64* ct_out = reinterpret_cast<u64*>(w + f.ct_out);
     int8_t* err = reinterpret_cast<int8_t*>(w + f.err);
-    u64* c0p = reinterpret_cast<u64*>(w + f.c0p);
+    u64* p0 = reinterpret_cast<u64*>(w + f.p0);
+    u64* mnt = reinterpret_cast<u64*>(w + f.mnt);
     u64* mpoly = reinterpret_cast<u64*>(w + f.mpoly);
     u64* yres = reinterpret_cast<u64*>(w + f.yres);
     enc[l].pk = P->pk_w;
@@ -1443,14 +1445,20 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     encr[l].sk = sk->sk;
     encr[l].ct = ct_in;
     encr[l].seed = enc_seed + (u64)l;
-    addp[l].pk = P->pk_v;
-    addp[l].ac = P->acc_v;
-    addp[l].ac.ptr = u.x0;
-    addp[l].ct_in = ct_in;
-    addp[l].out_c0 = c0p;
+    memset(&prep[l], 0, sizeof(ModeMoPrep::Params));
+    prep[l].pk = P->pk_v;
+    prep[l].ac = P->acc_v;
+    prep[l].ac.ptr = u.x0;
+    prep[l].mpoly = mpoly;
+    prep[l].n_in = (int)P->ct_in;
+    prep[l].out_in = p0;
+    prep[l].out_mask = mnt;
     memset(&mac[l], 0, sizeof(MacParams));
-    mac[l].a0 = c0p;
-    mac[l].a0_stride = lnw;
+    mac[l].a0 = ct_in;   // + NTT(Delta x0) on load, - NTT(Delta s) on store (Alg. 1 steps 2-3)
+    mac[l].a0_stride = 2 * lnw;
+    mac[l].p0 = p0;
+    mac[l].p0_stride = lnw;
+    mac[l].mask = mnt;
     mac[l].a1 = ct_in + lnw;
     mac[l].a1_stride = 2 * lnw;
     mac[l].b = pt;
@@ -1461,8 +1469,6 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     mac[l].NC = P->c.NC;
     mac[l].lanes = (int)lnw;
     mpol[l] = MaskPolyP{P->pk_y, P->acc_y, mask_seed + (u64)l, mpoly};
-    mask[l].mpoly = mpoly;
-    mask[l].ct = ct_out;
     mosh[l] = MoShareP{mask_seed + (u64)l, P->out_elems, u.bias, P->hw, P->co_out, u.y0};
     dec[l].ct = ct_out;
     dec[l].sk = sk->sk;
@@ -1471,6 +1477,7 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     for (long long i = 0; i < P->pt; ++i) it_pt.push_back(make_int2(l, (int)i));
     for (long long i = 0; i < P->ct_in; ++i) it_in.push_back(make_int2(l, (int)i));
     for (long long i = 0; i < P->ct_out; ++i) it_out.push_back(make_int2(l, (int)i));
+    for (long long i = 0; i < P->ct_in + P->ct_out; ++i) it_prep.push_back(make_int2(l, (int)i));
     for (long long c = 0; c < (P->out_elems + 1023) / 1024; ++c) it_sh.push_back(make_int2(l, (int)c));
     const int lane_blocks = (int)((lnw + 127) / 128);
     for (long long m = 0; m < P->c.M(); ++m)
@@ -1479,12 +1486,11 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   }
   if (!ctx->dev.mac_split) return PENCIL_E_UNIMPL;
   std::vector<char> blob;
-  size_t at = 0, o_enc, o_encr, o_addp, o_mask, o_dec, o_samp, o_mpol, o_mosh, o_comb, o_mac, o_pt, o_in, o_out,
-         o_sh, o_imac, o_words;
+  size_t at = 0, o_enc, o_encr, o_prep, o_dec, o_samp, o_mpol, o_mosh, o_comb, o_mac, o_pt, o_in, o_out, o_sh,
+         o_iprep, o_imac, o_words;
   put(blob, at, enc, o_enc);
   put(blob, at, encr, o_encr);
-  put(blob, at, addp, o_addp);
-  put(blob, at, mask, o_mask);
+  put(blob, at, prep, o_prep);
   put(blob, at, dec, o_dec);
   put(blob, at, samp, o_samp);
   put(blob, at, mpol, o_mpol);
@@ -1495,6 +1501,7 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   put(blob, at, it_in, o_in);
   put(blob, at, it_out, o_out);
   put(blob, at, it_sh, o_sh);
+  put(blob, at, it_prep, o_iprep);
   put(blob, at, it_mac, o_imac);
   std::vector<u64> words(nl + 2, 0);  // ready[nl], step, abort flag
   put(blob, at, words, o_words);
@@ -1510,8 +1517,7 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   D.n_layers = nl;
   D.encode = reinterpret_cast<const ModeEncode::Params*>(d + o_enc);
   D.encrypt = reinterpret_cast<const ModeEncrypt::Params*>(d + o_encr);
-  D.addplain = reinterpret_cast<const ModeAddPlain::Params*>(d + o_addp);
-  D.mask = reinterpret_cast<const ModeMask::Params*>(d + o_mask);
+  D.prep = reinterpret_cast<const ModeMoPrep::Params*>(d + o_prep);
   D.decrypt = reinterpret_cast<const ModeDecrypt::Params*>(d + o_dec);
   D.sample = reinterpret_cast<const SampleP*>(d + o_samp);
   D.maskpoly = reinterpret_cast<const MaskPolyP*>(d + o_mpol);
@@ -1524,6 +1530,8 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   D.n_in = (long long)it_in.size();
   D.items_out = reinterpret_cast<const int2*>(d + o_out);
   D.n_out = (long long)it_out.size();
+  D.items_prep = reinterpret_cast<const int2*>(d + o_iprep);
+  D.n_prep = (long long)it_prep.size();
   D.items_share = reinterpret_cast<const int2*>(d + o_sh);
   D.n_share = (long long)it_sh.size();
   D.items_mac = reinterpret_cast<const int4*>(d + o_imac);

@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(128, (NT == 4 && !DUAL) ? 6 : 0) k_mac_ring(De
 // returns.
 #define MAC_BT 128
 #define MAC_BSTAGES 4
-#define MAC_WAIT_LIMIT (1 << 22)
+#define MAC_WAIT_LIMIT (1 << 20)
+#define MAC_WAIT_HINT_NS 1000
 
 __device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
@@ -287,17 +288,20 @@ __device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
 __device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// One poll; the thread may be suspended for up to MAC_WAIT_HINT_NS while the
+// phase is incomplete (instead of spinning on issue slots).
 __device__ __forceinline__ bool mbar_try_wait(u32 bar, u32 parity) {
   u32 done;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "n"(MAC_WAIT_HINT_NS)
       : "memory");
   return done != 0;
 }
+// At most MAC_WAIT_LIMIT polls (about MAC_WAIT_LIMIT x MAC_WAIT_HINT_NS, ~1 s).
 __device__ __forceinline__ bool mbar_wait_bounded(u32 bar, u32 parity) {
   for (int i = 0; i < MAC_WAIT_LIMIT; ++i)
     if (mbar_try_wait(bar, parity)) return true;
@@ -409,12 +413,31 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
     const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
     const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
     const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
+    u32 bL[NT], bH[NT];
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      const u32 bL = (u32)bw[j] & M30, bH = (u32)(bw[j] >> 30);
-      mac_split(acc[j][0], a0L, a0H, bL, bH);
-      mac_split(acc[j][1], a1L, a1H, bL, bH);
-      if constexpr (DUAL) {
+      bL[j] = (u32)bw[j] & M30;
+      bH[j] = (u32)(bw[j] >> 30);
+    }
+    // Two passes, each touching every accumulator once, so the two S1 terms of a
+    // product are 2 NT multiply-adds apart (no back-to-back dependent pair).
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      acc[j][0].s0 += (u64)a0L * bL[j];
+      acc[j][0].s1 += (u64)a0H * bL[j];
+      acc[j][1].s0 += (u64)a1L * bL[j];
+      acc[j][1].s1 += (u64)a1H * bL[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      acc[j][0].s2 += (u64)a0H * bH[j];
+      acc[j][0].s1 += (u64)a0L * bH[j];
+      acc[j][1].s2 += (u64)a1H * bH[j];
+      acc[j][1].s1 += (u64)a1L * bH[j];
+    }
+    if constexpr (DUAL) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
         mac_split(acc[j][0], (u32)c0w[j] & M30, (u32)(c0w[j] >> 30), pL, pH);
         mac_split(acc[j][1], (u32)c1w[j] & M30, (u32)(c1w[j] >> 30), pL, pH);
       }
@@ -1113,7 +1136,14 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = ntt_multi<ModeEncrypt, false>(ctx, B.encrypt, B.items_in, B.n_in, B.step, s);
     if (e != cudaSuccess) return e;
-    e = ntt_multi<ModeAddPlain, false>(ctx, B.addplain, B.items_in, B.n_in, B.step, s);
+  }
+  if (B.n_out) {   // the MO's mask s, then NTT(Delta x0) and NTT(Delta s) of every layer in one launch
+    k_mask_poly_multi<<<blocks_for(B.n_out * (n / 4), 256), 256, 0, s>>>(ctx, B.maskpoly, B.items_out, B.n_out,
+                                                                            B.step);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (B.n_prep) {
+    e = ntt_multi<ModeMoPrep, false>(ctx, B.prep, B.items_prep, B.n_prep, B.step, s);
     if (e != cudaSuccess) return e;
   }
   k_signal<<<blocks_for(B.n_layers, 128), 128, 0, s>>>(B.ready, B.n_layers, B.withhold, B.step);
@@ -1134,13 +1164,6 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
                                                                                 B.ready, B.step, B.abort_flag);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (B.n_out) {
-    k_mask_poly_multi<<<blocks_for(B.n_out * (n / 4), 256), 256, 0, s>>>(ctx, B.maskpoly, B.items_out, B.n_out,
-                                                                            B.step);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = ntt_multi<ModeMask, false>(ctx, B.mask, B.items_out, B.n_out, B.step, s);
-    if (e != cudaSuccess) return e;
   }
   if (B.n_share) {
     k_mo_share_multi<<<blocks_for(B.n_share * 256, 256), 256, 0, s>>>(B.moshare, B.items_share, B.n_share,

@@ -84,8 +84,7 @@ struct BatchDev {
   int n_layers;
   const ModeEncode::Params* encode;
   const ModeEncrypt::Params* encrypt;
-  const ModeAddPlain::Params* addplain;
-  const ModeMask::Params* mask;
+  const ModeMoPrep::Params* prep;    // NTT(Delta x0) and NTT(Delta s) of every layer
   const ModeDecrypt::Params* decrypt;
   const SampleP* sample;
   const MaskPolyP* maskpoly;
@@ -98,6 +97,8 @@ struct BatchDev {
   long long n_in;
   const int2* items_out;
   long long n_out;
+  const int2* items_prep;   // (layer, polynomial): input polynomials, then output polynomials
+  long long n_prep;
   const int2* items_share;
   long long n_share;
   const int4* items_mac;

@@ -317,33 +317,6 @@ struct ModeEncrypt {
   }
 };
 
-// MO add_plain (Alg. 1 step 2): out_c0 = ct_in.c0 + NTT(Delta * pi_v(x0)).
-struct ModeAddPlain {
-  static constexpr bool kHeavyLoad = true;
-  static constexpr int kLoadUnroll = 16;
-  static constexpr int kEpilogueUnroll = 4;
-  struct Params {
-    Packing pk;
-    Accessor ac;
-    const u64* ct_in;   // [count][2][L][N]
-    u64* out_c0;        // [count][L][N]
-  };
-  static __device__ __forceinline__ void rebase(Params&, u64) {}
-  template <int N>
-  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
-                                             int e) {
-    const u64 m = gather(P.pk, P.ac, poly, e) & c.t_mask;
-    return mul_shoup(m, lc.delta, lc.deltas, lc.q);
-  }
-  template <int N>
-  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
-                                                int limb, int e, u64 x0, u64 x1) {
-    const ulonglong2 c0 = __ldg(reinterpret_cast<const ulonglong2*>(P.ct_in + ct_off(poly, 0, limb, c.L, N) + e));
-    *reinterpret_cast<ulonglong2*>(P.out_c0 + limb_off(poly, limb, c.L, N) + e) =
-        make_ulonglong2(add_mod(c0.x, x0, lc.q), add_mod(c0.y, x1, lc.q));
-  }
-};
-
 // MO plaintext encoding: centred lift of Z_t values, NTT.
 struct ModeEncode {
   static constexpr bool kHeavyLoad = true;
@@ -366,30 +339,6 @@ struct ModeEncode {
   static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
                                                 int limb, int e, u64 x0, u64 x1) {
     *reinterpret_cast<ulonglong2*>(P.pt + limb_off(poly, limb, c.L, N) + e) = make_ulonglong2(x0, x1);
-  }
-};
-
-// MO re-mask (Alg. 1 step 3): ct_out.c0 -= NTT(Delta * s).
-struct ModeMask {
-  static constexpr bool kHeavyLoad = false;
-  static constexpr int kLoadUnroll = 32;
-  static constexpr int kEpilogueUnroll = 4;
-  struct Params {
-    const u64* mpoly;   // [count][N] Z_t mask coefficients
-    u64* ct;            // [count][2][L][N]
-  };
-  static __device__ __forceinline__ void rebase(Params&, u64) {}
-  template <int N>
-  static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int poly, int,
-                                             int e) {
-    return mul_shoup(P.mpoly[(size_t)poly * N + e], lc.delta, lc.deltas, lc.q);
-  }
-  template <int N>
-  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
-                                                int limb, int e, u64 x0, u64 x1) {
-    ulonglong2* p = reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
-    const ulonglong2 c0 = *p;
-    *p = make_ulonglong2(sub_mod(c0.x, x0, lc.q), sub_mod(c0.y, x1, lc.q));
   }
 };
 
@@ -533,9 +482,7 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, false)       \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, true)        \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncrypt, false)   \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeAddPlain, false)  \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false)    \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMask, false)      \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMoPrep, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
