@@ -57,7 +57,12 @@ typedef struct PencilPlan PencilPlan;
  * limbs (Sec. 5 "RNS Decomposition"): the largest primes below 2^prime_bits
  * that are 1 mod 2N, in descending order.  Supported: log_n in {12, 13, 14},
  * num_primes in [1, 4], prime_bits in [30, 60], t_bits in [8, 60].  The
- * encryption error is a discrete Gaussian with sigma = 3.2 on [-19, 19]. */
+ * encryption error is a discrete Gaussian with sigma = 3.2 on [-19, 19].
+ * Throughout, "Delta m" for a message m in [0, t) denotes the BFV scaling
+ * round(q m / t) = floor(q / t) m + round((q mod t) m / t): a plaintext
+ * multiple of such a ciphertext then carries no (q mod t)-sized overflow
+ * term, which keeps products of two uniform Z_t values decryptable (Alg. 2's
+ * cross terms at t = 2^59, q ~ 2^180). */
 typedef struct {
   int32_t log_n;
   int32_t num_primes;
@@ -301,6 +306,19 @@ int pencil_ring_linear(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* k
  * layer ([B][n_o] or [B][C_out][H_out][W_out]); each party sums its own share. */
 int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* g, uint64_t* out, void* stream);
 
+/* Linear combination over Z_t (t = 2^t_bits of ctx), the HE-free online phase
+ * of the preprocessing protocol (Alg. 3: masked operands u - sum k_i u'_i and
+ * shares sum_i k_i <u'_i o v'_j>):
+ *   out[e] = addend[e] + s * sum_{i < terms} scalars[i] * src[src_offset
+ *            + (e / inner) * outer_stride + (e % inner) + i * term_stride]  mod t,
+ * e in [0, count), s = -1 if negate else +1.  src, addend (nullable), out: device
+ * arrays of Z_t values (out may alias addend, not src); scalars: host array of
+ * terms <= 64 values.  Errors: PENCIL_E_ARG for null pointers, negative sizes,
+ * inner < 1 or too many terms. */
+int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner, int64_t outer_stride,
+                   int64_t term_stride, const uint64_t* scalars, int32_t terms, const uint64_t* addend,
+                   int32_t negate, uint64_t* out, int64_t count, void* stream);
+
 /* In-place batched negacyclic NTT (inverse = 0) or INTT (inverse = 1) of
  * `count` polynomials laid out [count][L][N], canonical in and out (Sec. 5 "NTT"). */
 int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inverse, void* stream);
@@ -359,7 +377,7 @@ enum {
   PENCIL_K_NTT_RAW = 0, PENCIL_K_INTT_RAW, PENCIL_K_NTT_ENCRYPT, PENCIL_K_NTT_ADDPLAIN, PENCIL_K_NTT_ENCODE,
   PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
   PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_RING,
-  PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_COUNT
+  PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_LINCOMB, PENCIL_K_COUNT
 };
 typedef struct {
   int32_t kernel;   /* PENCIL_K_* */

@@ -9,8 +9,12 @@ Ciphertexts are kept in NTT form, limb-major: c[comp][limb][slot].
 
 * keygen   : s ternary (from `sampling.ternary_secret`), stored as NTT(s) per limb.
 * encrypt  : c1 = a (uniform, drawn directly in the NTT domain),
-             c0 = NTT(Delta*m + e) - a * NTT(s).
-* add_plain: c0 += NTT(Delta*m')   (Alg. 1 step 2: adding the MO's share).
+             c0 = NTT([q m / t] + e) - a * NTT(s), [.] rounding to nearest
+             (= Delta m + [(q mod t) m / t], the scaling of SEAL, which the
+             paper's GPU BFV follows): a plaintext-ciphertext product then
+             carries no (q mod t) x overflow term, so products of two uniform
+             Z_t values decrypt correctly at t = 2^59, q ~ 2^180 (Sec. 6).
+* add_plain: c0 += NTT([q m' / t])   (Alg. 1 step 2: adding the MO's share).
 * encode   : a signed integer polynomial lifted to every limb, in NTT form.
 * decrypt  : x = INTT(c0 + c1 * NTT(s)) per limb, recombined exactly by the
              Chinese remainder theorem into [0, q), and
@@ -69,12 +73,12 @@ def encode_plain(p: BfvParams, values: Sequence[int]) -> np.ndarray:
 
 
 def scaled_message(p: BfvParams, m: Sequence[int], e: Sequence[int] | None = None) -> np.ndarray:
-    """Delta * m + e per limb, coefficient form."""
-    d = p.delta
+    """round(q m / t) + e per limb (m read in [0, t)), coefficient form."""
+    Q, t = p.q, p.t
     if e is None:
         e = [0] * p.n
-    return np.stack([np.array([(d * int(mi) + int(ei)) % q for mi, ei in zip(m, e)],
-                              dtype=object) for q in p.primes])
+    sm = [(Q * (int(mi) % t) + t // 2) // t + int(ei) for mi, ei in zip(m, e)]
+    return np.stack([np.array([v % q for v in sm], dtype=object) for q in p.primes])
 
 
 def encrypt(p: BfvParams, sk: SecretKey, m: Sequence[int], seed: int, ct_index: int) -> np.ndarray:
@@ -91,7 +95,7 @@ def encrypt(p: BfvParams, sk: SecretKey, m: Sequence[int], seed: int, ct_index: 
 
 
 def add_plain(p: BfvParams, ct: np.ndarray, m: Sequence[int]) -> np.ndarray:
-    """ct + Delta * m (Alg. 1 step 2, adding a plaintext share)."""
+    """ct + round(q m / t) (Alg. 1 step 2, adding a plaintext share)."""
     out = ct.copy()
     add = to_ntt(p, scaled_message(p, m))
     for i, q in enumerate(p.primes):
@@ -100,7 +104,7 @@ def add_plain(p: BfvParams, ct: np.ndarray, m: Sequence[int]) -> np.ndarray:
 
 
 def sub_plain(p: BfvParams, ct: np.ndarray, m: Sequence[int]) -> np.ndarray:
-    """ct - Delta * m (Alg. 1 step 3, subtracting the mask)."""
+    """ct - round(q m / t) (Alg. 1 step 3, subtracting the mask)."""
     out = ct.copy()
     sub = to_ntt(p, scaled_message(p, m))
     for i, q in enumerate(p.primes):

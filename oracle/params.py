@@ -9,7 +9,8 @@ which needs q_i = 1 mod 2N and a primitive 2N-th root of unity psi_i.
 Readings (the paper leaves these open):
 * primes are the largest q_i < 2^bits with q_i = 1 mod 2N, in descending order;
 * psi_i is the numerically smallest primitive 2N-th root of unity mod q_i;
-* Delta = floor(q / t)  (the usual BFV scaling factor).
+* Delta = floor(q / t)  (the usual BFV scaling factor); messages are scaled as
+  round(q m / t) = Delta m + round((q mod t) m / t) (see bfv.py).
 """
 from __future__ import annotations
 

@@ -219,7 +219,7 @@ def mask_polynomial(p: BfvParams, layer: Layer, role: str, part: Partition,
 def mo_forward_ct(p: BfvParams, layer: Layer, role: str, part: Partition, ct_in: Dict,
                   pts: Dict, x0, mask_seed: int, ct_out: int) -> np.ndarray:
     """Alg. 1 steps 2-3 for one output ciphertext:
-    sum_k (ct_in[m,k] + Delta pi_v(x0)) * pt[k,n] - Delta s."""
+    sum_k (ct_in[m,k] + [q pi_v(x0) / t]) * pt[k,n] - [q s / t]."""
     g = geometry(layer, role)
     c = counts(g, part)
     m, nn = divmod(ct_out, c.NC)
@@ -235,7 +235,7 @@ def mo_forward_ct(p: BfvParams, layer: Layer, role: str, part: Partition, ct_in:
 def mo_wgrad_ct(p: BfvParams, layer: Layer, part: Partition, ct_x1: Dict, pt_gy0: Dict,
                 ct_gy1: Dict, pt_x0: Dict, mask_seed: int, ct_out: int) -> np.ndarray:
     """Alg. 2 steps 2-3 for one output ciphertext:
-    sum_k Enc(x1)[m,k] * gy0[k,n] + Enc(gy1)[k,n] * x0[m,k] - Delta s."""
+    sum_k Enc(x1)[m,k] * gy0[k,n] + Enc(gy1)[k,n] * x0[m,k] - [q s / t]."""
     g = geometry(layer, WGRAD)
     c = counts(g, part)
     m, nn = divmod(ct_out, c.NC)

@@ -1,6 +1,6 @@
 """Randomness of the protocol, drawn from fixed Philox streams (oracle).
 
-Sec. 2.2 (BFV): encryption of m is (c0, c1) = (-a*s + e + Delta*m, a) with a
+Sec. 2.2 (BFV): encryption of m is (c0, c1) = (-a*s + e + [q m / t], a) with a
 uniform, s the secret key and e a small error.  Alg. 1 step 3 (and Alg. 2
 step 3): the model owner draws a uniform mask s in Z_t.
 

@@ -326,6 +326,11 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     lc.nqtil = mulmod(lc.ninv, lc.qtil, q);
     lc.nqtils = shoup(lc.nqtil, q);
   }
+  {   // q_total mod t (t = 2^t_bits divides 2^64: the product of the primes mod 2^64, masked)
+    u64 qt = 1;
+    for (int j = 0; j < d.L; ++j) qt *= qs[j];
+    d.q_mod_t = qt & d.t_mask;
+  }
   d.mac_nt = 4;
   d.mac_staging = 1;   // measured: bulk copies by a producer warp, 4 columns per thread
   d.mac_split = 1;
@@ -1143,6 +1148,33 @@ extern "C" int pencil_ring_linear(PencilCtx* ctx, const PencilPlan* P, const uin
   R.t_mask = ctx->dev.t_mask;
   PROF(ctx, PENCIL_K_RING, s);
   CUDA_TRY(launch_ring(R, s));
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner,
+                              int64_t outer_stride, int64_t term_stride, const uint64_t* scalars, int32_t terms,
+                              const uint64_t* addend, int32_t negate, uint64_t* out, int64_t count, void* stream) {
+  if (!ctx || !src || !out || count < 0 || inner < 1 || src_offset < 0 || outer_stride < 0 || term_stride < 0)
+    return PENCIL_E_ARG;
+  if (terms < 0 || terms > PENCIL_LINCOMB_MAX_TERMS || (terms > 0 && !scalars)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  LincombP P;
+  memset(&P, 0, sizeof(P));
+  P.src = src;
+  P.off = src_offset;
+  P.inner = inner;
+  P.outer = outer_stride;
+  P.tstride = term_stride;
+  P.count = count;
+  P.addend = addend;
+  P.out = out;
+  P.terms = terms;
+  P.negate = negate ? 1 : 0;
+  for (int i = 0; i < terms; ++i) P.k[i] = scalars[i];
+  {
+    PROF(ctx, PENCIL_K_LINCOMB, (cudaStream_t)stream);
+    CUDA_TRY(launch_lincomb(P, ctx->dev.t_mask, (cudaStream_t)stream));
+  }
   return PENCIL_OK;
 }
 

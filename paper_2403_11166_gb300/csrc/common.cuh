@@ -39,6 +39,7 @@ struct DevCtx {
   int mac_split;             // 1: every q_j < 2^60 with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
   int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
   int mac_staging;           // operand staging of the split MAC: 0 per-thread cp.async ring, 1 bulk copies
+  u64 q_mod_t;               // (q_total mod t): messages are scaled as round(q_total m / t)
 };
 
 // A strided view of a user tensor seen as (a, b, r, s) with spatial zero
@@ -143,6 +144,17 @@ __host__ __device__ __forceinline__ void gs_bf4(u64& x, u64& y, u64 w, u64 ws, u
 }
 
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
+
+// round(q_total m / t) mod q_j for m in [0, t): Delta m + floor(((q_total mod t) m + t / 2) / t),
+// the BFV message scaling (t = 2^t_bits, so the division is a shift of the
+// 128-bit product; the quotient is below t < q_j).
+__device__ __forceinline__ u64 scale_msg(u64 m, const LimbConst& lc, const DevCtx& c) {
+  const u64 lo = c.q_mod_t * m, hi = __umul64hi(c.q_mod_t, m);
+  const u64 slo = lo + (1ull << (c.t_bits - 1));
+  const u64 shi = hi + (slo < lo ? 1ull : 0ull);
+  const u64 extra = (shi << (64 - c.t_bits)) | (slo >> c.t_bits);
+  return add_mod(mul_shoup(m, lc.delta, lc.deltas, lc.q), extra, lc.q);
+}
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
 
 // 128-bit accumulate: (hi, lo) += a * b.

@@ -1001,6 +1001,30 @@ cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_ma
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ linear combinations of shares
+// Online phase of the preprocessing protocol (Alg. 3): masked operands and
+// shares are linear combinations over Z_t, t = 2^t_bits (u64 wrap-around is
+// exact mod t):  out[e] = addend[e] (+ or -) sum_i k_i src[off + (e / inner) outer
+// + e % inner + i tstride].
+__global__ void k_lincomb(LincombP P, u64 t_mask) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P.count; e += stride) {
+    const long long base = P.off + (e / P.inner) * P.outer + e % P.inner;
+    u64 acc = 0;
+    for (int i = 0; i < P.terms; ++i) acc += P.k[i] * __ldg(P.src + base + i * P.tstride);
+    u64 v = P.addend ? __ldg(P.addend + e) : 0ull;
+    v = P.negate ? v - acc : v + acc;
+    P.out[e] = v & t_mask;
+  }
+}
+
+cudaError_t launch_lincomb(const LincombP& P, u64 t_mask, cudaStream_t s) {
+  if (P.count <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((P.count + 255) / 256, 152LL * 16);
+  k_lincomb<<<(unsigned)blocks, 256, 0, s>>>(P, t_mask);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ batched layers
 // Many linear layers (Alg. 1 forward) with a fixed launch sequence: every stage
 // of every layer runs in one multi-plan launch over (layer, polynomial) items,

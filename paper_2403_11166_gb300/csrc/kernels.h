@@ -30,6 +30,17 @@ struct MacParams {
   int m_base;
 };
 
+#define PENCIL_LINCOMB_MAX_TERMS 64
+struct LincombP {
+  const u64* src;
+  long long off, inner, outer, tstride, count;
+  const u64* addend;   // nullable
+  u64* out;
+  int terms, negate;
+  u64 k[PENCIL_LINCOMB_MAX_TERMS];
+};
+cudaError_t launch_lincomb(const LincombP& P, u64 t_mask, cudaStream_t s);
+
 cudaError_t upload_cdt();
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P, bool dual, cudaStream_t s);
 cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s);

@@ -278,7 +278,7 @@ struct ModeRaw {
   }
 };
 
-// DO encryption: prologue Delta*m + e (m gathered by the packing), epilogue
+// DO encryption: prologue round(q m / t) + e (m gathered by the packing), epilogue
 // c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain.
 struct ModeEncrypt {
   static constexpr bool kHeavyLoad = true;
@@ -298,7 +298,7 @@ struct ModeEncrypt {
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
     const u64 m = gather(P.pk, P.ac, poly, e) & c.t_mask;
-    const u64 r = mul_shoup(m, lc.delta, lc.deltas, lc.q);
+    const u64 r = scale_msg(m, lc, c);
     const int ee = P.err[(size_t)poly * N + e];
     return ee >= 0 ? add_mod(r, (u64)ee, lc.q) : sub_mod(r, (u64)(-ee), lc.q);
   }
@@ -343,8 +343,8 @@ struct ModeEncode {
 };
 
 // MO's ciphertext-independent terms of Alg. 1 steps 2-3, one launch for both:
-// polynomials [0, n_in) -> out_in = NTT(Delta * pi_v(x0)) (added to c0 by the
-// multiply-accumulate), [n_in, count) -> out_mask = NTT(Delta * s) of the mask
+// polynomials [0, n_in) -> out_in = NTT(round(q pi_v(x0) / t)) (added to c0 by the
+// multiply-accumulate), [n_in, count) -> out_mask = NTT(round(q s / t)) of the mask
 // polynomials (subtracted by the multiply-accumulate's store).
 struct ModeMoPrep {
   static constexpr bool kHeavyLoad = true;
@@ -364,7 +364,7 @@ struct ModeMoPrep {
                                              int e) {
     const u64 m = poly < P.n_in ? gather(P.pk, P.ac, poly, e) & c.t_mask
                                 : P.mpoly[(size_t)(poly - P.n_in) * N + e];
-    return mul_shoup(m, lc.delta, lc.deltas, lc.q);
+    return scale_msg(m, lc, c);
   }
   template <int N>
   static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,

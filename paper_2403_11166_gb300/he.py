@@ -34,14 +34,15 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "encrypt_share_noalloc", "pencil_ctx_tune", "pencil_ctx_get_tune", "pencil_batch_create",
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
-           "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice")
+           "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
+           "pencil_lincomb")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 TUNE_MAC_STAGING = 2
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
-                "ring", "bias_grad", "ntt_mo_prep")
+                "ring", "bias_grad", "ntt_mo_prep", "lincomb")
 
 
 class PencilError(RuntimeError):
@@ -94,6 +95,7 @@ def _load():
         "pencil_plan_linear": [P, ctypes.POINTER(LayerDesc), I32, ctypes.POINTER(Partition), ctypes.POINTER(P)],
         "pencil_plan_destroy": [P],
         "pencil_plan_slice": [P, I32, I32, ctypes.POINTER(P)],
+        "pencil_lincomb": [P, P, I64, I64, I64, I64, P, I32, P, I32, P, I64, P],
         "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
@@ -334,6 +336,16 @@ def he_linear_forward_apply(ctx: Context, plan: Plan, ct_in, pt, ct_out, ws, str
     w, nb = _ws(ws)
     _check(lib.he_linear_forward_apply(ctx.h, plan.h, _ptr(ct_in), _ptr(pt), _ptr(ct_out), w, nb, _stream(stream)),
            "he_linear_forward_apply")
+
+
+def pencil_lincomb(ctx: Context, src, scalars, count: int, out, addend=None, negate: bool = False,
+                   src_offset: int = 0, inner: int = None, outer_stride: int = 0, term_stride: int = 0, stream=None):
+    """out[e] = addend[e] +/- sum_i scalars[i] src[src_offset + (e // inner) outer_stride + e % inner
+    + i term_stride] mod t (see pencil_lincomb in the header)."""
+    ks = (ctypes.c_uint64 * max(1, len(scalars)))(*[int(v) for v in scalars])
+    _check(lib.pencil_lincomb(ctx.h, _ptr(src), src_offset, count if inner is None else inner, outer_stride,
+                              term_stride, ks, len(scalars), _ptr(addend), int(negate), _ptr(out), count,
+                              _stream(stream)), "pencil_lincomb")
 
 
 def he_linear_backward(ctx: Context, plan_dgrad, plan_wgrad, ct_gy1_d, pt_wt, ct_x1_w, ct_gy1_w, gy0, x0,

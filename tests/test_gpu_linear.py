@@ -427,3 +427,69 @@ def test_slice_validation(he):
     with pytest.raises(he.PencilError) as e:
         pw.slice(0, 1)
     assert e.value.code == -1
+
+
+# ---------------------------------------------------------------- the paper's own parameter set
+# N = 8192, three 60-bit primes, t = 2^59, f = 25 (Sec. 6 training parameters).
+T59 = 59
+
+
+@pytest.mark.parametrize("role", [FWD, DGRAD, WGRAD])
+def test_paper_parameter_set_t59_f25(he, role):
+    cfg = (13, 3, 60)
+    L = Layer("conv", B=3, Ci=4, Co=5, h=7, w=6, s=3, pad=1)
+    ctx = he.Context(*cfg, t_bits=T59)
+    p = BfvParams(log_n=13, num_primes=3, prime_bits=60, t_bits=T59)
+    sk = ctx.keygen(7)
+    osk = bfv.keygen(p, 7)
+    g = inputs.rng(59)
+    W = inputs.gaussian_fixed(g, L.w_shape(), frac_bits=25)
+    x = inputs.gaussian_fixed(g, L.x_shape(), frac_bits=25)
+    gy = inputs.gaussian_fixed(g, L.y_shape(), frac_bits=25)
+    x0, x1 = inputs.split_shares(g, x, t_bits=T59)
+    gy0, gy1 = inputs.split_shares(g, gy, t_bits=T59)
+    mask = np.uint64((1 << T59) - 1)
+    hrole = {FWD: he.ROLE_FWD, DGRAD: he.ROLE_DGRAD, WGRAD: he.ROLE_WGRAD}[role]
+    plan = he.Plan(ctx, _he_layer(he, L), hrole, None)
+    S = plan.sizes
+    opart = Partition(*plan.part)
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_backward, S.ws_decrypt))
+    if role in (FWD, DGRAD):
+        v0, v1 = (x0, x1) if role == FWD else (gy0, gy1)
+        pt = plan.new_pt(S.pt)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, to_dev(W), pt)
+        ct_in, ct_out = plan.new_ct(S.ct_in), plan.new_ct(S.ct_out)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(v1), 5, ct_in, ws)
+        y0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+        y1 = torch.empty_like(y0)
+        if role == FWD:
+            he.he_linear_forward(ctx, plan, ct_in, pt, to_dev(v0), None, 6, ct_out, y0, ws)
+        else:
+            he.he_linear_backward(ctx, plan, None, ct_in, pt, None, None, to_dev(v0), None, 6, 0, ct_out, y0, None,
+                                  None, ws)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws)
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        oy0, oy1, _, _, oct_out = protocol.he_linear(p, osk, L, role, opart, W, v1, v0, 5, 6)
+        assert (to_np(y0) == np.asarray(oy0, dtype=np.uint64).reshape(-1)).all()
+        assert (to_np(y1) == np.asarray(oy1, dtype=np.uint64).reshape(-1)).all()
+        o = S.ct_out - 1
+        assert (to_np(ct_out)[o] == as_u64(oct_out[o])).all()
+        ref = protocol.ring_op(L, role, W, x if role == FWD else gy, T59).reshape(-1)
+        with np.errstate(over="ignore"):
+            assert (((to_np(y0) + to_np(y1)) & mask) == ref).all()
+    else:
+        ct_x1, ct_g1, ct_gw = plan.new_ct(S.ct_in), plan.new_ct(S.pt), plan.new_ct(S.ct_out)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), 31, ct_x1, ws)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_KERNEL, to_dev(gy1), 32, ct_g1, ws)
+        gw_mask = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+        tilde = torch.empty_like(gw_mask)
+        he.he_linear_backward(ctx, None, plan, None, None, ct_x1, ct_g1, to_dev(gy0), to_dev(x0), 0, 33,
+                              None, None, ct_gw, gw_mask, ws)
+        he.decrypt_to_share(ctx, sk, plan, ct_gw, tilde, True, ws)
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        gw, want_tilde, want_s = protocol.he_wgrad(p, osk, L, opart, gy0, gy1, x0, x1, 31, 32, 33)
+        assert (to_np(gw_mask) == want_s.reshape(-1)).all()
+        assert (to_np(tilde) == want_tilde.reshape(-1)).all()
+        assert (gw == protocol.ring_op(L, WGRAD, gy, x, T59)).all()

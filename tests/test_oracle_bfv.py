@@ -69,3 +69,22 @@ def test_noise_check_flags_corruption():
     bad[0, 0, 3] = (bad[0, 0, 3] + p.primes[0] // 3) % p.primes[0]
     assert bfv.noise_budget_ok(p, sk, ct)
     assert not bfv.noise_budget_ok(p, sk, bad)
+
+
+def test_uniform_product_at_paper_parameters_decrypts():
+    """t = 2^59, q ~ 2^180 (Sec. 6): Dec(w * Enc(m) - s) + s = w * m mod t for
+    UNIFORM w and m in Z_t (Alg. 2's cross terms multiply two shares).  With the
+    plain Delta m scaling the (q mod t) x overflow term of this product exceeds
+    Delta / 2 and decryption fails; with round(q m / t) it does not."""
+    p = BfvParams(log_n=10, num_primes=3, prime_bits=60, t_bits=59)
+    sk = bfv.keygen(p, 17)
+    g = np.random.default_rng(5)
+    m = [int(v) for v in g.integers(0, p.t, p.n, dtype=np.uint64)]
+    w = [int(v) for v in g.integers(0, p.t, p.n, dtype=np.uint64)]
+    s = [int(v) for v in g.integers(0, p.t, p.n, dtype=np.uint64)]
+    ct = bfv.mul_plain(p, bfv.encrypt(p, sk, m, 3, 0), bfv.encode_plain(p, w))
+    ct = bfv.sub_plain(p, ct, s)
+    assert bfv.noise_budget_ok(p, sk, ct)
+    got = bfv.decrypt(p, sk, ct)
+    want = negacyclic_schoolbook([bfv.centered(v, p.t) for v in w], m, p.t)
+    assert [(a + b) % p.t for a, b in zip(got, s)] == [int(v) % p.t for v in want]
