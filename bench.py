@@ -405,9 +405,56 @@ def large_conv(he, device: int, reps: int = 3):
                                                                   ("wgrad", he.ROLE_WGRAD))}}
 
 
+def pencil_plus(he, device: int, m: int = 8, reps: int = 3):
+    """Preprocessing protocol (Alg. 3) for the forward product of the headline layer
+    (conv3x3 16->16, 32x32, B = 64, N = 8192) with m masks per party: the one-time
+    preprocessing (all m^2 products in one stacked Alg. 1 evaluation) and the
+    HE-free online phase, next to the HE online forward it replaces."""
+    import torch
+    from paper_2403_11166_gb300 import inputs, prep
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=device)
+    sk = ctx.keygen(77)
+    Ly = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
+                  LAYER["pad"])
+    g = inputs.rng(78)
+    dev = f"cuda:{device}"
+    W = torch.as_tensor(inputs.gaussian_fixed(g, (LAYER["c_out"], LAYER["c_in"], 3, 3)), device=dev)
+    xs = (LAYER["batch"], LAYER["c_in"], LAYER["h"], LAYER["w"])
+    x1 = torch.as_tensor(inputs.uniform_zt(g, xs).view(np.int64), device=dev)
+    U = torch.as_tensor(inputs.uniform_zt(g, (m * LAYER["c_out"], LAYER["c_in"], 3, 3)).view(np.int64), device=dev)
+    V = torch.as_tensor(inputs.uniform_zt(g, (m * LAYER["batch"],) + xs[1:]).view(np.int64), device=dev)
+    pp = prep.PrepProduct(ctx, sk, Ly, he.ROLE_FWD, m)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pp.preprocess(U, V, 91, 92)
+    b.record()
+    b.synchronize()
+    prep_ms = a.elapsed_time(b)
+    k = [int(v) for v in inputs.uniform_zt(g, (m,))]
+    l = [int(v) for v in inputs.uniform_zt(g, (m,))]
+    pp.online(W, x1, k, l)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        a.record()
+        pp.online(W, x1, k, l)
+        b.record()
+        b.synchronize()
+        t.append(a.elapsed_time(b))
+    assert ctx.sync_status() == 0
+    out = {"m": m, "preprocessing_ms": prep_ms, "preprocessing_products": pp.products,
+           "online_ms": statistics.median(t), "online_products_equivalent": pp.plan.sizes.products,
+           "online_he_free": True}
+    del pp
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def extras(he, device: int):
     return {"batched_uneven": batched_uneven(he, device), "training_step_cnn": training_step(he, device),
-            "large_conv_128_fwd_bwd": large_conv(he, device)}
+            "large_conv_128_fwd_bwd": large_conv(he, device), "pencil_plus_fwd_m8": pencil_plus(he, device)}
 
 
 # ---------------------------------------------------------------- oracle timing (host cores)

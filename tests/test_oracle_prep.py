@@ -8,7 +8,7 @@ import pytest
 from oracle import bfv, prep, protocol
 from oracle.packing import Partition
 from oracle.params import BfvParams
-from oracle.protocol import DGRAD, FWD, Layer
+from oracle.protocol import DGRAD, FWD, WGRAD, Layer
 from paper_2403_11166_gb300 import inputs
 
 T = 41
@@ -24,15 +24,33 @@ CASES = [
     (Layer("conv", B=1, Ci=2, Co=2, h=4, w=4, s=3, pad=1), FWD, 2, Partition(2, 2, 4, 4, 4, 3, 3)),
     (Layer("conv", B=1, Ci=2, Co=2, h=4, w=4, s=3, pad=1), DGRAD, 2, Partition(2, 2, 4, 4, 4, 3, 3)),
     (Layer("fc", B=2, Ci=5, Co=3), FWD, 3, Partition(6, 5, 9, 1, 1, 1, 1)),
+    (Layer("conv", B=2, Ci=2, Co=2, h=4, w=4, s=3, pad=1), WGRAD, 2, None),
+    (Layer("conv", B=2, Ci=2, Co=2, h=4, w=4, s=3, pad=1), prep.WGRAD_REV, 2, None),
+    (Layer("fc", B=3, Ci=4, Co=3), WGRAD, 2, None),
 ]
+
+
+def _shapes(L, role):
+    """(u shape, v shape) of the operator."""
+    return {FWD: (L.w_shape(), L.x_shape()), DGRAD: (L.w_shape(), L.y_shape()),
+            WGRAD: (L.y_shape(), L.x_shape()), prep.WGRAD_REV: (L.x_shape(), L.y_shape())}[role]
+
+
+def _part(L, role, m, n):
+    """One polynomial per (batch item, channel pair): the whole output window in one tile."""
+    Ls = prep.stacked_layer(L, role, m)
+    g = protocol.geometry(Ls, WGRAD if role == prep.WGRAD_REV else role)
+    part = Partition(1, 1, 1, g.Ho, g.Wo, g.KH, g.KW)
+    assert part.fits(n)
+    return part
 
 
 def _operands(L, role, m, seed):
     g = inputs.rng(seed)
-    u = inputs.gaussian_fixed(g, L.w_shape())
-    vshape = L.x_shape() if role == FWD else L.y_shape()
+    ushape, vshape = _shapes(L, role)
+    u = inputs.gaussian_fixed(g, ushape) if role in (FWD, DGRAD) else inputs.uniform_zt(g, ushape)
     v = inputs.uniform_zt(g, vshape)
-    u_masks = [inputs.uniform_zt(g, L.w_shape()) for _ in range(m)]
+    u_masks = [inputs.uniform_zt(g, ushape) for _ in range(m)]
     v_masks = [inputs.uniform_zt(g, vshape) for _ in range(m)]
     k = [int(a) for a in inputs.uniform_zt(g, (m,))]
     l = [int(a) for a in inputs.uniform_zt(g, (m,))]
@@ -42,17 +60,19 @@ def _operands(L, role, m, seed):
 @pytest.mark.parametrize("L,role,m,part", CASES)
 def test_prep_blocks_are_the_products_and_online_reconstructs(L, role, m, part):
     p = BfvParams(log_n=10, num_primes=3, prime_bits=60)   # room for uniform Z_t masks in the product
+    if part is None:
+        part = _part(L, role, m, p.n)
     assert part.fits(p.n)
     sk = bfv.keygen(p, 3)
     u, v, um, vm, k, l = _operands(L, role, m, 5)
     S0, S1 = prep.prep(p, sk, L, role, part, um, vm, 11, 12)
     for i in range(m):
         for j in range(m):
-            want = protocol.ring_op(L, role, um[i], vm[j], T)
+            want = prep.op(L, role, um[i], vm[j], T)
             got = _add(prep.block(S0, L, role, i, j), prep.block(S1, L, role, i, j))
             assert (got == want).all(), (i, j)
     ut, vt, z0, z1 = prep.online(L, role, u, v, um, vm, S0, S1, k, l, T)
-    assert (_add(z0, z1) == protocol.ring_op(L, role, u, v, T)).all()
+    assert (_add(z0, z1) == prep.op(L, role, u, v, T)).all()
     # the masked operands are what the parties send: u~ + sum k u' = u, v~ + sum l v' = v
     with np.errstate(over="ignore"):
         back_u = ut.copy()
