@@ -444,7 +444,7 @@ def pencil_plus(he, device: int, m: int = 8, reps: int = 3):
         t.append(a.elapsed_time(b))
     assert ctx.sync_status() == 0
     out = {"m": m, "preprocessing_ms": prep_ms, "preprocessing_products": pp.products,
-           "online_ms": statistics.median(t), "online_products_equivalent": pp.plan.sizes.products,
+           "online_ms": statistics.median(t), "online_products_equivalent": pp.plan_one.sizes.products,
            "online_he_free": True}
     del pp
     ctx.close()

@@ -909,25 +909,6 @@ cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const A
 //   out[flat(a, o, i, j)] = addend[flat] + sum_{c, u, v} Wt(o, c, u, v) V(a, c, i + u, j + v)  (mod t)
 // Reduction length R = Ci * KH * KW.  Short reductions: one thread per output;
 // long ones (grad_W: R = batch x H_out x W_out): one block per output.
-__device__ __forceinline__ u64 ring_term(const RingParams& P, int a, int o, int i, int j, long long r) {
-  const int KW = P.kbound.w, KH = P.kbound.z;
-  const int v = (int)(r % KW);
-  const int u = (int)((r / KW) % KH);
-  const int c = (int)(r / ((long long)KW * KH));
-  int rr = i + u - P.v.pr, ss = j + v - P.v.ps;
-  if ((unsigned)rr >= (unsigned)P.v.hr || (unsigned)ss >= (unsigned)P.v.wr) return 0;
-  const u64 x = __ldg(P.v.ptr + P.v.base + a * P.v.s0 + c * P.v.s1 + rr * P.v.s2 + ss * P.v.s3);
-  const u64 w = __ldg(P.w.ptr + P.w.base + o * P.w.s0 + c * P.w.s1 + u * P.w.s2 + v * P.w.s3);
-  return x * w;
-}
-
-__device__ __forceinline__ void ring_coords(const RingParams& P, long long id, int& a, int& o, int& i, int& j) {
-  j = (int)(id % P.Wo);
-  i = (int)((id / P.Wo) % P.Ho);
-  o = (int)((id / ((long long)P.Wo * P.Ho)) % P.kbound.x);
-  a = (int)(id / ((long long)P.Wo * P.Ho * P.kbound.x));
-}
-
 __device__ __forceinline__ void ring_store(const RingParams& P, int a, int o, int i, int j, u64 acc) {
   const i64 flat = P.y.base + a * P.y.s0 + o * P.y.s1 + i * P.y.s2 + j * P.y.s3;
   if (P.addend) acc += P.addend[flat];
@@ -935,22 +916,68 @@ __device__ __forceinline__ void ring_store(const RingParams& P, int a, int o, in
   P.out[flat] = acc & P.t_mask;
 }
 
-__global__ void k_ring_thread(RingParams P, long long R) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= P.outs) return;
-  int a, o, i, j;
-  ring_coords(P, id, a, o, i, j);
-  u64 acc = 0;
-  for (long long r = 0; r < R; ++r) acc += ring_term(P, a, o, i, j, r);
-  ring_store(P, a, o, i, j, acc);
+// Short reductions: thread = output position (a, i, j) x RT consecutive output
+// channels o; the reduction runs over (c, u, v) in nested loops (no divisions),
+// each input value loaded once for the RT channels; the kernel values are the
+// same for every thread of the CTA (one channel tile per grid row: broadcast).
+#define RING_OT 4
+__global__ void __launch_bounds__(128) k_ring_tile(RingParams P) {
+  const long long HWo = (long long)P.Ho * P.Wo;
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o0 = blockIdx.y * RING_OT;
+  const int Co = P.kbound.x, Ci = P.kbound.y, KH = P.kbound.z, KW = P.kbound.w;
+  if (pos >= P.outs / Co) return;
+  const int a = (int)(pos / HWo);
+  const int p = (int)(pos - (long long)a * HWo);
+  const int i = p / P.Wo, j = p - (p / P.Wo) * P.Wo;
+  const int no = min(RING_OT, Co - o0);
+  u64 acc[RING_OT];
+#pragma unroll
+  for (int t = 0; t < RING_OT; ++t) acc[t] = 0;
+  const u64* vb = P.v.ptr + P.v.base + a * P.v.s0;
+  const u64* wb = P.w.ptr + P.w.base + (i64)o0 * P.w.s0;
+  for (int c = 0; c < Ci; ++c) {
+    for (int u = 0; u < KH; ++u) {
+      const int rr = i + u - P.v.pr;
+      if ((unsigned)rr >= (unsigned)P.v.hr) continue;
+      for (int v = 0; v < KW; ++v) {
+        const int ss = j + v - P.v.ps;
+        if ((unsigned)ss >= (unsigned)P.v.wr) continue;
+        const u64 x = __ldg(vb + c * P.v.s1 + rr * P.v.s2 + ss * P.v.s3);
+        const u64* w = wb + c * P.w.s1 + u * P.w.s2 + v * P.w.s3;
+#pragma unroll
+        for (int t = 0; t < RING_OT; ++t)
+          if (t < no) acc[t] += x * __ldg(w + t * P.w.s0);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RING_OT; ++t)
+    if (t < no) ring_store(P, a, o0 + t, i, j, acc[t]);
 }
 
-__global__ void __launch_bounds__(256) k_ring_block(RingParams P, long long R) {
+// Long reductions (grad_W: over batch x output positions): one CTA per output,
+// threads over the (u, v) positions of each c (consecutive threads read
+// consecutive elements).
+__global__ void __launch_bounds__(256) k_ring_block(RingParams P) {
   const long long id = blockIdx.x;
-  int a, o, i, j;
-  ring_coords(P, id, a, o, i, j);
+  const int KH = P.kbound.z, KW = P.kbound.w, Ci = P.kbound.y;
+  const int j = (int)(id % P.Wo);
+  const int i = (int)((id / P.Wo) % P.Ho);
+  const int o = (int)((id / ((long long)P.Wo * P.Ho)) % P.kbound.x);
+  const int a = (int)(id / ((long long)P.Wo * P.Ho * P.kbound.x));
+  const int UV = KH * KW;
   u64 acc = 0;
-  for (long long r = threadIdx.x; r < R; r += blockDim.x) acc += ring_term(P, a, o, i, j, r);
+  const u64* vb = P.v.ptr + P.v.base + a * P.v.s0;
+  const u64* wb = P.w.ptr + P.w.base + o * P.w.s0;
+  for (int c = 0; c < Ci; ++c) {
+    for (int q = threadIdx.x; q < UV; q += blockDim.x) {
+      const int u = q / KW, v = q - (q / KW) * KW;
+      const int rr = i + u - P.v.pr, ss = j + v - P.v.ps;
+      if ((unsigned)rr >= (unsigned)P.v.hr || (unsigned)ss >= (unsigned)P.v.wr) continue;
+      acc += __ldg(vb + c * P.v.s1 + rr * P.v.s2 + ss * P.v.s3) * __ldg(wb + c * P.w.s1 + u * P.w.s2 + v * P.w.s3);
+    }
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
   __shared__ u64 part[8];
@@ -966,10 +993,15 @@ __global__ void __launch_bounds__(256) k_ring_block(RingParams P, long long R) {
 cudaError_t launch_ring(const RingParams& P, cudaStream_t s) {
   const long long R = (long long)P.kbound.y * P.kbound.z * P.kbound.w;
   if (P.outs == 0) return cudaSuccess;
-  if (R >= 2048 && P.outs <= (1ll << 31) - 1) {
-    k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P, R);
+  if ((long long)P.kbound.z * P.kbound.w >= 256 && P.outs <= (1ll << 31) - 1) {
+    k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P);
   } else {
-    k_ring_thread<<<(unsigned)((P.outs + 255) / 256), 256, 0, s>>>(P, R);
+    const long long positions = P.outs / P.kbound.x;
+    const unsigned gx = (unsigned)((positions + 127) / 128);
+    const unsigned gy = (unsigned)((P.kbound.x + RING_OT - 1) / RING_OT);
+    if (gy > 65535) return cudaErrorInvalidValue;
+    (void)R;
+    k_ring_tile<<<dim3(gx, gy), 128, 0, s>>>(P);
   }
   return cudaGetLastError();
 }
