@@ -452,9 +452,65 @@ def pencil_plus(he, device: int, m: int = 8, reps: int = 3):
     return out
 
 
+# The paper's single-layer shapes (Table V: batch 64, online training of one
+# linear layer; conv padding "same"), with its A6000 per-sample times as context.
+TABLE5 = [("fc", 256, 100, 1, 1, 6.8), ("fc", 512, 10, 1, 1, 2.6), ("fc", 2048, 1001, 1, 1, 256.1),
+          ("conv", 64, 64, 16, 5, 165.0), ("conv", 3, 64, 56, 3, 244.0), ("conv", 64, 3, 56, 3, 237.0)]
+
+
+def table5_layers(he, device: int, reps: int = 2):
+    """Forward + grad_X + grad_W of each layer through the HE path (Alg. 1, Alg. 2),
+    N = 8192, batch 64: ms per layer step and per sample, ciphertext bytes per sample."""
+    import torch
+    from paper_2403_11166_gb300 import autograd, inputs
+    out = []
+    for kind, ci, co, hw, ks, paper_ms in TABLE5:
+        sess = autograd.HeSession(LOG_N, L, PRIME_BITS, T_BITS, seed=11, device=device)
+        B = 64
+        if kind == "fc":
+            Ly = he.Layer(he.FC, B, ci, co, 1, 1, 1, 0)
+            xs, ys, ws = (B, ci), (B, co), (co, ci)
+        else:
+            Ly = he.Layer(he.CONV, B, ci, co, hw, hw, ks, ks // 2)
+            xs, ys, ws = (B, ci, hw, hw), (B, co, hw, hw), (co, ci, ks, ks)
+        g = inputs.rng(12)
+        dev = sess.device
+        W = torch.as_tensor(inputs.gaussian_fixed(g, ws), device=dev) & sess.mask
+        x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+                  inputs.split_shares(g, inputs.gaussian_fixed(g, xs)))
+        g0, g1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+                  inputs.split_shares(g, inputs.gaussian_fixed(g, ys)))
+
+        def step():
+            sess.forward(Ly, W, None, x0, x1)
+            sess.backward(Ly, W, x0, x1, g0, g1, True)
+        step()
+        torch.cuda.synchronize()
+        sess.bytes_do_to_mo = sess.bytes_mo_to_do = 0
+        t = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        assert sess.ctx.sync_status() == 0
+        ms = statistics.median(t)
+        comm = (sess.bytes_do_to_mo + sess.bytes_mo_to_do) / reps
+        out.append({"layer": f"{kind} {ci}->{co}" + (f" {hw}x{hw} k{ks}" if kind == "conv" else ""),
+                    "ms_fwd_bwd": round(ms, 3), "ms_per_sample": round(ms / B, 4),
+                    "ciphertext_MB_per_sample": round(comm / B / 1e6, 3),
+                    "paper_a6000_ms_per_sample_context": paper_ms})
+        del sess
+        torch.cuda.empty_cache()
+    return out
+
+
 def extras(he, device: int):
     return {"batched_uneven": batched_uneven(he, device), "training_step_cnn": training_step(he, device),
-            "large_conv_128_fwd_bwd": large_conv(he, device), "pencil_plus_fwd_m8": pencil_plus(he, device)}
+            "large_conv_128_fwd_bwd": large_conv(he, device), "pencil_plus_fwd_m8": pencil_plus(he, device),
+            "paper_table5_layers_b64": table5_layers(he, device)}
 
 
 # ---------------------------------------------------------------- oracle timing (host cores)
