@@ -90,6 +90,16 @@ int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
  * warp per CTA copies whole 1 KB operand rows with bulk asynchronous copies
  * (cp.async.bulk + mbarrier), the other warps only multiply. */
 enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1, PENCIL_TUNE_MAC_STAGING = 2 };
+
+/* Noise flooding of the ciphertexts the MO returns (circuit privacy; the paper
+ * is silent, no counterpart): with bits > 0, every later he_linear_forward(_prepare)
+ * and he_linear_backward (and batch commit) adds NTT(f) to each output
+ * ciphertext, f_i uniform in [-2^bits, 2^bits) from Philox (key (mask_seed, 6),
+ * counter (i / 4, output ciphertext index, 0, 0), word i % 4; for a batch,
+ * mask_seed + layer).  Decrypted shares are unchanged.  bits = 0 turns it off.
+ * Errors: PENCIL_E_ARG for bits outside [0, 62], PENCIL_E_PARAMS when
+ * log2 q - t_bits - bits < 8 (no noise room). */
+int pencil_ctx_flooding(PencilCtx* ctx, int32_t bits);
 int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value);
 int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value);
 

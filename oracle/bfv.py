@@ -103,6 +103,16 @@ def add_plain(p: BfvParams, ct: np.ndarray, m: Sequence[int]) -> np.ndarray:
     return out
 
 
+def add_noise(p: BfvParams, ct: np.ndarray, f: Sequence[int]) -> np.ndarray:
+    """c0 += NTT(f) for an integer polynomial f (flooding the noise of a returned
+    ciphertext; its plaintext is unchanged while |noise + f| < Delta / 2)."""
+    out = ct.copy()
+    add = to_ntt(p, lift_plain(p, f))
+    for i, q in enumerate(p.primes):
+        out[0, i] = (out[0, i] + add[i]) % q
+    return out
+
+
 def sub_plain(p: BfvParams, ct: np.ndarray, m: Sequence[int]) -> np.ndarray:
     """ct - round(q m / t) (Alg. 1 step 3, subtracting the mask)."""
     out = ct.copy()

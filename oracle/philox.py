@@ -49,6 +49,7 @@ DOMAIN_A = 2           # encryption mask a:     ctr = (i // 2, ct, limb, 0), wor
 DOMAIN_E = 3           # encryption error e:    ctr = (i // 4, ct, 0, 0),  word i % 4
 DOMAIN_MASK = 4        # re-mask, per output element: ctr = (flat // 4, 0, 0, 0), word flat % 4
 DOMAIN_MASK_PAD = 5    # re-mask, unused ct coefficients: ctr = (i // 4, ct_out, 0, 0), word i % 4
+DOMAIN_FLOOD = 6       # flooding noise of returned cts: ctr = (i // 4, ct_out, 0, 0), word i % 4
 
 
 def word(seed: int, domain: int, block: int, a: int = 0, b: int = 0, lane: int = 0) -> int:

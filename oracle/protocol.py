@@ -34,7 +34,7 @@ from .packing import (Geometry, Partition, counts, decode_positions, pack_input,
 from .params import BfvParams
 from .ring import (ring_conv2d, ring_conv2d_dgrad, ring_conv2d_wgrad, ring_matmul,
                    ring_matmul_dgrad, ring_matmul_wgrad)
-from .sampling import mask_elements, mask_pad
+from .sampling import flood_noise, mask_elements, mask_pad
 
 FWD, DGRAD, WGRAD = "fwd", "dgrad", "wgrad"
 
@@ -216,10 +216,17 @@ def mask_polynomial(p: BfvParams, layer: Layer, role: str, part: Partition,
     return poly
 
 
+def flood(p: BfvParams, ct: np.ndarray, mask_seed: int, ct_out: int, flood_bits: int) -> np.ndarray:
+    """Noise flooding of a returned ciphertext (no-op for flood_bits = 0)."""
+    if not flood_bits:
+        return ct
+    return bfv.add_noise(p, ct, flood_noise(mask_seed, ct_out, p.n, flood_bits))
+
+
 def mo_forward_ct(p: BfvParams, layer: Layer, role: str, part: Partition, ct_in: Dict,
-                  pts: Dict, x0, mask_seed: int, ct_out: int) -> np.ndarray:
+                  pts: Dict, x0, mask_seed: int, ct_out: int, flood_bits: int = 0) -> np.ndarray:
     """Alg. 1 steps 2-3 for one output ciphertext:
-    sum_k (ct_in[m,k] + [q pi_v(x0) / t]) * pt[k,n] - [q s / t]."""
+    sum_k (ct_in[m,k] + [q pi_v(x0) / t]) * pt[k,n] - [q s / t] (+ flooding noise)."""
     g = geometry(layer, role)
     c = counts(g, part)
     m, nn = divmod(ct_out, c.NC)
@@ -229,11 +236,12 @@ def mo_forward_ct(p: BfvParams, layer: Layer, role: str, part: Partition, ct_in:
         ct = bfv.add_plain(p, ct_in[m * c.K + k], pack_input(V0, g, part, p.n, m, k))
         prod = bfv.mul_plain(p, ct, pts[k * c.NC + nn])
         acc = prod if acc is None else bfv.add_ct(p, acc, prod)
-    return bfv.sub_plain(p, acc, mask_polynomial(p, layer, role, part, mask_seed, ct_out))
+    out = bfv.sub_plain(p, acc, mask_polynomial(p, layer, role, part, mask_seed, ct_out))
+    return flood(p, out, mask_seed, ct_out, flood_bits)
 
 
 def mo_wgrad_ct(p: BfvParams, layer: Layer, part: Partition, ct_x1: Dict, pt_gy0: Dict,
-                ct_gy1: Dict, pt_x0: Dict, mask_seed: int, ct_out: int) -> np.ndarray:
+                ct_gy1: Dict, pt_x0: Dict, mask_seed: int, ct_out: int, flood_bits: int = 0) -> np.ndarray:
     """Alg. 2 steps 2-3 for one output ciphertext:
     sum_k Enc(x1)[m,k] * gy0[k,n] + Enc(gy1)[k,n] * x0[m,k] - [q s / t]."""
     g = geometry(layer, WGRAD)
@@ -245,7 +253,8 @@ def mo_wgrad_ct(p: BfvParams, layer: Layer, part: Partition, ct_x1: Dict, pt_gy0
         b = bfv.mul_plain(p, ct_gy1[k * c.NC + nn], pt_x0[m * c.K + k])
         term = bfv.add_ct(p, a, b)
         acc = term if acc is None else bfv.add_ct(p, acc, term)
-    return bfv.sub_plain(p, acc, mask_polynomial(p, layer, WGRAD, part, mask_seed, ct_out))
+    out = bfv.sub_plain(p, acc, mask_polynomial(p, layer, WGRAD, part, mask_seed, ct_out))
+    return flood(p, out, mask_seed, ct_out, flood_bits)
 
 
 def decrypt_outputs(p: BfvParams, sk, layer: Layer, role: str, part: Partition,
@@ -275,13 +284,13 @@ def mo_share(p: BfvParams, layer: Layer, role: str, mask_seed: int, bias=None) -
 
 
 def he_linear(p: BfvParams, sk, layer: Layer, role: str, part: Partition, kernel, x1, x0,
-              enc_seed: int, mask_seed: int, bias=None):
+              enc_seed: int, mask_seed: int, bias=None, flood_bits: int = 0):
     """Full Alg. 1 (fwd / dgrad roles) on small shapes: returns (y0, y1, ct_in, pts, ct_out)."""
     g = geometry(layer, role)
     c = counts(g, part)
     ct_in = encrypt_inputs(p, sk, layer, role, part, x1, enc_seed)
     pts = encode_kernel(p, layer, role, part, kernel)
-    ct_out = {i: mo_forward_ct(p, layer, role, part, ct_in, pts, x0, mask_seed, i)
+    ct_out = {i: mo_forward_ct(p, layer, role, part, ct_in, pts, x0, mask_seed, i, flood_bits)
               for i in range(c.ct_out)}
     y1 = decrypt_outputs(p, sk, layer, role, part, ct_out).reshape(output_shape(layer, role))
     y0 = mo_share(p, layer, role, mask_seed, bias)
@@ -289,7 +298,7 @@ def he_linear(p: BfvParams, sk, layer: Layer, role: str, part: Partition, kernel
 
 
 def he_wgrad(p: BfvParams, sk, layer: Layer, part: Partition, gy0, gy1, x0, x1,
-             enc_seed_x: int, enc_seed_g: int, mask_seed: int):
+             enc_seed_x: int, enc_seed_g: int, mask_seed: int, flood_bits: int = 0):
     """Full Alg. 2 on small shapes.  Returns (grad_W, DO's decrypted tilde, MO mask)."""
     g = geometry(layer, WGRAD)
     c = counts(g, part)
@@ -297,7 +306,7 @@ def he_wgrad(p: BfvParams, sk, layer: Layer, part: Partition, gy0, gy1, x0, x1,
     ct_gy1 = encrypt_kernel_operand(p, sk, layer, WGRAD, part, gy1, enc_seed_g)
     pt_gy0 = encode_kernel(p, layer, WGRAD, part, gy0)
     pt_x0 = encode_input(p, layer, WGRAD, part, x0)
-    ct_out = {i: mo_wgrad_ct(p, layer, part, ct_x1, pt_gy0, ct_gy1, pt_x0, mask_seed, i)
+    ct_out = {i: mo_wgrad_ct(p, layer, part, ct_x1, pt_gy0, ct_gy1, pt_x0, mask_seed, i, flood_bits)
               for i in range(c.ct_out)}
     shape = output_shape(layer, WGRAD)
     tilde = decrypt_outputs(p, sk, layer, WGRAD, part, ct_out).reshape(shape)

@@ -16,7 +16,7 @@ from typing import List
 
 import mpmath
 
-from .philox import (DOMAIN_A, DOMAIN_E, DOMAIN_MASK, DOMAIN_MASK_PAD,
+from .philox import (DOMAIN_A, DOMAIN_E, DOMAIN_MASK, DOMAIN_MASK_PAD, DOMAIN_FLOOD,
                      DOMAIN_SECRET, philox4x64)
 
 CDT_TAIL = 19
@@ -102,4 +102,15 @@ def mask_pad(seed: int, ct_out: int, n: int, t: int) -> List[int]:
     out = []
     for blk in range(n // 4):
         out.extend(x % t for x in philox4x64((blk, ct_out, 0, 0), (seed, DOMAIN_MASK_PAD)))
+    return out
+
+
+def flood_noise(seed: int, ct_out: int, n: int, bits: int) -> List[int]:
+    """Flooding noise added to returned ciphertext ct_out: coefficient i is
+    (w mod 2^(bits+1)) - 2^bits, uniform in [-2^bits, 2^bits), w = Philox word
+    (key (seed, DOMAIN_FLOOD), counter (i / 4, ct_out, 0, 0)) i % 4."""
+    out = []
+    for blk in range(n // 4):
+        out.extend((x % (1 << (bits + 1))) - (1 << bits)
+                   for x in philox4x64((blk, ct_out, 0, 0), (seed, DOMAIN_FLOOD)))
     return out

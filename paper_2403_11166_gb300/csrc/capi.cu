@@ -400,6 +400,17 @@ extern "C" int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value) {
   return PENCIL_E_ARG;
 }
 
+extern "C" int pencil_ctx_flooding(PencilCtx* ctx, int32_t bits) {
+  if (!ctx) return PENCIL_E_ARG;
+  if (bits < 0 || bits > 62) return PENCIL_E_ARG;
+  // the flooded noise must stay far below Delta / 2: log2 q_total - t_bits - bits >= 8
+  int qbits = 0;
+  for (u64 q : ctx->primes) qbits += 64 - __builtin_clzll(q);
+  if (bits > 0 && qbits - 1 - ctx->dev.t_bits - bits < 8) return PENCIL_E_PARAMS;
+  ctx->dev.flood_bits = bits;
+  return PENCIL_OK;
+}
+
 extern "C" int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* value) {
   if (!ctx || !value) return PENCIL_E_ARG;
   if (knob == PENCIL_TUNE_NTT_LOG_RADIX) {
@@ -919,6 +930,7 @@ static int alg1_prepare(PencilCtx* ctx, const PencilPlan* P, const u64* x0, cons
   R.n_in = (int)P->ct_in;
   R.out_in = w.p0;
   R.out_mask = w.mnt;
+  R.seed = mask_seed;
   {
     PROF(ctx, PENCIL_K_NTT_MO_PREP, s);
     CUDA_TRY((ntt<ModeMoPrep, false>(ctx->dev, R, (int)(P->ct_in + P->ct_out), s)));
@@ -1049,6 +1061,7 @@ extern "C" int he_linear_backward(PencilCtx* ctx, const PencilPlan* Pd, const Pe
     R.mpoly = mpoly;
     R.n_in = 0;
     R.out_mask = mnt;
+    R.seed = mask_seed_w;
     {
       PROF(ctx, PENCIL_K_NTT_MO_PREP, s);
       CUDA_TRY((ntt<ModeMoPrep, false>(ctx->dev, R, (int)Pw->ct_out, s)));
@@ -1485,6 +1498,7 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     prep[l].n_in = (int)P->ct_in;
     prep[l].out_in = p0;
     prep[l].out_mask = mnt;
+    prep[l].seed = mask_seed + (u64)l;
     memset(&mac[l], 0, sizeof(MacParams));
     mac[l].a0 = ct_in;   // + NTT(Delta x0) on load, - NTT(Delta s) on store (Alg. 1 steps 2-3)
     mac[l].a0_stride = 2 * lnw;

@@ -40,6 +40,7 @@ struct DevCtx {
   int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
   int mac_staging;           // operand staging of the split MAC: 0 per-thread cp.async ring, 1 bulk copies
   u64 q_mod_t;               // (q_total mod t): messages are scaled as round(q_total m / t)
+  int flood_bits;            // 0, or the flooding noise of returned ciphertexts: uniform in [-2^b, 2^b)
 };
 
 // A strided view of a user tensor seen as (a, b, r, s) with spatial zero
@@ -231,6 +232,11 @@ __device__ __forceinline__ Philox4 philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u6
 #define PENCIL_DOM_E 3ull
 #define PENCIL_DOM_MASK 4ull
 #define PENCIL_DOM_MASK_PAD 5ull
+#define PENCIL_DOM_FLOOD 6ull
+
+__device__ __forceinline__ u64 philox_word(const Philox4& w, int i) {
+  return i == 0 ? w.v[0] : i == 1 ? w.v[1] : i == 2 ? w.v[2] : w.v[3];
+}
 
 // ------------------------------------------------------------------ packing gathers
 __device__ __forceinline__ u64 gather(const Packing& pk, const Accessor& ac, int idx, int e) {

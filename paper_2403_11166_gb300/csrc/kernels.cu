@@ -768,10 +768,6 @@ cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out
 // element `flat`, Philox(key (seed, 4), counter (flat/4, 0, 0, 0)) word flat%4;
 // elsewhere Philox(key (seed, 5), counter (i/4, ct, 0, 0)) word i%4; mod t.
 // Coefficients 4 blk .. 4 blk + 3 of the mask polynomial of output ciphertext ct.
-__device__ __forceinline__ u64 philox_word(const Philox4& w, int i) {
-  return i == 0 ? w.v[0] : i == 1 ? w.v[1] : i == 2 ? w.v[2] : w.v[3];
-}
-
 // Coefficients 4 blk .. 4 blk + 3 of output polynomial ct.  Consecutive
 // coefficients usually carry consecutive outputs, so one Philox block of the
 // element stream is reused while flat / 4 stays the same; the padding stream

@@ -357,14 +357,21 @@ struct ModeMoPrep {
     int n_in;
     u64* out_in;        // [n_in][L][N]
     u64* out_mask;      // [count - n_in][L][N]
+    u64 seed;           // mask seed (key of the flooding stream)
   };
-  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  static __device__ __forceinline__ void rebase(Params& P, u64 step) { P.seed += step << 32; }   // as the mask's
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
                                              int e) {
-    const u64 m = poly < P.n_in ? gather(P.pk, P.ac, poly, e) & c.t_mask
-                                : P.mpoly[(size_t)(poly - P.n_in) * N + e];
-    return scale_msg(m, lc, c);
+    if (poly < P.n_in) return scale_msg(gather(P.pk, P.ac, poly, e) & c.t_mask, lc, c);
+    const int idx = poly - P.n_in;
+    const u64 r = scale_msg(P.mpoly[(size_t)idx * N + e], lc, c);
+    if (!c.flood_bits) return r;
+    // flooding noise f (uniform in [-2^b, 2^b)) of returned ciphertext idx: Delta s - f
+    const u64 w = philox_word(philox4x64((u64)(e >> 2), (u64)idx, 0ull, 0ull, P.seed, PENCIL_DOM_FLOOD), e & 3) &
+                  ((2ull << c.flood_bits) - 1);
+    const u64 half = 1ull << c.flood_bits;
+    return w >= half ? sub_mod(r, reduce64(w - half, lc), lc.q) : add_mod(r, reduce64(half - w, lc), lc.q);
   }
   template <int N>
   static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,

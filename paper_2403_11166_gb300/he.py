@@ -35,7 +35,7 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
            "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
-           "pencil_lincomb")
+           "pencil_lincomb", "pencil_ctx_flooding")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
@@ -96,6 +96,7 @@ def _load():
         "pencil_plan_destroy": [P],
         "pencil_plan_slice": [P, I32, I32, ctypes.POINTER(P)],
         "pencil_lincomb": [P, P, I64, I64, I64, I64, P, I32, P, I32, P, I64, P],
+        "pencil_ctx_flooding": [P, I32],
         "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
@@ -208,6 +209,10 @@ class Context:
 
     def keygen(self, seed: int, stream=None) -> "SecretKey":
         return SecretKey(self, seed, stream)
+
+    def flooding(self, bits: int):
+        """pencil_ctx_flooding: flood the noise of returned ciphertexts (0 = off)."""
+        _check(lib.pencil_ctx_flooding(self.h, bits), "pencil_ctx_flooding")
 
     def close(self):
         if self.h:

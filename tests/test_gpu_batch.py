@@ -91,6 +91,20 @@ def test_batch_equals_per_layer_calls(he, cols):
         _check_step(he, ctx, sk, plans, batch, data, step)
 
 
+def test_batch_flooded_equals_per_layer_calls(he):
+    """Noise flooding in the batch engine: the flood stream is re-keyed per step
+    like the mask, so every step equals the flooded per-layer calls."""
+    ctx = he.Context(13, 3, 60)
+    ctx.flooding(60)
+    sk = ctx.keygen(6)
+    layers, plans, batch, data = _setup(he, ctx, sk, seed=3)
+    for step in (0, 1):
+        batch.forward()
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        _check_step(he, ctx, sk, plans, batch, data, step)
+
+
 def test_batch_in_cuda_graph(he):
     ctx = he.Context(13, 3, 60)
     sk = ctx.keygen(4)

@@ -493,3 +493,62 @@ def test_paper_parameter_set_t59_f25(he, role):
         assert (to_np(gw_mask) == want_s.reshape(-1)).all()
         assert (to_np(tilde) == want_tilde.reshape(-1)).all()
         assert (gw == protocol.ring_op(L, WGRAD, gy, x, T59)).all()
+
+
+@pytest.mark.parametrize("role", [FWD, WGRAD])
+def test_noise_flooding_matches_oracle(he, role):
+    """pencil_ctx_flooding: returned ciphertexts are the oracle's flooded ones bit
+    for bit, decrypted shares are unchanged, and the noise check still passes."""
+    cfg = (13, 3, 60)
+    L = Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1)
+    p = BfvParams(log_n=13, num_primes=3, prime_bits=60)
+    osk = bfv.keygen(p, 4)
+    g = inputs.rng(31)
+    W = inputs.gaussian_fixed(g, L.w_shape())
+    x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L.x_shape()))
+    gy0, gy1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L.y_shape()))
+    outs = []
+    for bits in (0, 62):
+        ctx = he.Context(*cfg)
+        ctx.flooding(bits)
+        sk = ctx.keygen(4)
+        hrole = he.ROLE_FWD if role == FWD else he.ROLE_WGRAD
+        plan = he.Plan(ctx, _he_layer(he, L), hrole, None)
+        S = plan.sizes
+        ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_backward, S.ws_decrypt))
+        y1 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+        y0 = torch.empty_like(y1)
+        ct_out = plan.new_ct(S.ct_out)
+        if role == FWD:
+            pt, ct_in = plan.new_pt(S.pt), plan.new_ct(S.ct_in)
+            he.encode_weights(ctx, plan, he.OPERAND_KERNEL, to_dev(W), pt)
+            he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), 5, ct_in, ws)
+            he.he_linear_forward(ctx, plan, ct_in, pt, to_dev(x0), None, 6, ct_out, y0, ws)
+        else:
+            ct_x1, ct_g1 = plan.new_ct(S.ct_in), plan.new_ct(S.pt)
+            he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, to_dev(x1), 5, ct_x1, ws)
+            he.encrypt_share(ctx, sk, plan, he.OPERAND_KERNEL, to_dev(gy1), 7, ct_g1, ws)
+            he.he_linear_backward(ctx, None, plan, None, None, ct_x1, ct_g1, to_dev(gy0), to_dev(x0), 0, 6,
+                                  None, None, ct_out, y0, ws)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws)
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        outs.append((plan, to_np(ct_out), to_np(y0), to_np(y1)))
+    (plan, ct0, a0, a1), (_, ct1, b0, b1) = outs
+    assert (a0 == b0).all() and (a1 == b1).all()
+    assert not (ct0 == ct1).all()
+    part = Partition(*plan.part)
+    o = ct1.shape[0] - 1
+    if role == FWD:
+        want = protocol.he_linear(p, osk, L, FWD, part, W, x1, x0, 5, 6, flood_bits=62)[4][o]
+    else:
+        from oracle.packing import counts
+        c = counts(protocol.geometry(L, WGRAD), part)
+        m, nn = divmod(o, c.NC)
+        cts_x = protocol.encrypt_inputs(p, osk, L, WGRAD, part, x1, 5, indices=[m * c.K + k for k in range(c.K)])
+        cts_g = protocol.encrypt_kernel_operand(p, osk, L, WGRAD, part, gy1, 7,
+                                                indices=[k * c.NC + nn for k in range(c.K)])
+        pg = protocol.encode_kernel(p, L, WGRAD, part, gy0, indices=[k * c.NC + nn for k in range(c.K)])
+        px = protocol.encode_input(p, L, WGRAD, part, x0, indices=[m * c.K + k for k in range(c.K)])
+        want = protocol.mo_wgrad_ct(p, L, part, cts_x, pg, cts_g, px, 6, o, flood_bits=62)
+    assert (ct1[o] == as_u64(want)).all()

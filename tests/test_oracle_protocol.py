@@ -102,3 +102,29 @@ def test_simulator_view_zero_input_gives_minus_mask():
     zero = np.zeros(layer.x_shape(), dtype=np.uint64)
     y0, y1, *_ = protocol.he_linear(p, sk, layer, FWD, Partition(1, 5, 5, 1, 1, 1, 1), W, zero, zero, 7, 8)
     assert (_add(y0, y1) == 0).all()
+
+
+def test_noise_flooding_keeps_shares_and_adds_exactly_the_flood_polynomial():
+    """Flooding a returned ciphertext (circuit privacy; the paper is silent): the
+    flooded ciphertext minus the unflooded one is NTT(f) with f uniform in
+    [-2^B, 2^B), and the decrypted shares are unchanged."""
+    from oracle import bfv as obfv, sampling
+    from oracle.packing import Partition as Pt
+    from oracle.params import BfvParams as BP
+    p = BP(log_n=10, num_primes=3, prime_bits=60)
+    sk = obfv.keygen(p, 2)
+    L = Layer("conv", B=1, Ci=2, Co=2, h=4, w=4, s=3, pad=1)
+    part = Pt(1, 2, 2, 4, 4, 3, 3)
+    g = np.random.default_rng(3)
+    W = g.integers(-2000, 2000, L.w_shape())
+    x1 = g.integers(0, 1 << 41, L.x_shape(), dtype=np.uint64)
+    x0 = g.integers(0, 1 << 41, L.x_shape(), dtype=np.uint64)
+    plain = protocol.he_linear(p, sk, L, "fwd", part, W, x1, x0, 5, 6)
+    flooded = protocol.he_linear(p, sk, L, "fwd", part, W, x1, x0, 5, 6, flood_bits=62)
+    assert (np.asarray(plain[0]) == np.asarray(flooded[0])).all()
+    assert (np.asarray(plain[1]) == np.asarray(flooded[1])).all()
+    f = sampling.flood_noise(6, 0, p.n, 62)
+    assert min(f) >= -(1 << 62) and max(f) < (1 << 62) and max(abs(v) for v in f) > (1 << 60)
+    diff = obfv.add_noise(p, plain[4][0], f)
+    assert (diff == flooded[4][0]).all()
+    assert not (plain[4][0] == flooded[4][0]).all()
