@@ -212,7 +212,7 @@ int encode_weights(PencilCtx* ctx, const PencilPlan* plan, int32_t operand,
  * Alg. 2 step 1).  For ciphertext index c (0-based within this call):
  *   c1 = a,  a[i] = (w0 * 2^64 + w1) mod q_j from Philox (key (seed, 2),
  *             counter (i/2, c, j, 0), words 2(i%2), 2(i%2)+1) -- NTT form;
- *   c0 = NTT(Delta * m + e) - a * NTT(s),  Delta = floor(q / t),
+ *   c0 = NTT(Delta m + e) - a * NTT(s)  (Delta m = round(q m / t), above),
  *   e[i] from the CDT on Philox (key (seed, 3), counter (i/4, c, 0, 0), word i%4).
  * operand INPUT packs `share` with pi_v into ct[M*K]; operand KERNEL packs it
  * with pi_W into ct[K*NC] (Alg. 2's Enc(<gY>_1)).  ws >= ws_encrypt bytes. */

@@ -1,4 +1,4 @@
-"""Symmetric-key BFV with RNS limbs (oracle; test infrastructure only).
+"""BFV with RNS limbs (symmetric and public-key encryption) (oracle; test infrastructure only).
 
 Sec. 2.2: BFV {N, t, q}; plaintexts in Z_t[X]/(X^N+1), ciphertexts in
 (Z_q[X]/(X^N+1))^2; one plaintext-ciphertext product per linear layer, no
@@ -14,6 +14,11 @@ Ciphertexts are kept in NTT form, limb-major: c[comp][limb][slot].
              paper's GPU BFV follows): a plaintext-ciphertext product then
              carries no (q mod t) x overflow term, so products of two uniform
              Z_t values decrypt correctly at t = 2^59, q ~ 2^180 (Sec. 6).
+* pk_keygen: public key (Sec. 2.2's BFV [Fan-Vercauteren]; the paper's
+             simulators exchange pk): p1 = a uniform (NTT form),
+             p0 = -(a * NTT(s)) - NTT(e).
+* encrypt_pk: u ternary, e1, e2 errors;  c0 = NTT([q m / t] + e1) + NTT(u) * p0,
+             c1 = NTT(e2) + NTT(u) * p1, so c0 + c1 s = [q m / t] + e1 - u e + e2 s.
 * add_plain: c0 += NTT([q m' / t])   (Alg. 1 step 2: adding the MO's share).
 * encode   : a signed integer polynomial lifted to every limb, in NTT form.
 * decrypt  : x = INTT(c0 + c1 * NTT(s)) per limb, recombined exactly by the
@@ -29,7 +34,8 @@ import numpy as np
 
 from .ntt import intt_radix2, ntt_radix2
 from .params import BfvParams
-from .sampling import gaussian_error, ternary_secret, uniform_a
+from .philox import DOMAIN_PK_A, DOMAIN_PK_E, DOMAIN_PK_E2
+from .sampling import gaussian_error, ternary_secret, ternary_u, uniform_a
 
 
 @dataclass
@@ -91,6 +97,37 @@ def encrypt(p: BfvParams, sk: SecretKey, m: Sequence[int], seed: int, ct_index: 
         a = np.array(uniform_a(seed, ct_index, i, p.n, q), dtype=object)
         c1.append(a)
         c0.append((base[i] - a * sk.s_hat[i]) % q)
+    return np.stack([np.stack(c0), np.stack(c1)])
+
+
+@dataclass
+class PublicKey:
+    p0: np.ndarray               # object array [L][N], NTT form
+    p1: np.ndarray               # object array [L][N], NTT form (= a)
+
+
+def pk_keygen(p: BfvParams, sk: SecretKey, seed: int) -> PublicKey:
+    """pk = (-(a s + e), a) with a from stream (seed, PK_A, 0, limb), e from (seed, PK_E, 0)."""
+    e_hat = to_ntt(p, lift_plain(p, gaussian_error(seed, 0, p.n, p.sigma, DOMAIN_PK_E)))
+    p0, p1 = [], []
+    for i, q in enumerate(p.primes):
+        a = np.array(uniform_a(seed, 0, i, p.n, q, DOMAIN_PK_A), dtype=object)
+        p1.append(a)
+        p0.append((-(a * sk.s_hat[i]) - e_hat[i]) % q)
+    return PublicKey(p0=np.stack(p0), p1=np.stack(p1))
+
+
+def encrypt_pk(p: BfvParams, pk: PublicKey, m: Sequence[int], seed: int, ct_index: int) -> np.ndarray:
+    """Public-key encryption, c[2][L][N] (NTT form).  Randomness of ciphertext
+    ct_index: u from stream (seed, PK_U, ct_index), e1 from (seed, E, ct_index)
+    (the symmetric encryption's error stream), e2 from (seed, PK_E2, ct_index)."""
+    u_hat = to_ntt(p, lift_plain(p, ternary_u(seed, ct_index, p.n)))
+    base0 = to_ntt(p, scaled_message(p, m, gaussian_error(seed, ct_index, p.n, p.sigma)))
+    base1 = to_ntt(p, lift_plain(p, gaussian_error(seed, ct_index, p.n, p.sigma, DOMAIN_PK_E2)))
+    c0, c1 = [], []
+    for i, q in enumerate(p.primes):
+        c0.append((base0[i] + u_hat[i] * pk.p0[i]) % q)
+        c1.append((base1[i] + u_hat[i] * pk.p1[i]) % q)
     return np.stack([np.stack(c0), np.stack(c1)])
 
 

@@ -50,6 +50,11 @@ DOMAIN_E = 3           # encryption error e:    ctr = (i // 4, ct, 0, 0),  word 
 DOMAIN_MASK = 4        # re-mask, per output element: ctr = (flat // 4, 0, 0, 0), word flat % 4
 DOMAIN_MASK_PAD = 5    # re-mask, unused ct coefficients: ctr = (i // 4, ct_out, 0, 0), word i % 4
 DOMAIN_FLOOD = 6       # flooding noise of returned cts: ctr = (i // 4, ct_out, 0, 0), word i % 4
+DOMAIN_PK_A = 7        # public key's a:        ctr = (i // 2, 0, limb, 0), words 2(i%2), 2(i%2)+1
+DOMAIN_PK_E = 8        # public key's error e:  ctr = (i // 4, 0, 0, 0),  word i % 4
+DOMAIN_PK_U = 9        # public-key encryption u (ternary): ctr = (i // 4, ct, 0, 0), word i % 4
+DOMAIN_PK_E2 = 10      # public-key encryption e2: ctr = (i // 4, ct, 0, 0), word i % 4
+                       # (its e1 is the symmetric encryption's e: DOMAIN_E)
 
 
 def word(seed: int, domain: int, block: int, a: int = 0, b: int = 0, lane: int = 0) -> int:

@@ -17,7 +17,7 @@ from typing import List
 import mpmath
 
 from .philox import (DOMAIN_A, DOMAIN_E, DOMAIN_MASK, DOMAIN_MASK_PAD, DOMAIN_FLOOD,
-                     DOMAIN_SECRET, philox4x64)
+                     DOMAIN_PK_U, DOMAIN_SECRET, philox4x64)
 
 CDT_TAIL = 19
 CDT_BITS = 63
@@ -65,23 +65,34 @@ def ternary_secret(seed: int, n: int) -> List[int]:
     return out
 
 
-def uniform_a(seed: int, ct: int, limb: int, n: int, q: int) -> List[int]:
-    """Encryption mask a for (ciphertext ct, limb), already in NTT form."""
+def uniform_a(seed: int, ct: int, limb: int, n: int, q: int, domain: int = DOMAIN_A) -> List[int]:
+    """Encryption mask a for (ciphertext ct, limb), already in NTT form (the
+    public key's a with domain DOMAIN_PK_A, ct = 0)."""
     out = []
     for blk in range(n // 2):
-        w = philox4x64((blk, ct, limb, 0), (seed, DOMAIN_A))
+        w = philox4x64((blk, ct, limb, 0), (seed, domain))
         out.append(((w[0] << 64) | w[1]) % q)
         out.append(((w[2] << 64) | w[3]) % q)
     return out
 
 
-def gaussian_error(seed: int, ct: int, n: int, sigma: float = 3.2) -> List[int]:
-    """Encryption error e for ciphertext ct (one integer polynomial, all limbs)."""
+def gaussian_error(seed: int, ct: int, n: int, sigma: float = 3.2, domain: int = DOMAIN_E) -> List[int]:
+    """Encryption error e for ciphertext ct (one integer polynomial, all limbs);
+    the public key's error and public-key encryption's e2 use their own domains."""
     table = cdt_table(sigma)
     out = []
     for blk in range(n // 4):
-        w = philox4x64((blk, ct, 0, 0), (seed, DOMAIN_E))
+        w = philox4x64((blk, ct, 0, 0), (seed, domain))
         out.extend(cdt_sample(x, table) for x in w)
+    return out
+
+
+def ternary_u(seed: int, ct: int, n: int) -> List[int]:
+    """Public-key encryption's u for ciphertext ct: (w_i mod 3) - 1 in {-1, 0, 1}."""
+    out = []
+    for blk in range(n // 4):
+        w = philox4x64((blk, ct, 0, 0), (seed, DOMAIN_PK_U))
+        out.extend((x % 3) - 1 for x in w)
     return out
 
 

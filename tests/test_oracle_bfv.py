@@ -88,3 +88,56 @@ def test_uniform_product_at_paper_parameters_decrypts():
     got = bfv.decrypt(p, sk, ct)
     want = negacyclic_schoolbook([bfv.centered(v, p.t) for v in w], m, p.t)
     assert [(a + b) % p.t for a, b in zip(got, s)] == [int(v) % p.t for v in want]
+
+
+def _negacyclic_int(a, b):
+    """Exact negacyclic product of two small integer polynomials (int64)."""
+    n = len(a)
+    full = np.convolve(np.asarray(a, dtype=np.int64), np.asarray(b, dtype=np.int64))
+    out = full[:n].copy()
+    out[:n - 1] -= full[n:]
+    return out
+
+
+def test_public_key_relation(params):
+    """p0 + p1 s = -e: the key's phase is exactly the negated error of its own
+    stream (coefficient form), so p0 carries -(a s) with the right sign."""
+    from oracle import sampling
+    from oracle.philox import DOMAIN_PK_E
+    p = params
+    sk = bfv.keygen(p, 3)
+    pk = bfv.pk_keygen(p, sk, 11)
+    e = sampling.gaussian_error(11, 0, p.n, p.sigma, DOMAIN_PK_E)
+    phase = bfv.from_ntt(p, np.stack([(pk.p0[i] + pk.p1[i] * sk.s_hat[i]) % q for i, q in enumerate(p.primes)]))
+    for i, q in enumerate(p.primes):
+        assert [int(v) for v in phase[i]] == [(-x) % q for x in e]
+    assert any(e)
+
+
+def test_public_key_encryption_phase_and_roundtrip(params):
+    """Enc_pk: c0 + c1 s - round(q m / t) = e1 - u e + e2 s exactly, every
+    product recomputed as a schoolbook negacyclic convolution over the
+    integers (no NTT), and Dec recovers m."""
+    from oracle import sampling
+    from oracle.philox import DOMAIN_PK_E, DOMAIN_PK_E2
+    p = params
+    sk = bfv.keygen(p, 3)
+    pk = bfv.pk_keygen(p, sk, 11)
+    r = random.Random(4)
+    for idx in (0, 2):
+        m = [r.randrange(p.t) for _ in range(p.n)]
+        ct = bfv.encrypt_pk(p, pk, m, seed=21, ct_index=idx)
+        assert bfv.decrypt(p, sk, ct) == m
+        assert bfv.noise_budget_ok(p, sk, ct)
+        u = sampling.ternary_u(21, idx, p.n)
+        e = sampling.gaussian_error(11, 0, p.n, p.sigma, DOMAIN_PK_E)
+        e1 = sampling.gaussian_error(21, idx, p.n, p.sigma)
+        e2 = sampling.gaussian_error(21, idx, p.n, p.sigma, DOMAIN_PK_E2)
+        noise = np.asarray(e1, dtype=np.int64) - _negacyclic_int(u, e) + _negacyclic_int(e2, sk.s)
+        got = bfv.decrypt_phase(p, sk, ct)
+        for j in range(p.n):
+            want = (p.q * m[j] + p.t // 2) // p.t + int(noise[j])
+            assert got[j] == want % p.q, j
+    assert set(u) == {-1, 0, 1}
+    # independent ciphertexts of the same message differ
+    assert not (bfv.encrypt_pk(p, pk, m, 21, 0) == bfv.encrypt_pk(p, pk, m, 21, 1)).all()
