@@ -63,6 +63,8 @@ def parse():
                     help="stream the layer through encrypt / multiply-accumulate / decrypt in this many row slices")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
     ap.add_argument("--extras-only", action="store_true", help="run only the extra workloads (JSON line)")
+    ap.add_argument("--extra", action="append", default=None,
+                    help="with --extras-only: run only this extra workload (repeatable)")
     return ap.parse_args()
 
 
@@ -507,10 +509,61 @@ def table5_layers(he, device: int, reps: int = 2):
     return out
 
 
-def extras(he, device: int):
-    return {"batched_uneven": batched_uneven(he, device), "training_step_cnn": training_step(he, device),
-            "large_conv_128_fwd_bwd": large_conv(he, device), "pencil_plus_fwd_m8": pencil_plus(he, device),
-            "paper_table5_layers_b64": table5_layers(he, device)}
+def pk_and_flooding(he, device: int, reps: int = 10, flood_bits: int = 62):
+    """The headline layer (conv3x3 16->16, 32x32, B = 64, N = 8192): the DO's
+    encryption of its input share with the secret key and with the public key,
+    and the MO's Alg. 1 forward without and with noise flooding."""
+    import torch
+    from paper_2403_11166_gb300 import inputs
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=device)
+    sk = ctx.keygen(81)
+    pk = ctx.pk_keygen(sk, 82)
+    Ly = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
+                  LAYER["pad"])
+    plan = he.Plan(ctx, Ly, he.ROLE_FWD, None)
+    S = plan.sizes
+    dev = f"cuda:{device}"
+    g = inputs.rng(83)
+    W = torch.as_tensor(inputs.gaussian_fixed(g, (LAYER["c_out"], LAYER["c_in"], 3, 3)).view(np.int64), device=dev)
+    x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in inputs.split_shares(
+        g, inputs.gaussian_fixed(g, (LAYER["batch"], LAYER["c_in"], LAYER["h"], LAYER["w"]))))
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_encrypt_pk, S.ws_forward))
+    pt, ct_in, ct_out = plan.new_pt(S.pt), plan.new_ct(S.ct_in), plan.new_ct(S.ct_out)
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
+    he.encode_weights(ctx, plan, he.OPERAND_KERNEL, W, pt)
+
+    def timed(fn):
+        fn(0)
+        torch.cuda.synchronize()
+        t = []
+        for r in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(r + 1)
+            b.record()
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        return statistics.median(t)
+    ms_sk = timed(lambda r: he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1, 100 + r, ct_in, ws))
+    ms_pk = timed(lambda r: he.encrypt_share_pk(ctx, pk, plan, he.OPERAND_INPUT, x1, 100 + r, ct_in, ws))
+    fwd = lambda r: he.he_linear_forward(ctx, plan, ct_in, pt, x0, None, 200 + r, ct_out, y0, ws)
+    ms_fwd = timed(fwd)
+    ctx.flooding(flood_bits)
+    ms_fwd_flood = timed(fwd)
+    ctx.flooding(0)
+    ok = ctx.sync_status() == 0
+    return {"ct_in": S.ct_in, "encrypt_sk_ms": ms_sk, "encrypt_pk_ms": ms_pk,
+            "encrypt_sk_ct_per_s": S.ct_in / (ms_sk * 1e-3), "encrypt_pk_ct_per_s": S.ct_in / (ms_pk * 1e-3),
+            "forward_ms": ms_fwd, "forward_flooded_ms": ms_fwd_flood, "flood_bits": flood_bits, "status_ok": ok}
+
+
+EXTRAS = {"batched_uneven": batched_uneven, "training_step_cnn": training_step,
+          "large_conv_128_fwd_bwd": large_conv, "pencil_plus_fwd_m8": pencil_plus,
+          "paper_table5_layers_b64": table5_layers, "public_key_and_flooding": pk_and_flooding}
+
+
+def extras(he, device: int, names=None):
+    return {k: fn(he, device) for k, fn in EXTRAS.items() if not names or k in names}
 
 
 # ---------------------------------------------------------------- oracle timing (host cores)
@@ -641,7 +694,7 @@ def run_ours(args):
             print(json.dumps({"ntt_sweep": sw}), flush=True)
         return
     if args.extras_only:
-        ex = extras(he, local)
+        ex = extras(he, local, args.extra)
         if rank == 0:
             print(json.dumps(ex), flush=True)
         return

@@ -51,6 +51,7 @@ extern "C" {
 
 typedef struct PencilCtx PencilCtx;
 typedef struct PencilSecretKey PencilSecretKey;
+typedef struct PencilPublicKey PencilPublicKey;
 typedef struct PencilPlan PencilPlan;
 
 /* BFV instance {N, t, q} (Sec. 2.2) with q the product of `num_primes` RNS
@@ -114,6 +115,20 @@ int pencil_sync_status(PencilCtx* ctx, int32_t* status);
 int pencil_keygen(PencilCtx* ctx, uint64_t seed, PencilSecretKey** out, void* stream);
 int pencil_sk_destroy(PencilSecretKey* sk);
 
+/* DO side: BFV public key (the scheme of Sec. 2.2 [Fan-Vercauteren]; the
+ * paper's security simulators hand pk between the parties), for
+ * encrypt_share_pk:
+ *   p1 = a,  a[i] = (w0 * 2^64 + w1) mod q_j, Philox key (seed, 7), counter
+ *            (i/2, 0, j, 0), words 2(i%2), 2(i%2)+1 -- NTT form;
+ *   p0 = -(a * NTT(s)) - NTT(e),  e[i] from the CDT (as encrypt_share's errors)
+ *            on Philox key (seed, 8), counter (i/4, 0, 0, 0), word i%4.
+ * Device memory owned by the handle ([2][L][N] values with Shoup companions,
+ * plus N bytes of scratch).  Errors: PENCIL_E_ARG (null or foreign sk),
+ * PENCIL_E_CUDA (allocation or launch). */
+int pencil_pk_keygen(PencilCtx* ctx, const PencilSecretKey* sk, uint64_t seed, PencilPublicKey** out,
+                     void* stream);
+int pencil_pk_destroy(PencilPublicKey* pk);
+
 /* ---------------------------------------------------------------- plans */
 enum { PENCIL_FC = 0, PENCIL_CONV = 1 };
 /* Role of a plan: the forward product (Alg. 1), the input gradient
@@ -158,6 +173,7 @@ typedef struct {
   int64_t ws_forward;    /* bytes of ws for he_linear_forward          */
   int64_t ws_backward;   /* bytes of ws for he_linear_backward (this plan's role) */
   int64_t ws_decrypt;    /* bytes of ws for decrypt_to_share           */
+  int64_t ws_encrypt_pk; /* bytes of ws for encrypt_share_pk (either operand) */
 } PencilPlanSizes;
 
 /* Plans `role` of `layer`.  `part` = NULL lets the planner choose the
@@ -219,6 +235,21 @@ int encode_weights(PencilCtx* ctx, const PencilPlan* plan, int32_t operand,
 int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* plan,
                   int32_t operand, const uint64_t* share, uint64_t seed, uint64_t* ct,
                   void* ws, size_t ws_bytes, void* stream);
+
+/* Public-key BFV encryption of a packed share: the same packing, operands,
+ * slices and output layout as encrypt_share, with the randomness of
+ * ciphertext index c (0-based within the plan's operand):
+ *   u[i]  = (w mod 3) - 1,  Philox key (seed, 9),  counter (i/4, c, 0, 0), word i%4;
+ *   e1[i] = CDT on Philox key (seed, 3),  e2[i] = CDT on Philox key (seed, 10),
+ *           counter (i/4, c, 0, 0), word i%4;
+ *   c0 = NTT(Delta m + e1) + NTT(u) * p0,   c1 = NTT(e2) + NTT(u) * p1,
+ * so c0 + c1 s = Delta m + e1 - u e + e2 s (e the key's error).  Three
+ * kernels: the samples (int8), NTT(u) into ws, and one NTT pass over both
+ * components of every ciphertext with the products fused into its epilogue.
+ * ws >= ws_encrypt_pk bytes, 16-byte aligned.  Errors as encrypt_share;
+ * PENCIL_E_ARG for a key of another context. */
+int encrypt_share_pk(PencilCtx* ctx, const PencilPublicKey* pk, const PencilPlan* plan, int32_t operand,
+                     const uint64_t* share, uint64_t seed, uint64_t* ct, void* ws, size_t ws_bytes, void* stream);
 
 /* encrypt_share without a workspace argument and without any allocation.
  * (The paper has no counterpart: this is a deployment variant of the call
@@ -387,7 +418,8 @@ enum {
   PENCIL_K_NTT_RAW = 0, PENCIL_K_INTT_RAW, PENCIL_K_NTT_ENCRYPT, PENCIL_K_NTT_ADDPLAIN, PENCIL_K_NTT_ENCODE,
   PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
   PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_RING,
-  PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_LINCOMB, PENCIL_K_COUNT
+  PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_LINCOMB, PENCIL_K_SAMPLE_PK, PENCIL_K_NTT_PK_U,
+  PENCIL_K_NTT_ENCRYPT_PK, PENCIL_K_COUNT
 };
 typedef struct {
   int32_t kernel;   /* PENCIL_K_* */

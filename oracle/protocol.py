@@ -160,25 +160,31 @@ def ring_op(layer: Layer, role: str, a, b, t_bits: int):
 # ---------------------------------------------------------------------------
 # Step-by-step HE protocol.
 # ---------------------------------------------------------------------------
+def _enc(p: BfvParams, sk, pk, m, seed: int, i: int) -> np.ndarray:
+    return bfv.encrypt(p, sk, m, seed, i) if pk is None else bfv.encrypt_pk(p, pk, m, seed, i)
+
+
 def encrypt_inputs(p: BfvParams, sk, layer: Layer, role: str, part: Partition,
-                   share, seed: int, indices=None) -> Dict[int, np.ndarray]:
-    """DO: Enc(pi_v(share)) for ct_in[m * K + k] (all, or only `indices`)."""
+                   share, seed: int, indices=None, pk=None) -> Dict[int, np.ndarray]:
+    """DO: Enc(pi_v(share)) for ct_in[m * K + k] (all, or only `indices`);
+    with the secret key, or with the public key `pk` when one is given."""
     g = geometry(layer, role)
     c = counts(g, part)
     V = role_input(layer, role, share)
     idx = range(c.ct_in) if indices is None else indices
-    return {i: bfv.encrypt(p, sk, pack_input(V, g, part, p.n, i // c.K, i % c.K), seed, i)
+    return {i: _enc(p, sk, pk, pack_input(V, g, part, p.n, i // c.K, i % c.K), seed, i)
             for i in idx}
 
 
 def encrypt_kernel_operand(p: BfvParams, sk, layer: Layer, role: str, part: Partition,
-                           share, seed: int, indices=None) -> Dict[int, np.ndarray]:
-    """DO: Enc(pi_W(share)) for kernel-position operand [k * NC + n] (Alg. 2's Enc(<gY>_1))."""
+                           share, seed: int, indices=None, pk=None) -> Dict[int, np.ndarray]:
+    """DO: Enc(pi_W(share)) for kernel-position operand [k * NC + n] (Alg. 2's
+    Enc(<gY>_1)); secret- or public-key as encrypt_inputs."""
     g = geometry(layer, role)
     c = counts(g, part)
     Wt = role_kernel(layer, role, share)
     idx = range(c.pt) if indices is None else indices
-    return {i: bfv.encrypt(p, sk, pack_weight(Wt, g, part, p.n, i // c.NC, i % c.NC), seed, i)
+    return {i: _enc(p, sk, pk, pack_weight(Wt, g, part, p.n, i // c.NC, i % c.NC), seed, i)
             for i in idx}
 
 

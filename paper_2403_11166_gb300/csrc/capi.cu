@@ -165,6 +165,11 @@ struct PencilSecretKey {
   ulonglong2* sk = nullptr;
 };
 
+struct PencilPublicKey {
+  PencilCtx* ctx;
+  ulonglong2* key = nullptr;   // [2][L][N] (value, Shoup companion), then N bytes of scratch
+};
+
 struct Geom {
   int B, Ci, Co, H, W, KH, KW;
   int Ho() const { return H - KH + 1; }
@@ -191,7 +196,7 @@ struct PencilPlan {
   u64* d_tab = nullptr;          // [3][N]: v, w, y tables
   int4* d_org = nullptr;         // origins: v [ct_in], w [pt], y [ct_out]
   Packing pk_v, pk_w, pk_y;
-  long long ws_encrypt, ws_forward, ws_backward, ws_decrypt;
+  long long ws_encrypt, ws_forward, ws_backward, ws_decrypt, ws_encrypt_pk;
   // A slice (pencil_plan_slice) covers output rows m in [m_first, m_first + m_count)
   // of its parent and shares the parent's tables; a full plan covers [0, M).
   long long m_first = 0, m_count = 0;
@@ -468,6 +473,43 @@ extern "C" int pencil_sk_destroy(PencilSecretKey* sk) {
   DeviceGuard guard(sk->ctx->device);
   cudaFree(sk->sk);
   delete sk;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_pk_keygen(PencilCtx* ctx, const PencilSecretKey* sk, uint64_t seed, PencilPublicKey** out,
+                                void* stream) {
+  if (!ctx || !sk || !out || sk->ctx != ctx) return PENCIL_E_ARG;
+  *out = nullptr;
+  DeviceGuard guard(ctx->device);
+  PencilPublicKey* pk = new (std::nothrow) PencilPublicKey();
+  if (!pk) return PENCIL_E_CUDA;
+  pk->ctx = ctx;
+  const size_t key_bytes = 2ull * ctx->dev.L * ctx->n * sizeof(ulonglong2);
+  if (cudaMalloc(&pk->key, key_bytes + ctx->n) != cudaSuccess) {
+    delete pk;
+    return PENCIL_E_CUDA;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  int8_t* err = reinterpret_cast<int8_t*>(pk->key) + key_bytes;
+  ModePkKeygen::Params P;
+  P.err = err;
+  P.sk = sk->sk;
+  P.key = pk->key;
+  P.seed = seed;
+  if (launch_sample_err(seed, 0, 1, ctx->n, err, s, PENCIL_DOM_PK_E) != cudaSuccess ||
+      ntt<ModePkKeygen, false>(ctx->dev, P, 1, s) != cudaSuccess) {
+    pencil_pk_destroy(pk);
+    return PENCIL_E_CUDA;
+  }
+  *out = pk;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_pk_destroy(PencilPublicKey* pk) {
+  if (!pk) return PENCIL_E_ARG;
+  DeviceGuard guard(pk->ctx->device);
+  cudaFree(pk->key);
+  delete pk;
   return PENCIL_OK;
 }
 
@@ -750,6 +792,7 @@ extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, 
   auto al = [](long long b) { return (b + 255) / 256 * 256; };
   const long long lnb = (long long)ctx->dev.L * n * 8;
   P->ws_encrypt = al(std::max(P->ct_in, P->pt) * (long long)n);
+  P->ws_encrypt_pk = al(std::max(P->ct_in, P->pt) * lnb) + 3 * al(std::max(P->ct_in, P->pt) * (long long)n);
   // Alg. 1: NTT(Delta x0) per input ct, NTT(Delta s) per output ct, s per output ct
   P->ws_forward = al(P->ct_in * lnb) + al(P->ct_out * lnb) + al(P->ct_out * (long long)n * 8);
   if (role == PENCIL_ROLE_WGRAD)   // Alg. 2: encoded <gY>_0 and <X>_0, NTT(Delta s), s
@@ -841,6 +884,7 @@ extern "C" int pencil_plan_sizes(const PencilPlan* P, PencilPlanSizes* s) {
   s->ws_forward = P->ws_forward;
   s->ws_backward = P->ws_backward;
   s->ws_decrypt = P->ws_decrypt;
+  s->ws_encrypt_pk = P->ws_encrypt_pk;
   return PENCIL_OK;
 }
 
@@ -893,6 +937,54 @@ extern "C" int encrypt_share(PencilCtx* ctx, const PencilSecretKey* sk, const Pe
   {
     PROF(ctx, PENCIL_K_NTT_ENCRYPT, s);
     CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s, (int)first)));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int encrypt_share_pk(PencilCtx* ctx, const PencilPublicKey* pk, const PencilPlan* P, int32_t operand,
+                                const uint64_t* share, uint64_t seed, uint64_t* ct, void* ws, size_t ws_bytes,
+                                void* stream) {
+  if (!ctx || !pk || !P || !share || !ct || !ws || P->ctx != ctx || pk->ctx != ctx) return PENCIL_E_ARG;
+  if (operand != PENCIL_OPERAND_INPUT && operand != PENCIL_OPERAND_KERNEL) return PENCIL_E_ARG;
+  if (!aligned16(ct) || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_encrypt_pk) return PENCIL_E_CAPACITY;
+  if (operand == PENCIL_OPERAND_KERNEL && P->parent) return PENCIL_E_ARG;   // slices cover input / output rows
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const long long first = operand == PENCIL_OPERAND_KERNEL ? 0 : P->in_first();
+  const long long count = operand == PENCIL_OPERAND_KERNEL ? P->pt : P->in_count();
+  // ws: NTT(u) [n_all][L][N], then e1, e2, u [n_all][N] each (int8), indexed by
+  // the absolute ciphertext position like encrypt_share's errors.
+  const long long n_all = std::max(P->ct_in, P->pt);
+  auto al = [](long long b) { return (b + 255) / 256 * 256; };
+  char* w = reinterpret_cast<char*>(ws);
+  u64* u_hat = reinterpret_cast<u64*>(w);
+  int8_t* e1 = reinterpret_cast<int8_t*>(w + al(n_all * (long long)ctx->dev.L * ctx->n * 8));
+  int8_t* e2 = e1 + al(n_all * (long long)ctx->n);
+  int8_t* u = e2 + al(n_all * (long long)ctx->n);
+  {
+    PROF(ctx, PENCIL_K_SAMPLE_PK, s);
+    CUDA_TRY(launch_sample_pk(seed, (int)first, (int)count, ctx->n, e1, e2, u, s));
+  }
+  ModePkU::Params U;
+  U.u = u;
+  U.u_hat = u_hat;
+  {
+    PROF(ctx, PENCIL_K_NTT_PK_U, s);
+    CUDA_TRY((ntt<ModePkU, false>(ctx->dev, U, (int)count, s, (int)first)));
+  }
+  ModeEncryptPk::Params M;
+  M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
+  M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
+  M.ac.ptr = share;
+  M.e1 = e1;
+  M.e2 = e2;
+  M.u_hat = u_hat;
+  M.key = pk->key;
+  M.ct = ct;
+  {
+    PROF(ctx, PENCIL_K_NTT_ENCRYPT_PK, s);
+    CUDA_TRY((ntt<ModeEncryptPk, false>(ctx->dev, M, (int)(2 * count), s, (int)(2 * first))));
   }
   return PENCIL_OK;
 }

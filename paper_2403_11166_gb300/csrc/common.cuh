@@ -233,6 +233,10 @@ __device__ __forceinline__ Philox4 philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u6
 #define PENCIL_DOM_MASK 4ull
 #define PENCIL_DOM_MASK_PAD 5ull
 #define PENCIL_DOM_FLOOD 6ull
+#define PENCIL_DOM_PK_A 7ull    // public key's a
+#define PENCIL_DOM_PK_E 8ull    // public key's error
+#define PENCIL_DOM_PK_U 9ull    // public-key encryption's ternary u
+#define PENCIL_DOM_PK_E2 10ull  // public-key encryption's e2 (its e1 is PENCIL_DOM_E)
 
 __device__ __forceinline__ u64 philox_word(const Philox4& w, int i) {
   return i == 0 ? w.v[0] : i == 1 ? w.v[1] : i == 2 ? w.v[2] : w.v[3];

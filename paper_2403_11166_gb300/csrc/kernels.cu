@@ -746,21 +746,50 @@ __device__ __forceinline__ int8_t cdt_sample(u64 w) {
   return (int8_t)((w >> 63) ? -mag : mag);
 }
 
-__global__ void k_sample_err(u64 seed, int first, int count, int n, int8_t* out) {
+__global__ void k_sample_err(u64 seed, int first, int count, int n, int8_t* out, u64 dom) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int per = n >> 2;
   if (id >= (long long)count * per) return;
   const int ct = first + (int)(id / per);
   const int blk = (int)(id % per);
-  const Philox4 w = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_E);
+  const Philox4 w = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, dom);
   reinterpret_cast<char4*>(out + (size_t)ct * n)[blk] =
       make_char4(cdt_sample(w.v[0]), cdt_sample(w.v[1]), cdt_sample(w.v[2]), cdt_sample(w.v[3]));
 }
 
-cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s) {
+cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s, u64 dom) {
   const long long total = (long long)count * (n >> 2);
   if (total == 0) return cudaSuccess;
-  k_sample_err<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, first, count, n, out);
+  k_sample_err<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, first, count, n, out, dom);
+  return cudaGetLastError();
+}
+
+// Public-key encryption's small polynomials of ciphertexts [first, first + count):
+// e1 (PENCIL_DOM_E, the symmetric encryption's stream), e2 (PENCIL_DOM_PK_E2) from
+// the CDT and u = (w mod 3) - 1 (PENCIL_DOM_PK_U); counter (i/4, ct, 0, 0), word i%4.
+__global__ void k_sample_pk(u64 seed, int first, int count, int n, int8_t* e1, int8_t* e2, int8_t* u) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = n >> 2;
+  if (id >= (long long)count * per) return;
+  const int ct = first + (int)(id / per);
+  const int blk = (int)(id % per);
+  const size_t o = (size_t)ct * n;
+  const Philox4 a = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_E);
+  reinterpret_cast<char4*>(e1 + o)[blk] =
+      make_char4(cdt_sample(a.v[0]), cdt_sample(a.v[1]), cdt_sample(a.v[2]), cdt_sample(a.v[3]));
+  const Philox4 b = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_PK_E2);
+  reinterpret_cast<char4*>(e2 + o)[blk] =
+      make_char4(cdt_sample(b.v[0]), cdt_sample(b.v[1]), cdt_sample(b.v[2]), cdt_sample(b.v[3]));
+  const Philox4 c = philox4x64((u64)blk, (u64)ct, 0ull, 0ull, seed, PENCIL_DOM_PK_U);
+  reinterpret_cast<char4*>(u + o)[blk] = make_char4((signed char)(c.v[0] % 3ull) - 1, (signed char)(c.v[1] % 3ull) - 1,
+                                                    (signed char)(c.v[2] % 3ull) - 1, (signed char)(c.v[3] % 3ull) - 1);
+}
+
+cudaError_t launch_sample_pk(u64 seed, int first, int count, int n, int8_t* e1, int8_t* e2, int8_t* u,
+                             cudaStream_t s) {
+  const long long total = (long long)count * (n >> 2);
+  if (total == 0) return cudaSuccess;
+  k_sample_pk<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(seed, first, count, n, e1, e2, u);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,10 @@ cudaError_t launch_lincomb(const LincombP& P, u64 t_mask, cudaStream_t s);
 
 cudaError_t upload_cdt();
 cudaError_t launch_mac(const DevCtx& ctx, const MacParams& P, bool dual, cudaStream_t s);
-cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s);
+cudaError_t launch_sample_err(u64 seed, int first, int count, int n, int8_t* out, cudaStream_t s,
+                              u64 dom = PENCIL_DOM_E);
+cudaError_t launch_sample_pk(u64 seed, int first, int count, int n, int8_t* e1, int8_t* e2, int8_t* u,
+                             cudaStream_t s);
 cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accessor& ac, u64 seed, int count, u64* out,
                              cudaStream_t s);
 cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,

@@ -410,6 +410,109 @@ struct ModeKeygen {
   }
 };
 
+__device__ __forceinline__ u64 lift_small(int v, u64 q) { return v >= 0 ? (u64)v : q - (u64)(-v); }
+__device__ __forceinline__ u64 neg_mod(u64 v, u64 q) { return v ? q - v : 0; }
+
+// DO public key (BFV as in Fan-Vercauteren): x = NTT(e) of the sampled error;
+// p1 = a, uniform in the NTT domain from Philox (key (seed, 7), counter
+// (i/2, 0, limb, 0), words 2(i%2), 2(i%2)+1); p0 = -(a s) - x.  Both stored
+// with Shoup companions: key[comp][L][N].
+struct ModePkKeygen {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 8;
+  static constexpr int kEpilogueUnroll = 1;
+  struct Params {
+    const int8_t* err;       // [N]
+    const ulonglong2* sk;    // [L][N]
+    ulonglong2* key;         // [2][L][N]
+    u64 seed;
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int, int, int e) {
+    return lift_small(P.err[e], lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int, int limb,
+                                                int e, u64 x0, u64 x1) {
+    const Philox4 w = philox4x64((u64)(e >> 1), 0ull, (u64)limb, 0ull, P.seed, PENCIL_DOM_PK_A);
+    const u64 a0 = reduce128(w.v[0], w.v[1], lc);
+    const u64 a1 = reduce128(w.v[2], w.v[3], lc);
+    const ulonglong2 s0 = __ldg(P.sk + (size_t)limb * N + e);
+    const ulonglong2 s1 = __ldg(P.sk + (size_t)limb * N + e + 1);
+    const u64 p00 = neg_mod(add_mod(mul_shoup(a0, s0.x, s0.y, lc.q), x0, lc.q), lc.q);
+    const u64 p01 = neg_mod(add_mod(mul_shoup(a1, s1.x, s1.y, lc.q), x1, lc.q), lc.q);
+    ulonglong2* k0 = P.key + (size_t)limb * N + e;
+    ulonglong2* k1 = P.key + (size_t)(c.L + limb) * N + e;
+    k0[0] = make_ulonglong2(p00, shoup_companion(p00, lc.q));
+    k0[1] = make_ulonglong2(p01, shoup_companion(p01, lc.q));
+    k1[0] = make_ulonglong2(a0, shoup_companion(a0, lc.q));
+    k1[1] = make_ulonglong2(a1, shoup_companion(a1, lc.q));
+  }
+};
+
+// Public-key encryption, first pass: NTT(u) of each ciphertext's ternary u.
+struct ModePkU {
+  static constexpr bool kHeavyLoad = false;
+  static constexpr int kLoadUnroll = 16;
+  static constexpr int kEpilogueUnroll = 8;
+  struct Params {
+    const int8_t* u;   // [ct][N]
+    u64* u_hat;        // [ct][L][N]
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx&, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    return lift_small(P.u[(size_t)poly * N + e], lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    *reinterpret_cast<ulonglong2*>(P.u_hat + limb_off(poly, limb, c.L, N) + e) = make_ulonglong2(x0, x1);
+  }
+};
+
+// Public-key encryption, second pass, over polynomials 2 ct + comp:
+//   comp 0: NTT(Delta m + e1) + NTT(u) p0,   comp 1: NTT(e2) + NTT(u) p1,
+// written straight into ciphertext ct (whose [2][L][N] layout makes
+// polynomial 2 ct + comp the component's slot).
+struct ModeEncryptPk {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr int kLoadUnroll = 8;
+  static constexpr int kEpilogueUnroll = 4;
+  struct Params {
+    Packing pk;
+    Accessor ac;
+    const int8_t* e1;          // [ct][N]
+    const int8_t* e2;          // [ct][N]
+    const u64* u_hat;          // [ct][L][N]
+    const ulonglong2* key;     // [2][L][N]
+    u64* ct;                   // [ct][2][L][N]
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
+                                             int e) {
+    const int ct = poly >> 1;
+    if (poly & 1) return lift_small(P.e2[(size_t)ct * N + e], lc.q);
+    const u64 r = scale_msg(gather(P.pk, P.ac, ct, e) & c.t_mask, lc, c);
+    const int ee = P.e1[(size_t)ct * N + e];
+    return ee >= 0 ? add_mod(r, (u64)ee, lc.q) : sub_mod(r, (u64)(-ee), lc.q);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                                int limb, int e, u64 x0, u64 x1) {
+    const int ct = poly >> 1, comp = poly & 1;
+    const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(P.u_hat + limb_off(ct, limb, c.L, N) + e);
+    const ulonglong2 k0 = __ldg(P.key + (size_t)(comp * c.L + limb) * N + e);
+    const ulonglong2 k1 = __ldg(P.key + (size_t)(comp * c.L + limb) * N + e + 1);
+    const u64 y0 = add_mod(x0, mul_shoup(u.x, k0.x, k0.y, lc.q), lc.q);
+    const u64 y1 = add_mod(x1, mul_shoup(u.y, k1.x, k1.y, lc.q), lc.q);
+    *reinterpret_cast<ulonglong2*>(P.ct + ct_off(ct, comp, limb, c.L, N) + e) = make_ulonglong2(y0, y1);
+  }
+};
+
 // DO decryption, first half: x = INTT(c0 + c1 * s_hat); stores y = x * qtilde mod q_j
 // (the INTT's N^{-1} and qtilde are one constant).
 struct ModeDecrypt {
@@ -492,6 +595,9 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMoPrep, false)    \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkKeygen, false)  \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkU, false)       \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncryptPk, false) \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
 // Radix 2^4 and 2^5 register blocks for one N.
 #define PENCIL_NTT_INSTANTIATE(SPEC, LOGN) \

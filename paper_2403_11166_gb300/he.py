@@ -35,14 +35,15 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_batch_destroy", "pencil_batch_workspace", "pencil_batch_bind", "pencil_batch_commit",
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
            "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
-           "pencil_lincomb", "pencil_ctx_flooding")
+           "pencil_lincomb", "pencil_ctx_flooding", "pencil_pk_keygen", "pencil_pk_destroy",
+           "encrypt_share_pk")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 TUNE_MAC_STAGING = 2
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
-                "ring", "bias_grad", "ntt_mo_prep", "lincomb")
+                "ring", "bias_grad", "ntt_mo_prep", "lincomb", "sample_pk", "ntt_pk_u", "ntt_encrypt_pk")
 
 
 class PencilError(RuntimeError):
@@ -72,7 +73,7 @@ class Partition(ctypes.Structure):
 class PlanSizes(ctypes.Structure):
     _fields_ = [("part", Partition)] + [(k, ctypes.c_int64) for k in (
         "ct_in", "pt", "ct_out", "products", "ct_words", "pt_words", "out_elems",
-        "ws_encrypt", "ws_forward", "ws_backward", "ws_decrypt")]
+        "ws_encrypt", "ws_forward", "ws_backward", "ws_decrypt", "ws_encrypt_pk")]
 
 
 class ProfEntry(ctypes.Structure):
@@ -97,6 +98,9 @@ def _load():
         "pencil_plan_slice": [P, I32, I32, ctypes.POINTER(P)],
         "pencil_lincomb": [P, P, I64, I64, I64, I64, P, I32, P, I32, P, I64, P],
         "pencil_ctx_flooding": [P, I32],
+        "pencil_pk_keygen": [P, P, U64, ctypes.POINTER(P), P],
+        "pencil_pk_destroy": [P],
+        "encrypt_share_pk": [P, P, P, I32, P, U64, P, P, SZ, P],
         "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
@@ -210,6 +214,9 @@ class Context:
     def keygen(self, seed: int, stream=None) -> "SecretKey":
         return SecretKey(self, seed, stream)
 
+    def pk_keygen(self, sk: "SecretKey", seed: int, stream=None) -> "PublicKey":
+        return PublicKey(self, sk, seed, stream)
+
     def flooding(self, bits: int):
         """pencil_ctx_flooding: flood the noise of returned ciphertexts (0 = off)."""
         _check(lib.pencil_ctx_flooding(self.h, bits), "pencil_ctx_flooding")
@@ -237,6 +244,21 @@ class SecretKey:
         try:
             if self.h and self.ctx.h:
                 lib.pencil_sk_destroy(self.h)
+        except Exception:
+            pass
+
+
+class PublicKey:
+    def __init__(self, ctx: Context, sk: SecretKey, seed: int, stream=None):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib.pencil_pk_keygen(ctx.h, sk.h, seed, ctypes.byref(h), _stream(stream)), "pencil_pk_keygen")
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                lib.pencil_pk_destroy(self.h)
         except Exception:
             pass
 
@@ -323,6 +345,13 @@ def encrypt_share(ctx: Context, sk: SecretKey, plan: Plan, operand: int, share: 
     w, nb = _ws(ws)
     _check(lib.encrypt_share(ctx.h, sk.h, plan.h, operand, _ptr(share), seed, _ptr(ct), w, nb, _stream(stream)),
            "encrypt_share")
+
+
+def encrypt_share_pk(ctx: Context, pk: PublicKey, plan: Plan, operand: int, share: torch.Tensor, seed: int,
+                     ct: torch.Tensor, ws: torch.Tensor, stream=None):
+    w, nb = _ws(ws)
+    _check(lib.encrypt_share_pk(ctx.h, pk.h, plan.h, operand, _ptr(share), seed, _ptr(ct), w, nb, _stream(stream)),
+           "encrypt_share_pk")
 
 
 def he_linear_forward(ctx: Context, plan: Plan, ct_in, pt, x0, bias, mask_seed: int, ct_out, y0, ws, stream=None):
