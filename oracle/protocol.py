@@ -277,6 +277,51 @@ def decrypt_outputs(p: BfvParams, sk, layer: Layer, role: str, part: Partition,
     return out
 
 
+def compact_returned(p: BfvParams, layer: Layer, role: str, part: Partition, ct_outs: Dict[int, np.ndarray]):
+    """MO: the send form of returned ciphertexts with the coefficients that
+    carry no output dropped: c1 as is (NTT form), c0 in coefficient form at the
+    output coefficients only, gathered as c0c[limb][flat] (flat = the output
+    element's index in the user's layout).  Returns (c1 by ct index, c0c)."""
+    g = geometry(layer, role)
+    c = counts(g, part)
+    c0c = np.zeros((len(p.primes), int(np.prod(output_shape(layer, role)))), dtype=object)
+    c1s = {}
+    for idx, ct in ct_outs.items():
+        coeff = bfv.from_ntt(p, ct[0])
+        for e, (b, o, i, j) in decode_positions(g, part, idx // c.NC, idx % c.NC):
+            c0c[:, output_flat(layer, role, b, o, i, j)] = coeff[:, e]
+        c1s[idx] = ct[1]
+    return c1s, c0c
+
+
+def decrypt_compact(p: BfvParams, sk, layer: Layer, role: str, part: Partition, c1s: Dict[int, np.ndarray],
+                    c0c: np.ndarray, out: np.ndarray | None = None) -> np.ndarray:
+    """DO: decrypt the send form: at an output coefficient e of ciphertext idx,
+    x = INTT(c1 * NTT(s))[e] + c0c[flat] per limb, CRT, m = round(t x / q) mod t."""
+    g = geometry(layer, role)
+    c = counts(g, part)
+    q, t = p.q, p.t
+    if out is None:
+        out = np.zeros(int(np.prod(output_shape(layer, role))), dtype=np.uint64)
+    for idx, c1 in c1s.items():
+        c1s_coeff = bfv.from_ntt(p, np.stack([c1[i] * sk.s_hat[i] % qi for i, qi in enumerate(p.primes)]))
+        for e, (b, o, i, j) in decode_positions(g, part, idx // c.NC, idx % c.NC):
+            flat = output_flat(layer, role, b, o, i, j)
+            x = bfv.crt(p, [(int(c1s_coeff[li, e]) + int(c0c[li, flat])) % qi for li, qi in enumerate(p.primes)])
+            out[flat] = ((2 * t * x + q) // (2 * q)) % t
+    return out
+
+
+def send_bytes(p: BfvParams, layer: Layer, role: str, part: Partition, compact: bool) -> int:
+    """Bytes of the returned ciphertexts of one evaluation (64-bit words):
+    2 L N per ciphertext, or L N per ciphertext + L per output element compacted."""
+    c = counts(geometry(layer, role), part)
+    L, n = len(p.primes), p.n
+    if not compact:
+        return 8 * 2 * L * n * c.ct_out
+    return 8 * (L * n * c.ct_out + L * int(np.prod(output_shape(layer, role))))
+
+
 def mo_share(p: BfvParams, layer: Layer, role: str, mask_seed: int, bias=None) -> np.ndarray:
     """MO's output share: s (+ b broadcast over the output channel for the forward role)."""
     shape = output_shape(layer, role)

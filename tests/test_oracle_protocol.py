@@ -128,3 +128,60 @@ def test_noise_flooding_keeps_shares_and_adds_exactly_the_flood_polynomial():
     diff = obfv.add_noise(p, plain[4][0], f)
     assert (diff == flooded[4][0]).all()
     assert not (plain[4][0] == flooded[4][0]).all()
+
+
+@pytest.mark.parametrize("kind,role", [("conv", "fwd"), ("conv", "dgrad"), ("fc", "fwd"), ("conv", "wgrad")])
+def test_compact_return_form_decrypts_to_the_same_share(kind, role):
+    """Dropping the coefficients that carry no output before sending: decrypting
+    the send form (c1 in NTT form, c0 only at output coefficients) gives exactly
+    the DO share that decrypting the whole ciphertexts gives, and the send form
+    is smaller by one c0 per ciphertext minus one word per output and limb."""
+    from oracle import bfv as obfv
+    from oracle.packing import Partition as Pt, counts
+    from oracle.params import BfvParams as BP
+    p = BP(log_n=10, num_primes=3, prime_bits=60)
+    sk = obfv.keygen(p, 2)
+    g = np.random.default_rng(5)
+    if kind == "conv":
+        L = Layer("conv", B=2, Ci=3, Co=2, h=5, w=4, s=3, pad=1)
+        part = Pt(1, 2, 2, 4, 4, 3, 3) if role != "wgrad" else Pt(1, 2, 2, 4, 4, 4, 4)
+    else:
+        L = Layer("fc", B=3, Ci=20, Co=7, h=1, w=1, s=1, pad=0)
+        part = Pt(2, 8, 4, 1, 1, 1, 1)
+    t = 1 << 41
+    if role in ("fwd", "dgrad"):
+        W = g.integers(-2000, 2000, L.w_shape())
+        shape = L.x_shape() if role == "fwd" else L.y_shape()
+        v1 = g.integers(0, t, shape, dtype=np.uint64)
+        v0 = g.integers(0, t, shape, dtype=np.uint64)
+        _, y1, _, _, ct_out = protocol.he_linear(p, sk, L, role, part, W, v1, v0, 5, 6)
+    else:
+        x0, x1 = (g.integers(0, t, L.x_shape(), dtype=np.uint64) for _ in range(2))
+        gy0, gy1 = (g.integers(0, t, L.y_shape(), dtype=np.uint64) for _ in range(2))
+        _, y1, _ = protocol.he_wgrad(p, sk, L, part, gy0, gy1, x0, x1, 5, 6, 7)
+        c = counts(protocol.geometry(L, WGRAD), part)
+        cx = protocol.encrypt_inputs(p, sk, L, WGRAD, part, x1, 5)
+        cg = protocol.encrypt_kernel_operand(p, sk, L, WGRAD, part, gy1, 6)
+        pg = protocol.encode_kernel(p, L, WGRAD, part, gy0)
+        px = protocol.encode_input(p, L, WGRAD, part, x0)
+        ct_out = {i: protocol.mo_wgrad_ct(p, L, part, cx, pg, cg, px, 7, i) for i in range(c.ct_out)}
+    c1s, c0c = protocol.compact_returned(p, L, role, part, ct_out)
+    got = protocol.decrypt_compact(p, sk, L, role, part, c1s, c0c)
+    assert (got == np.asarray(y1, dtype=np.uint64).reshape(-1)).all()
+    words = sum(v.size for v in c1s.values()) + c0c.size
+    assert protocol.send_bytes(p, L, role, part, True) == 8 * words
+    assert protocol.send_bytes(p, L, role, part, True) < protocol.send_bytes(p, L, role, part, False)
+    # a c0 coefficient carrying no output really is dropped: changing one leaves the share unchanged
+    idx = next(iter(ct_out))
+    from oracle.packing import decode_positions
+    used = {e for e, _ in decode_positions(protocol.geometry(L, role), part, idx // counts(
+        protocol.geometry(L, role), part).NC, idx % counts(protocol.geometry(L, role), part).NC)}
+    free = [e for e in range(p.n) if e not in used]
+    if free:
+        bad = {k: v.copy() for k, v in ct_out.items()}
+        coeff = obfv.from_ntt(p, bad[idx][0])
+        for li, qi in enumerate(p.primes):
+            coeff[li, free[0]] = (coeff[li, free[0]] + qi // 3) % qi
+        bad[idx][0] = obfv.to_ntt(p, coeff)
+        c1b, c0b = protocol.compact_returned(p, L, role, part, bad)
+        assert (protocol.decrypt_compact(p, sk, L, role, part, c1b, c0b) == got).all()
