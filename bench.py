@@ -557,9 +557,65 @@ def pk_and_flooding(he, device: int, reps: int = 10, flood_bits: int = 62):
             "forward_ms": ms_fwd, "forward_flooded_ms": ms_fwd_flood, "flood_bits": flood_bits, "status_ok": ok}
 
 
+def compact_send(he, device: int, reps: int = 10):
+    """Returned ciphertexts with the coefficients that carry no output dropped
+    (compact_returned on the MO, decrypt_compact_to_share on the DO), forward
+    product of the headline conv layer and of the paper's fc 2048->1001 (batch
+    64), N = 8192: bytes returned per evaluation and the two calls' time beside
+    the whole-ciphertext decryption."""
+    import torch
+    from paper_2403_11166_gb300 import inputs
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=device)
+    sk = ctx.keygen(91)
+    dev = f"cuda:{device}"
+    layers = {"conv3x3 16->16 32x32 b64": (he.Layer(he.CONV, 64, 16, 16, 32, 32, 3, 1), (16, 16, 3, 3),
+                                           (64, 16, 32, 32)),
+              "fc 2048->1001 b64": (he.Layer(he.FC, 64, 2048, 1001, 1, 1, 1, 0), (1001, 2048), (64, 2048))}
+    out = {}
+    for name, (Ly, wshape, xshape) in layers.items():
+        plan = he.Plan(ctx, Ly, he.ROLE_FWD, None)
+        S = plan.sizes
+        g = inputs.rng(92)
+        W = torch.as_tensor(inputs.gaussian_fixed(g, wshape).view(np.int64), device=dev)
+        x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+                  inputs.split_shares(g, inputs.gaussian_fixed(g, xshape)))
+        ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+        pt, ct_in, ct_out = plan.new_pt(S.pt), plan.new_ct(S.ct_in), plan.new_ct(S.ct_out)
+        y0, y1, y1c = (torch.empty(S.out_elems, dtype=torch.int64, device=dev) for _ in range(3))
+        c0c = torch.empty((L, S.out_elems), dtype=torch.int64, device=dev)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, W, pt)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1, 93, ct_in, ws)
+        he.he_linear_forward(ctx, plan, ct_in, pt, x0, None, 94, ct_out, y0, ws)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            t = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+            return statistics.median(t)
+        ms_dec = timed(lambda: he.decrypt_to_share(ctx, sk, plan, ct_out, y1, True, ws))
+        ms_cmp = timed(lambda: he.compact_returned(ctx, plan, ct_out, c0c))
+        ms_decc = timed(lambda: he.decrypt_compact_to_share(ctx, sk, plan, ct_out, c0c, y1c, True, ws))
+        torch.cuda.synchronize()
+        full = 8 * 2 * L * (1 << LOG_N) * S.ct_out
+        compact = 8 * (L * (1 << LOG_N) * S.ct_out + L * S.out_elems)
+        out[name] = {"ct_out": S.ct_out, "out_elems": S.out_elems, "returned_MB": round(full / 1e6, 2),
+                     "returned_compact_MB": round(compact / 1e6, 2), "ratio": round(compact / full, 3),
+                     "decrypt_ms": ms_dec, "compact_ms": ms_cmp, "decrypt_compact_ms": ms_decc,
+                     "same_share": bool(torch.equal(y1, y1c)), "status_ok": ctx.sync_status() == 0}
+    return out
+
+
 EXTRAS = {"batched_uneven": batched_uneven, "training_step_cnn": training_step,
           "large_conv_128_fwd_bwd": large_conv, "pencil_plus_fwd_m8": pencil_plus,
-          "paper_table5_layers_b64": table5_layers, "public_key_and_flooding": pk_and_flooding}
+          "paper_table5_layers_b64": table5_layers, "public_key_and_flooding": pk_and_flooding,
+          "compact_send_form": compact_send}
 
 
 def extras(he, device: int, names=None):

@@ -329,6 +329,23 @@ int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan
                      const uint64_t* ct_out, uint64_t* y1, int32_t check_noise,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* Compact send form of returned ciphertexts (communication reduction: the
+ * coefficients that carry no output are dropped before the MO sends them).
+ * compact_returned (MO) writes c0c[j][flat] = coefficient of INTT(c0) mod q_j
+ * at the coefficient carrying output element flat ([L][out_elems] uint64,
+ * out_elems from pencil_plan_sizes, flat = the element's row-major index in
+ * the output tensor); c1 stays in ct_out in NTT form.  What travels is then
+ * the c1 halves of ct_out (L N words per ciphertext) and c0c (L words per
+ * output) instead of 2 L N words per ciphertext.  One INTT per ciphertext.
+ * decrypt_compact_to_share (DO) reads only the c1 halves of ct_out and c0c
+ * and writes the same y1 as decrypt_to_share would on the whole ciphertexts
+ * (same noise check, same ws).  Both take slices (their output rows only; c0c
+ * is indexed by absolute flat).  Errors as decrypt_to_share. */
+int compact_returned(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* ct_out, uint64_t* c0c, void* stream);
+int decrypt_compact_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* plan,
+                             const uint64_t* ct_out, const uint64_t* c0c, uint64_t* y1, int32_t check_noise,
+                             void* ws, size_t ws_bytes, void* stream);
+
 /* Plaintext ring operator of the plan's role over Z_t (uint64 wrap-around,
  * exact because t divides 2^64): out = addend + addend2 + op(kernel_operand,
  * input_operand) mod t, with op = W o X (FWD), grad_X = W (.)_x grad_Y (DGRAD),
@@ -419,7 +436,7 @@ enum {
   PENCIL_K_NTT_MASK, PENCIL_K_INTT_DECRYPT, PENCIL_K_NTT_KEYGEN, PENCIL_K_MAC, PENCIL_K_MAC_DUAL,
   PENCIL_K_SAMPLE_ERR, PENCIL_K_MASK_POLY, PENCIL_K_MO_SHARE, PENCIL_K_DECRYPT_COMBINE, PENCIL_K_RING,
   PENCIL_K_BIAS_GRAD, PENCIL_K_NTT_MO_PREP, PENCIL_K_LINCOMB, PENCIL_K_SAMPLE_PK, PENCIL_K_NTT_PK_U,
-  PENCIL_K_NTT_ENCRYPT_PK, PENCIL_K_COUNT
+  PENCIL_K_NTT_ENCRYPT_PK, PENCIL_K_INTT_COMPACT, PENCIL_K_COUNT
 };
 typedef struct {
   int32_t kernel;   /* PENCIL_K_* */

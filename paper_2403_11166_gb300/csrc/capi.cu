@@ -1219,6 +1219,7 @@ extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const
   D.ct = ct_out;
   D.sk = sk->sk;
   D.out = reinterpret_cast<u64*>(ws);
+  D.skip_c0 = 0;
   {
     PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
     CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->out_count(), s, (int)P->out_first())));
@@ -1227,6 +1228,50 @@ extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const
     PROF(ctx, PENCIL_K_DECRYPT_COMBINE, s);
     CUDA_TRY(launch_decrypt_combine(ctx->dev, P->pk_y, P->acc_y, D.out, (int)P->out_first(), (int)P->out_count(),
                                     check_noise ? 1 : 0, y1, s));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int compact_returned(PencilCtx* ctx, const PencilPlan* P, const uint64_t* ct_out, uint64_t* c0c,
+                                void* stream) {
+  if (!ctx || !P || !ct_out || !c0c || P->ctx != ctx) return PENCIL_E_ARG;
+  if (!aligned16(ct_out)) return PENCIL_E_ARG;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  ModeCompact::Params C;
+  C.ct = ct_out;
+  C.pk = P->pk_y;
+  C.ac = P->acc_y;
+  C.c0c = c0c;
+  C.out_elems = P->out_elems;
+  {
+    PROF(ctx, PENCIL_K_INTT_COMPACT, s);
+    CUDA_TRY((ntt<ModeCompact, true>(ctx->dev, C, (int)P->out_count(), s, (int)P->out_first())));
+  }
+  return PENCIL_OK;
+}
+
+extern "C" int decrypt_compact_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const PencilPlan* P,
+                                        const uint64_t* ct_out, const uint64_t* c0c, uint64_t* y1,
+                                        int32_t check_noise, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !sk || !P || !ct_out || !c0c || !y1 || !ws || P->ctx != ctx || sk->ctx != ctx) return PENCIL_E_ARG;
+  if (!aligned16(ct_out) || !aligned16(ws)) return PENCIL_E_ARG;
+  if ((long long)ws_bytes < P->ws_decrypt) return PENCIL_E_CAPACITY;
+  DeviceGuard guard(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  ModeDecrypt::Params D;
+  D.ct = ct_out;
+  D.sk = sk->sk;
+  D.out = reinterpret_cast<u64*>(ws);
+  D.skip_c0 = 1;
+  {
+    PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
+    CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->out_count(), s, (int)P->out_first())));
+  }
+  {
+    PROF(ctx, PENCIL_K_DECRYPT_COMBINE, s);
+    CUDA_TRY(launch_decrypt_combine(ctx->dev, P->pk_y, P->acc_y, D.out, (int)P->out_first(), (int)P->out_count(),
+                                    check_noise ? 1 : 0, y1, s, c0c, P->out_elems));
   }
   return PENCIL_OK;
 }
@@ -1611,6 +1656,7 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     dec[l].ct = ct_out;
     dec[l].sk = sk->sk;
     dec[l].out = yres;
+    dec[l].skip_c0 = 0;
     comb[l] = CombineP{P->pk_y, P->acc_y, yres, u.y1};
     for (long long i = 0; i < P->pt; ++i) it_pt.push_back(make_int2(l, (int)i));
     for (long long i = 0; i < P->ct_in; ++i) it_in.push_back(make_int2(l, (int)i));

@@ -885,15 +885,19 @@ cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bi
 // so round(t x / q) mod t = round(sum_j y_j th_j / 2^128) mod t with
 // th_j = floor(2^(128 + t_bits) / q_j).  The sum is kept as a 128-bit window
 // (64 integer bits, 64 fraction bits); truncation error < L * 2^-63.
+// c0c (compact send form, else null): c0 at the output coefficients in
+// coefficient form, [L][out_elems]; added as c0c * qtil to the INTT(c1 s) residues.
 __device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Packing& pk, const Accessor& ac,
-                                                    const u64* yres, int ct, int e, int check, u64* y1) {
+                                                    const u64* yres, int ct, int e, int check, u64* y1,
+                                                    const u64* c0c = nullptr, long long out_elems = 0) {
   const int n = ctx.n;
   const i64 flat = out_index(pk, ac, ct, e);
   if (flat < 0) return;
   u64 s_lo = 0, s_hi = 0;
   for (int j = 0; j < ctx.L; ++j) {
     const LimbConst& lc = ctx.limb[j];
-    const u64 y = __ldg(yres + ((size_t)ct * ctx.L + j) * n + e);
+    u64 y = __ldg(yres + ((size_t)ct * ctx.L + j) * n + e);
+    if (c0c) y = add_mod(y, mul_shoup(__ldg(c0c + (size_t)j * out_elems + flat), lc.qtil, lc.qtils, lc.q), lc.q);
     const u64 a_hi = __umul64hi(y, lc.th_lo);
     const u64 b_lo = y * lc.th_hi;
     const u64 b_hi = __umul64hi(y, lc.th_hi);
@@ -913,18 +917,20 @@ __device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Pac
 }
 
 __global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int first, int count,
-                                  int check, u64* y1) {
+                                  int check, u64* y1, const u64* c0c, long long out_elems) {
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int n = ctx.n;
   if (id >= (long long)count * n) return;
-  decrypt_combine_one(ctx, pk, ac, yres, first + (int)(id / n), (int)(id % n), check, y1);
+  decrypt_combine_one(ctx, pk, ac, yres, first + (int)(id / n), (int)(id % n), check, y1, c0c, out_elems);
 }
 
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
-                                   int first, int count, int check, u64* y1, cudaStream_t s) {
+                                   int first, int count, int check, u64* y1, cudaStream_t s, const u64* c0c,
+                                   long long out_elems) {
   const long long total = (long long)count * ctx.n;
   if (total == 0) return cudaSuccess;
-  k_decrypt_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, yres, first, count, check, y1);
+  k_decrypt_combine<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(ctx, pk, ac, yres, first, count, check, y1, c0c,
+                                                                    out_elems);
   return cudaGetLastError();
 }
 

@@ -52,7 +52,8 @@ cudaError_t launch_mask_poly(const DevCtx& ctx, const Packing& pk, const Accesso
 cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bias, long long hw, int co, u64* y0,
                             cudaStream_t s);
 cudaError_t launch_decrypt_combine(const DevCtx& ctx, const Packing& pk, const Accessor& ac, const u64* yres,
-                                   int first, int count, int check, u64* y1, cudaStream_t s);
+                                   int first, int count, int check, u64* y1, cudaStream_t s,
+                                   const u64* c0c = nullptr, long long out_elems = 0);
 
 // Plaintext correlation over Z_t of one plan role (see k_ring_* in kernels.cu).
 struct RingParams {

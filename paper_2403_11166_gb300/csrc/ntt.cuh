@@ -515,6 +515,8 @@ struct ModeEncryptPk {
 
 // DO decryption, first half: x = INTT(c0 + c1 * s_hat); stores y = x * qtilde mod q_j
 // (the INTT's N^{-1} and qtilde are one constant).
+// With skip_c0 (decryption of the compact send form) only c1 * s is transformed;
+// the output coefficients' c0 is added by the combine kernel.
 struct ModeDecrypt {
   static constexpr bool kHeavyLoad = true;
   static constexpr int kLoadUnroll = 8;
@@ -523,20 +525,50 @@ struct ModeDecrypt {
     const u64* ct;          // [count][2][L][N]
     const ulonglong2* sk;   // [L][N]
     u64* out;               // [count][L][N]
+    int skip_c0;
   };
   static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                              int limb, int e) {
-    const u64 c0 = __ldg(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
     const u64 c1 = __ldg(P.ct + ct_off(poly, 1, limb, c.L, N) + e);
     const ulonglong2 s = __ldg(P.sk + (size_t)limb * N + e);
-    return add_mod(c0, mul_shoup(c1, s.x, s.y, lc.q), lc.q);
+    const u64 c1s = mul_shoup(c1, s.x, s.y, lc.q);
+    if (P.skip_c0) return c1s;
+    return add_mod(__ldg(P.ct + ct_off(poly, 0, limb, c.L, N) + e), c1s, lc.q);
   }
   template <int N>
   static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
     P.out[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.nqtil, lc.nqtils, lc.q);   // N^{-1} qtil
+  }
+};
+
+// MO, compact send form of returned ciphertexts: INTT(c0) and, at the
+// coefficients carrying output element flat, c0c[limb][flat] = that coefficient
+// (the rest is dropped).
+struct ModeCompact {
+  static constexpr bool kHeavyLoad = false;
+  static constexpr int kLoadUnroll = 16;
+  static constexpr int kEpilogueUnroll = 16;
+  struct Params {
+    const u64* ct;          // [count][2][L][N]
+    Packing pk;             // output packing
+    Accessor ac;            // output layout
+    u64* c0c;               // [L][out_elems]
+    long long out_elems;
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst&, int poly, int limb,
+                                             int e) {
+    return __ldg(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store(const DevCtx&, const Params& P, const LimbConst& lc, int poly,
+                                               int limb, int e, u64 x) {
+    const i64 flat = out_index(P.pk, P.ac, poly, e);
+    if (flat >= 0) P.c0c[(size_t)limb * P.out_elems + flat] = mul_shoup(x, lc.ninv, lc.ninvs, lc.q);
   }
 };
 
@@ -598,6 +630,7 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkKeygen, false)  \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkU, false)       \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncryptPk, false) \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeCompact, true)      \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
 // Radix 2^4 and 2^5 register blocks for one N.
 #define PENCIL_NTT_INSTANTIATE(SPEC, LOGN) \

@@ -36,14 +36,15 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
            "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
            "pencil_lincomb", "pencil_ctx_flooding", "pencil_pk_keygen", "pencil_pk_destroy",
-           "encrypt_share_pk")
+           "encrypt_share_pk", "compact_returned", "decrypt_compact_to_share")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 TUNE_MAC_STAGING = 2
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
-                "ring", "bias_grad", "ntt_mo_prep", "lincomb", "sample_pk", "ntt_pk_u", "ntt_encrypt_pk")
+                "ring", "bias_grad", "ntt_mo_prep", "lincomb", "sample_pk", "ntt_pk_u", "ntt_encrypt_pk",
+                "intt_compact")
 
 
 class PencilError(RuntimeError):
@@ -101,6 +102,8 @@ def _load():
         "pencil_pk_keygen": [P, P, U64, ctypes.POINTER(P), P],
         "pencil_pk_destroy": [P],
         "encrypt_share_pk": [P, P, P, I32, P, U64, P, P, SZ, P],
+        "compact_returned": [P, P, P, P, P],
+        "decrypt_compact_to_share": [P, P, P, P, P, P, I32, P, SZ, P],
         "pencil_plan_sizes": [P, ctypes.POINTER(PlanSizes)],
         "encode_weights": [P, P, I32, P, P, P],
         "encrypt_share": [P, P, P, I32, P, U64, P, P, SZ, P],
@@ -395,6 +398,19 @@ def decrypt_to_share(ctx: Context, sk: SecretKey, plan: Plan, ct_out, y1, check_
     w, nb = _ws(ws)
     _check(lib.decrypt_to_share(ctx.h, sk.h, plan.h, _ptr(ct_out), _ptr(y1), int(check_noise), w, nb,
                                 _stream(stream)), "decrypt_to_share")
+
+
+def compact_returned(ctx: Context, plan: Plan, ct_out, c0c, stream=None):
+    """MO: c0 of the returned ciphertexts at their output coefficients only,
+    c0c[limb][flat] (int64 tensor of L x out_elems)."""
+    _check(lib.compact_returned(ctx.h, plan.h, _ptr(ct_out), _ptr(c0c), _stream(stream)), "compact_returned")
+
+
+def decrypt_compact_to_share(ctx: Context, sk: SecretKey, plan: Plan, ct_out, c0c, y1, check: bool, ws,
+                             stream=None):
+    w, nb = _ws(ws)
+    _check(lib.decrypt_compact_to_share(ctx.h, sk.h, plan.h, _ptr(ct_out), _ptr(c0c), _ptr(y1), 1 if check else 0,
+                                        w, nb, _stream(stream)), "decrypt_compact_to_share")
 
 
 def pencil_ntt_batch(ctx: Context, polys: torch.Tensor, inverse: bool, stream=None):
