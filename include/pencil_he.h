@@ -398,16 +398,30 @@ int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, int32_t inv
  * sets PENCIL_E_TIMEOUT in the status word and abandons the remaining work
  * (the outputs of that call are then invalid). */
 typedef struct PencilBatch PencilBatch;
-enum { PENCIL_BATCH_PT = 0, PENCIL_BATCH_CT_IN = 1, PENCIL_BATCH_CT_OUT = 2 };
-/* plans: `count` FWD plans of ctx (each may appear once per layer). */
+enum { PENCIL_BATCH_PT = 0, PENCIL_BATCH_CT_IN = 1, PENCIL_BATCH_CT_OUT = 2, PENCIL_BATCH_CT_KERNEL = 3 };
+/* plans: `count` whole plans of ctx, any role: a FWD or DGRAD plan is one Alg. 1
+ * product (forward, or the input gradient W (.)_x grad_Y), a WGRAD plan one
+ * Alg. 2 weight gradient (both cross terms).  A plan may appear several times.
+ * So a training step's forward and backward products of every layer run as one
+ * launch sequence. */
 int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plans, int32_t count, PencilBatch** out);
 int pencil_batch_destroy(PencilBatch* batch);
 /* Bytes of device workspace holding every layer's plaintexts and ciphertexts. */
 int pencil_batch_workspace(const PencilBatch* batch, int64_t* bytes);
-/* Device buffers of layer `layer` (user layouts as for the per-layer calls;
- * bias nullable). */
+/* Device buffers of an Alg. 1 entry `layer` (FWD or DGRAD plan; user layouts as
+ * for the per-layer calls): W, the DO's and MO's shares x1, x0 of the product's
+ * input (X, or grad_Y for DGRAD), bias (FWD only, nullable), the output shares
+ * y0 (MO), y1 (DO).  PENCIL_E_ARG for a WGRAD plan or a DGRAD bias. */
 int pencil_batch_bind(PencilBatch* batch, int32_t layer, const int64_t* W, const uint64_t* x1, const uint64_t* x0,
                       const uint64_t* bias, uint64_t* y0, uint64_t* y1);
+/* Device buffers of an Alg. 2 entry `layer` (WGRAD plan): shares gy0, gy1 of
+ * grad_Y and x0, x1 of X; outputs gw_mask (the MO's mask s) and tilde (the
+ * DO's decryption of the cross terms minus s), as he_linear_backward and
+ * decrypt_to_share give them.  Enc(<X>_1) uses enc_seed + layer, Enc(<gY>_1)
+ * enc_seed + layer + 2^31, the mask mask_seed + layer (plus step 2^32).
+ * PENCIL_E_ARG for another role. */
+int pencil_batch_bind_wgrad(PencilBatch* batch, int32_t layer, const uint64_t* gy0, const uint64_t* gy1,
+                            const uint64_t* x0, const uint64_t* x1, uint64_t* gw_mask, uint64_t* tilde);
 /* Builds the device work lists and parameters (allocates and copies: call it
  * before any capture).  Requires every layer bound, ws >= pencil_batch_workspace
  * bytes, and primes near 2^bits (the split multiply-accumulate; else
@@ -419,7 +433,9 @@ int pencil_batch_forward(PencilCtx* ctx, PencilBatch* batch, void* stream);
 /* Sets the step counter (synchronises the device) and clears an earlier abort. */
 int pencil_batch_set_step(PencilBatch* batch, uint64_t step);
 /* Copies layer `layer`'s plaintexts / input / output ciphertexts (as left by the
- * last call) to `dst` (device memory of the plan's counts, stream-ordered). */
+ * last call) to `dst` (device memory of the plan's counts, stream-ordered).
+ * For a WGRAD entry PT is the encoded <gY>_0 (pt count), CT_IN Enc(<X>_1),
+ * CT_KERNEL Enc(<gY>_1) (pt count; WGRAD entries only), CT_OUT the cross terms. */
 int pencil_batch_read(const PencilBatch* batch, int32_t layer, int32_t which, uint64_t* dst, void* stream);
 /* Failure injection for tests: layer `layer`'s ready word is never written
  * (-1: none), so the multiply-accumulate times out instead of hanging. */

@@ -1487,14 +1487,19 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
 struct PencilBatch {
   PencilCtx* ctx = nullptr;
   std::vector<const PencilPlan*> plans;
+  // FWD / DGRAD layers: W, x1, x0 (the DO's and MO's shares of the product's
+  // input), bias, y0, y1.  WGRAD layers: g0, g1 (shares of grad_Y), x0, x1,
+  // y0 = the MO's mask share, y1 = the DO's decrypted share.
   struct User {
     const int64_t* W = nullptr;
-    const u64 *x1 = nullptr, *x0 = nullptr, *bias = nullptr;
+    const u64 *x1 = nullptr, *x0 = nullptr, *bias = nullptr, *g0 = nullptr, *g1 = nullptr;
     u64 *y0 = nullptr, *y1 = nullptr;
     bool bound = false;
   };
+  // p0: NTT(Delta x0) (Alg. 1) or the encoded <X>_0 (Alg. 2); ct_k, err_k: Alg. 2's
+  // Enc(<gY>_1) at kernel positions and its errors.
   struct Off {
-    long long pt, ct_in, ct_out, err, p0, mnt, mpoly, yres;
+    long long pt, ct_in, ct_out, err, p0, mnt, mpoly, yres, ct_k, err_k;
   };
   std::vector<User> user;
   std::vector<Off> off;
@@ -1510,7 +1515,7 @@ extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plan
   if (!ctx || !plans || !out || count < 1) return PENCIL_E_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i)
-    if (!plans[i] || plans[i]->ctx != ctx || plans[i]->role != PENCIL_ROLE_FWD || plans[i]->parent) return PENCIL_E_ARG;
+    if (!plans[i] || plans[i]->ctx != ctx || plans[i]->parent) return PENCIL_E_ARG;
   PencilBatch* B = new (std::nothrow) PencilBatch();
   if (!B) return PENCIL_E_CUDA;
   B->ctx = ctx;
@@ -1538,6 +1543,13 @@ extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plan
     o += al(P->ct_out * n * 8);
     f.yres = o;
     o += al(P->ct_out * lnb);
+    f.ct_k = f.err_k = 0;
+    if (P->role == PENCIL_ROLE_WGRAD) {
+      f.ct_k = o;
+      o += al(P->pt * 2 * lnb);
+      f.err_k = o;
+      o += al(P->pt * n);
+    }
     B->off.push_back(f);
   }
   B->ws_bytes = o;
@@ -1564,7 +1576,19 @@ extern "C" int pencil_batch_workspace(const PencilBatch* B, int64_t* bytes) {
 extern "C" int pencil_batch_bind(PencilBatch* B, int32_t layer, const int64_t* W, const uint64_t* x1,
                                  const uint64_t* x0, const uint64_t* bias, uint64_t* y0, uint64_t* y1) {
   if (!B || layer < 0 || layer >= (int)B->plans.size() || !W || !x1 || !x0 || !y0 || !y1) return PENCIL_E_ARG;
-  B->user[layer] = PencilBatch::User{W, x1, x0, bias, y0, y1, true};
+  const int role = B->plans[layer]->role;
+  if (role == PENCIL_ROLE_WGRAD || (bias && role != PENCIL_ROLE_FWD)) return PENCIL_E_ARG;
+  B->user[layer] = PencilBatch::User{W, x1, x0, bias, nullptr, nullptr, y0, y1, true};
+  B->committed = false;
+  return PENCIL_OK;
+}
+
+extern "C" int pencil_batch_bind_wgrad(PencilBatch* B, int32_t layer, const uint64_t* gy0, const uint64_t* gy1,
+                                       const uint64_t* x0, const uint64_t* x1, uint64_t* gw_mask, uint64_t* tilde) {
+  if (!B || layer < 0 || layer >= (int)B->plans.size() || !gy0 || !gy1 || !x0 || !x1 || !gw_mask || !tilde)
+    return PENCIL_E_ARG;
+  if (B->plans[layer]->role != PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+  B->user[layer] = PencilBatch::User{nullptr, x1, x0, nullptr, gy0, gy1, gw_mask, tilde, true};
   B->committed = false;
   return PENCIL_OK;
 }
@@ -1592,17 +1616,44 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   const int nl = (int)B->plans.size();
   // the persistent multiply-accumulate tiles 2, 4 or 8 output columns per thread
   const int nt = ctx->dev.mac_nt == 0 ? 4 : ctx->dev.mac_nt;
-  std::vector<ModeEncode::Params> enc(nl);
-  std::vector<ModeEncrypt::Params> encr(nl);
+  // encode and encrypt entries: one each per Alg. 1 layer, two each per Alg. 2 layer
+  std::vector<ModeEncode::Params> enc;
+  std::vector<ModeEncrypt::Params> encr;
+  std::vector<SampleP> samp;
   std::vector<ModeMoPrep::Params> prep(nl);
   std::vector<ModeDecrypt::Params> dec(nl);
-  std::vector<SampleP> samp(nl);
   std::vector<MaskPolyP> mpol(nl);
   std::vector<MoShareP> mosh(nl);
   std::vector<CombineP> comb(nl);
   std::vector<MacParams> mac(nl);
   std::vector<int2> it_pt, it_in, it_out, it_sh, it_prep;
   std::vector<int4> it_mac;
+  bool has_dual = false;
+  auto add_encode = [&](const Packing& pk, const Accessor& ac, const void* src, u64* dst, long long count) {
+    ModeEncode::Params e;
+    e.pk = pk;
+    e.ac = ac;
+    e.ac.ptr = reinterpret_cast<const u64*>(src);
+    e.pt = dst;
+    const int idx = (int)enc.size();
+    enc.push_back(e);
+    for (long long i = 0; i < count; ++i) it_pt.push_back(make_int2(idx, (int)i));
+  };
+  auto add_encrypt = [&](const Packing& pk, const Accessor& ac, const u64* src, u64* ct, int8_t* err, u64 seed,
+                         long long count) {
+    ModeEncrypt::Params e;
+    e.pk = pk;
+    e.ac = ac;
+    e.ac.ptr = src;
+    e.err = err;
+    e.sk = sk->sk;
+    e.ct = ct;
+    e.seed = seed;
+    const int idx = (int)encr.size();
+    encr.push_back(e);
+    samp.push_back(SampleP{seed, err});
+    for (long long i = 0; i < count; ++i) it_in.push_back(make_int2(idx, (int)i));
+  };
   for (int l = 0; l < nl; ++l) {
     const PencilPlan* P = B->plans[l];
     const auto& u = B->user[l];
@@ -1615,53 +1666,62 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
     u64* mnt = reinterpret_cast<u64*>(w + f.mnt);
     u64* mpoly = reinterpret_cast<u64*>(w + f.mpoly);
     u64* yres = reinterpret_cast<u64*>(w + f.yres);
-    enc[l].pk = P->pk_w;
-    enc[l].ac = P->acc_w;
-    enc[l].ac.ptr = reinterpret_cast<const u64*>(u.W);
-    enc[l].pt = pt;
-    samp[l] = SampleP{enc_seed + (u64)l, err};
-    encr[l].pk = P->pk_v;
-    encr[l].ac = P->acc_v;
-    encr[l].ac.ptr = u.x1;
-    encr[l].err = err;
-    encr[l].sk = sk->sk;
-    encr[l].ct = ct_in;
-    encr[l].seed = enc_seed + (u64)l;
+    const bool wg = P->role == PENCIL_ROLE_WGRAD;
     memset(&prep[l], 0, sizeof(ModeMoPrep::Params));
-    prep[l].pk = P->pk_v;
-    prep[l].ac = P->acc_v;
-    prep[l].ac.ptr = u.x0;
     prep[l].mpoly = mpoly;
-    prep[l].n_in = (int)P->ct_in;
-    prep[l].out_in = p0;
     prep[l].out_mask = mnt;
     prep[l].seed = mask_seed + (u64)l;
     memset(&mac[l], 0, sizeof(MacParams));
-    mac[l].a0 = ct_in;   // + NTT(Delta x0) on load, - NTT(Delta s) on store (Alg. 1 steps 2-3)
+    mac[l].a0 = ct_in;
     mac[l].a0_stride = 2 * lnw;
-    mac[l].p0 = p0;
-    mac[l].p0_stride = lnw;
-    mac[l].mask = mnt;
     mac[l].a1 = ct_in + lnw;
     mac[l].a1_stride = 2 * lnw;
     mac[l].b = pt;
     mac[l].b_stride = lnw;
+    mac[l].mask = mnt;   // - NTT(Delta s) on store (Alg. 1 step 3, Alg. 2 step 2)
     mac[l].out = ct_out;
     mac[l].M = (int)P->c.M();
     mac[l].K = (int)P->c.K();
     mac[l].NC = P->c.NC;
     mac[l].lanes = (int)lnw;
+    if (wg) {
+      // Alg. 2: <gY>_0 at kernel positions and <X>_0 at input positions encoded;
+      // Enc(<X>_1) and Enc(<gY>_1) (seed + 2^31); out = Enc(x1) gy0 + Enc(gy1) x0 - Delta s
+      u64* ct_k = reinterpret_cast<u64*>(w + f.ct_k);
+      int8_t* err_k = reinterpret_cast<int8_t*>(w + f.err_k);
+      add_encode(P->pk_w, P->acc_w, u.g0, pt, P->pt);
+      add_encode(P->pk_v, P->acc_v, u.x0, p0, P->ct_in);
+      add_encrypt(P->pk_v, P->acc_v, u.x1, ct_in, err, enc_seed + (u64)l, P->ct_in);
+      add_encrypt(P->pk_w, P->acc_w, u.g1, ct_k, err_k, enc_seed + (u64)l + (1ull << 31), P->pt);
+      prep[l].n_in = 0;
+      mac[l].pa = p0;
+      mac[l].pa_stride = lnw;
+      mac[l].cb0 = ct_k;
+      mac[l].cb1 = ct_k + lnw;
+      mac[l].cb_stride = 2 * lnw;
+      has_dual = true;
+    } else {
+      // Alg. 1 (forward or input gradient): + NTT(Delta x0) on load
+      add_encode(P->pk_w, P->acc_w, u.W, pt, P->pt);
+      add_encrypt(P->pk_v, P->acc_v, u.x1, ct_in, err, enc_seed + (u64)l, P->ct_in);
+      prep[l].pk = P->pk_v;
+      prep[l].ac = P->acc_v;
+      prep[l].ac.ptr = u.x0;
+      prep[l].n_in = (int)P->ct_in;
+      prep[l].out_in = p0;
+      mac[l].p0 = p0;
+      mac[l].p0_stride = lnw;
+    }
     mpol[l] = MaskPolyP{P->pk_y, P->acc_y, mask_seed + (u64)l, mpoly};
-    mosh[l] = MoShareP{mask_seed + (u64)l, P->out_elems, u.bias, P->hw, P->co_out, u.y0};
+    mosh[l] = wg ? MoShareP{mask_seed + (u64)l, P->out_elems, nullptr, 1, 1, u.y0}
+                 : MoShareP{mask_seed + (u64)l, P->out_elems, u.bias, P->hw, P->co_out, u.y0};
     dec[l].ct = ct_out;
     dec[l].sk = sk->sk;
     dec[l].out = yres;
     dec[l].skip_c0 = 0;
     comb[l] = CombineP{P->pk_y, P->acc_y, yres, u.y1};
-    for (long long i = 0; i < P->pt; ++i) it_pt.push_back(make_int2(l, (int)i));
-    for (long long i = 0; i < P->ct_in; ++i) it_in.push_back(make_int2(l, (int)i));
     for (long long i = 0; i < P->ct_out; ++i) it_out.push_back(make_int2(l, (int)i));
-    for (long long i = 0; i < P->ct_in + P->ct_out; ++i) it_prep.push_back(make_int2(l, (int)i));
+    for (long long i = 0; i < prep[l].n_in + P->ct_out; ++i) it_prep.push_back(make_int2(l, (int)i));
     for (long long c = 0; c < (P->out_elems + 1023) / 1024; ++c) it_sh.push_back(make_int2(l, (int)c));
     const int lane_blocks = (int)((lnw + 127) / 128);
     for (long long m = 0; m < P->c.M(); ++m)
@@ -1725,7 +1785,8 @@ extern "C" int pencil_batch_commit(PencilBatch* B, const PencilSecretKey* sk, vo
   D.abort_flag = reinterpret_cast<int*>(D.ready + nl + 1);
   D.withhold = withhold;
   D.mac_nt = nt;
-  CUDA_TRY(batch_mac_blocks(ctx->dev, nt, &D.mac_blocks));
+  D.has_dual = has_dual ? 1 : 0;
+  CUDA_TRY(batch_mac_blocks(ctx->dev, nt, D.has_dual, &D.mac_blocks));
   B->ws = w;
   B->mac_nt = ctx->dev.mac_nt;
   B->committed = true;
@@ -1767,6 +1828,11 @@ extern "C" int pencil_batch_read(const PencilBatch* B, int32_t layer, int32_t wh
     case PENCIL_BATCH_CT_OUT:
       o = f.ct_out;
       bytes = P->ct_out * 2 * lnb;
+      break;
+    case PENCIL_BATCH_CT_KERNEL:
+      if (P->role != PENCIL_ROLE_WGRAD) return PENCIL_E_ARG;
+      o = f.ct_k;
+      bytes = P->pt * 2 * lnb;
       break;
     default:
       return PENCIL_E_ARG;

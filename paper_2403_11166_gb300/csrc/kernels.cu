@@ -1193,7 +1193,9 @@ __device__ __forceinline__ bool wait_ready(const u64* ready, int layer, u64 want
   return v != 0;
 }
 
-template <int NT>
+// HAS_DUAL: the batch holds Alg. 2 layers (MacParams::pa set), whose tiles take
+// two products per input block; the ring is then sized for them.
+template <int NT, bool HAS_DUAL>
 __global__ void __launch_bounds__(128) k_mac_persistent(DevCtx ctx, const MacParams* __restrict__ Ps,
                                                         const int4* __restrict__ items, long long n_items,
                                                         const u64* ready, const u64* step, int* abort_flag) {
@@ -1204,8 +1206,35 @@ __global__ void __launch_bounds__(128) k_mac_persistent(DevCtx ctx, const MacPar
     if (!wait_ready(ready, it.x, want, ctx.status, abort_flag)) return;
     const MacParams& P = Ps[it.x];
     const int lane = it.w * blockDim.x + threadIdx.x;
-    if (lane < P.lanes) mac_split_tile<NT, false>(ctx, P, it.y, it.z, lane, ring, threadIdx.x);
+    if (lane >= P.lanes) continue;
+    if constexpr (HAS_DUAL) {
+      if (P.pa) {
+        mac_split_tile<NT, true>(ctx, P, it.y, it.z, lane, ring, threadIdx.x);
+        continue;
+      }
+    }
+    mac_split_tile<NT, false>(ctx, P, it.y, it.z, lane, ring, threadIdx.x);
   }
+}
+
+template <int NT, bool HAS_DUAL>
+static cudaError_t launch_mac_persistent(const DevCtx& ctx, const BatchDev& B, unsigned grid, cudaStream_t s) {
+  constexpr size_t smem = MacRing<NT, HAS_DUAL>::bytes(128);
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_mac_persistent<NT, HAS_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_mac_persistent<NT, HAS_DUAL><<<grid, 128, smem, s>>>(ctx, B.mac, B.items_mac, B.n_mac, B.ready, B.step,
+                                                         B.abort_flag);
+  return cudaGetLastError();
+}
+
+template <int NT, bool HAS_DUAL>
+static cudaError_t mac_persistent_occupancy(int* per) {
+  constexpr size_t smem = MacRing<NT, HAS_DUAL>::bytes(128);
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_mac_persistent<NT, HAS_DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_mac_persistent<NT, HAS_DUAL>, 128, smem);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1237,20 +1266,16 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (B.n_mac) {
     const unsigned grid = (unsigned)std::min<long long>(B.n_mac, (long long)B.mac_blocks);
-    switch (B.mac_nt) {
-      case 2:
-        k_mac_persistent<2><<<grid, 128, MacRing<2, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
-                                                                                B.ready, B.step, B.abort_flag);
-        break;
-      case 8:
-        k_mac_persistent<8><<<grid, 128, MacRing<8, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
-                                                                                B.ready, B.step, B.abort_flag);
-        break;
-      default:
-        k_mac_persistent<4><<<grid, 128, MacRing<4, false>::bytes(128), s>>>(ctx, B.mac, B.items_mac, B.n_mac,
-                                                                                B.ready, B.step, B.abort_flag);
+    if (B.has_dual) {
+      e = B.mac_nt == 2   ? launch_mac_persistent<2, true>(ctx, B, grid, s)
+          : B.mac_nt == 8 ? launch_mac_persistent<8, true>(ctx, B, grid, s)
+                          : launch_mac_persistent<4, true>(ctx, B, grid, s);
+    } else {
+      e = B.mac_nt == 2   ? launch_mac_persistent<2, false>(ctx, B, grid, s)
+          : B.mac_nt == 8 ? launch_mac_persistent<8, false>(ctx, B, grid, s)
+                          : launch_mac_persistent<4, false>(ctx, B, grid, s);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
   }
   if (B.n_share) {
     k_mo_share_multi<<<blocks_for(B.n_share * 256, 256), 256, 0, s>>>(B.moshare, B.items_share, B.n_share,
@@ -1267,25 +1292,18 @@ cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int* blocks) {
+cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int has_dual, int* blocks) {
   (void)ctx;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    switch (nt) {
-      case 2:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<2>, 128,
-                                                        MacRing<2, false>::bytes(128));
-        break;
-      case 8:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<8>, 128,
-                                                        MacRing<8, false>::bytes(128));
-        break;
-      default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mac_persistent<4>, 128,
-                                                        MacRing<4, false>::bytes(128));
-    }
+    if (has_dual)
+      e = nt == 2 ? mac_persistent_occupancy<2, true>(&per)
+          : nt == 8 ? mac_persistent_occupancy<8, true>(&per) : mac_persistent_occupancy<4, true>(&per);
+    else
+      e = nt == 2 ? mac_persistent_occupancy<2, false>(&per)
+          : nt == 8 ? mac_persistent_occupancy<8, false>(&per) : mac_persistent_occupancy<4, false>(&per);
   }
   *blocks = std::max(1, sms * std::max(1, per));
   return e;

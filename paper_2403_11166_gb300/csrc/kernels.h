@@ -120,13 +120,14 @@ struct BatchDev {
   long long n_mac;
   int mac_blocks;
   int mac_nt;          // output columns per thread of the persistent multiply-accumulate: 2, 4 or 8
+  int has_dual;        // some layer is an Alg. 2 weight gradient (two products per input block)
   u64* ready;          // [n_layers]
   u64* step;           // replay counter
   int* abort_flag;
   int withhold;        // layer whose ready word is not written (failure injection), or -1
 };
 cudaError_t launch_batch_forward(const DevCtx& ctx, const BatchDev& B, cudaStream_t s);
-cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int* blocks);
+cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int has_dual, int* blocks);
 
 cudaError_t launch_mul_probe(int which, long long iters, int blocks, int threads, u64 seed, u64* sink,
                              cudaStream_t s);

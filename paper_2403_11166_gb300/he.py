@@ -36,8 +36,9 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_batch_forward", "pencil_batch_set_step", "pencil_batch_read", "pencil_batch_withhold",
            "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
            "pencil_lincomb", "pencil_ctx_flooding", "pencil_pk_keygen", "pencil_pk_destroy",
-           "encrypt_share_pk", "compact_returned", "decrypt_compact_to_share")
-BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT = 0, 1, 2
+           "encrypt_share_pk", "compact_returned", "decrypt_compact_to_share",
+           "pencil_batch_bind_wgrad")
+BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT, BATCH_CT_KERNEL = 0, 1, 2, 3
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 TUNE_MAC_STAGING = 2
@@ -125,6 +126,7 @@ def _load():
         "pencil_batch_destroy": [P],
         "pencil_batch_workspace": [P, ctypes.POINTER(I64)],
         "pencil_batch_bind": [P, I32, P, P, P, P, P, P],
+        "pencil_batch_bind_wgrad": [P, I32, P, P, P, P, P, P],
         "pencil_batch_commit": [P, P, P, SZ, U64, U64],
         "pencil_batch_forward": [P, P, P],
         "pencil_batch_set_step": [P, U64],
@@ -440,7 +442,8 @@ def encrypt_share_noalloc(ctx: Context, sk: SecretKey, plan: Plan, operand: int,
 
 
 class Batch:
-    """Many FWD plans of one context as one fixed launch sequence (pencil_batch_*)."""
+    """Many plans of one context (forward, input-gradient and weight-gradient
+    products) as one fixed launch sequence (pencil_batch_*)."""
 
     def __init__(self, ctx: Context, plans):
         self.ctx = ctx
@@ -458,6 +461,11 @@ class Batch:
         self._keep.append((W, x1, x0, bias, y0, y1))
         _check(lib.pencil_batch_bind(self.h, layer, _ptr(W), _ptr(x1), _ptr(x0), _ptr(bias), _ptr(y0), _ptr(y1)),
                "pencil_batch_bind")
+
+    def bind_wgrad(self, layer: int, gy0, gy1, x0, x1, gw_mask, tilde):
+        self._keep.append((gy0, gy1, x0, x1, gw_mask, tilde))
+        _check(lib.pencil_batch_bind_wgrad(self.h, layer, _ptr(gy0), _ptr(gy1), _ptr(x0), _ptr(x1), _ptr(gw_mask),
+                                           _ptr(tilde)), "pencil_batch_bind_wgrad")
 
     def commit(self, sk: SecretKey, ws: torch.Tensor, enc_seed: int, mask_seed: int):
         self._ws = ws

@@ -165,3 +165,126 @@ def test_autotuner_choice_keeps_results(he):
         assert p.part == tuple(best["partitions"][i])
         r = _reference(he, ctx, sk, p, W, x0, x1, None, 1000 + i, 5000 + i)
         assert torch.equal(y0, r[3]) and torch.equal(y1, r[4])
+
+
+def _shapes(he, L):
+    if L.kind == he.FC:
+        return (L.c_out, L.c_in), (L.batch, L.c_in), (L.batch, L.c_out)
+    ho, wo = L.height + 2 * L.pad - L.kernel + 1, L.width + 2 * L.pad - L.kernel + 1
+    return ((L.c_out, L.c_in, L.kernel, L.kernel), (L.batch, L.c_in, L.height, L.width),
+            (L.batch, L.c_out, ho, wo))
+
+
+def _mixed_setup(he, ctx, sk, seed):
+    conv = he.Layer(he.CONV, 4, 16, 8, 8, 8, 3, 1)
+    fc = he.Layer(he.FC, 16, 512, 10)
+    entries = [(he.ROLE_FWD, conv), (he.ROLE_DGRAD, conv), (he.ROLE_WGRAD, conv),
+               (he.ROLE_FWD, fc), (he.ROLE_DGRAD, fc), (he.ROLE_WGRAD, fc)]
+    plans = [he.Plan(ctx, L, r, None) for r, L in entries]
+    batch = he.Batch(ctx, plans)
+    g = inputs.rng(seed)
+    data = []
+    for i, ((r, L), p) in enumerate(zip(entries, plans)):
+        wshape, xshape, yshape = _shapes(he, L)
+        n = p.sizes.out_elems
+        y0 = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        y1 = torch.full_like(y0, -1)
+        if r == he.ROLE_WGRAD:
+            x0, x1 = (to_dev(a) for a in inputs.split_shares(g, inputs.gaussian_fixed(g, xshape)))
+            g0, g1 = (to_dev(a) for a in inputs.split_shares(g, inputs.gaussian_fixed(g, yshape)))
+            batch.bind_wgrad(i, g0, g1, x0, x1, y0, y1)
+            data.append(("wgrad", g0, g1, x0, x1, y0, y1))
+        else:
+            W = to_dev(inputs.gaussian_fixed(g, wshape))
+            v0, v1 = (to_dev(a) for a in inputs.split_shares(
+                g, inputs.gaussian_fixed(g, xshape if r == he.ROLE_FWD else yshape)))
+            bias = to_dev(inputs.uniform_zt(g, (L.c_out,))) if r == he.ROLE_FWD else None
+            batch.bind(i, W, v1, v0, bias, y0, y1)
+            data.append(("alg1", W, v0, v1, bias, y0, y1))
+    ws = torch.empty((batch.workspace_bytes + 7) // 8, dtype=torch.int64, device="cuda")
+    batch.commit(sk, ws, ENC, MASK)
+    return plans, batch, data
+
+
+def _check_mixed_step(he, ctx, sk, plans, batch, data, step):
+    for i, (p, d) in enumerate(zip(plans, data)):
+        enc, mask = ENC + i + (step << 32), MASK + i + (step << 32)
+        got_out = p.new_ct(p.sizes.ct_out)
+        batch.read(i, he.BATCH_CT_OUT, got_out)
+        if d[0] == "alg1":
+            _, W, v0, v1, bias, y0, y1 = d
+            pt, ct_in, ct_out, r0, r1 = _reference(he, ctx, sk, p, W, v0, v1, bias, enc, mask)
+            got_in = torch.empty_like(ct_in)
+            batch.read(i, he.BATCH_CT_IN, got_in)
+            torch.cuda.synchronize()
+            assert torch.equal(got_in, ct_in), i
+        else:
+            _, g0, g1, x0, x1, y0, y1 = d
+            S = p.sizes
+            ws = p.new_ws(max(S.ws_encrypt, S.ws_backward, S.ws_decrypt))
+            ct_x1, ct_g1, ct_out = p.new_ct(S.ct_in), p.new_ct(S.pt), p.new_ct(S.ct_out)
+            he.encrypt_share(ctx, sk, p, he.OPERAND_INPUT, x1, enc, ct_x1, ws)
+            he.encrypt_share(ctx, sk, p, he.OPERAND_KERNEL, g1, enc + (1 << 31), ct_g1, ws)
+            r0 = torch.empty(S.out_elems, dtype=torch.int64, device="cuda")
+            r1 = torch.empty_like(r0)
+            he.he_linear_backward(ctx, None, p, None, None, ct_x1, ct_g1, g0, x0, 0, mask, None, None, ct_out, r0, ws)
+            he.decrypt_to_share(ctx, sk, p, ct_out, r1, True, ws)
+            got_k = torch.empty_like(ct_g1)
+            batch.read(i, he.BATCH_CT_KERNEL, got_k)
+            torch.cuda.synchronize()
+            assert torch.equal(got_k, ct_g1), i
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        assert torch.equal(got_out, ct_out), i
+        assert torch.equal(y0, r0) and torch.equal(y1, r1), i
+
+
+def test_batch_forward_and_backward_roles(he):
+    """Forward, input-gradient and weight-gradient entries of a conv and an FC
+    layer in one batch: bit-identical to the per-layer calls on two steps."""
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(8)
+    plans, batch, data = _mixed_setup(he, ctx, sk, seed=4)
+    for step in (0, 1):
+        batch.forward()
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == 0
+        _check_mixed_step(he, ctx, sk, plans, batch, data, step)
+
+
+def test_batch_backward_roles_in_cuda_graph(he):
+    ctx = he.Context(13, 3, 60)
+    ctx.tune(he.TUNE_MAC_COLUMNS, 2)
+    sk = ctx.keygen(9)
+    plans, batch, data = _mixed_setup(he, ctx, sk, seed=5)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.forward(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.forward()
+    batch.set_step(3)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    _check_mixed_step(he, ctx, sk, plans, batch, data, 3)
+
+
+def test_batch_bind_checks_roles(he):
+    ctx = he.Context(12, 2, 54)
+    L = he.Layer(he.FC, 4, 32, 8)
+    pw = he.Plan(ctx, L, he.ROLE_WGRAD, None)
+    pd = he.Plan(ctx, L, he.ROLE_DGRAD, None)
+    batch = he.Batch(ctx, [pw, pd])
+    t = torch.zeros(4096, dtype=torch.int64, device="cuda")
+    with pytest.raises(he.PencilError):
+        batch.bind(0, t, t, t, None, t, t)          # a WGRAD entry takes bind_wgrad
+    with pytest.raises(he.PencilError):
+        batch.bind(1, t, t, t, t, t, t)             # no bias on the input gradient
+    with pytest.raises(he.PencilError):
+        batch.bind_wgrad(1, t, t, t, t, t, t)       # a DGRAD entry takes bind
+    batch.bind(1, t, t, t, None, t, t)
+    batch.bind_wgrad(0, t, t, t, t, t, t)
