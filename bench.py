@@ -341,6 +341,124 @@ def batched_uneven(he, device: int, reps: int = 5):
     return out
 
 
+def batched_fwd_bwd(he, device: int, reps: int = 5):
+    """A training step's HE products of the 96 uneven layers: forward (Alg. 1),
+    input gradient (Alg. 1 on the transposed kernel) and weight gradient (Alg. 2)
+    of every layer, 288 entries.  Per-layer C-ABI calls (encode, encrypt,
+    evaluate, decrypt for each) vs one captured CUDA graph of the batch."""
+    import torch
+    from paper_2403_11166_gb300 import tuner
+    layers = ([he.Layer(he.FC, 16, 512, 10)] * 32 + [he.Layer(he.CONV, 32, 64, 64, 8, 8, 3, 1)] * 32
+              + [he.Layer(he.CONV, 8, 128, 256, 4, 4, 1, 0)] * 32)
+    ctx = he.Context(LOG_N, L, PRIME_BITS, T_BITS, device=device)
+    sk = ctx.keygen(78)
+    dev = f"cuda:{device}"
+    roles = (he.ROLE_FWD, he.ROLE_DGRAD, he.ROLE_WGRAD)
+    entries = [(r, Ly) for Ly in layers for r in roles]
+    plans = [he.Plan(ctx, Ly, r, None) for r, Ly in entries]
+    g = torch.Generator(device="cpu").manual_seed(79)
+
+    def shares(shape):
+        return tuple(torch.randint(0, 1 << T_BITS, shape, generator=g, dtype=torch.int64).to(dev) for _ in range(2))
+    data = []
+    for i, ((r, Ly), p) in enumerate(zip(entries, plans)):
+        W, x0, x1 = tuner._layer_buffers(ctx, Ly, i)
+        if Ly.kind == he.FC:
+            yshape = (Ly.batch, Ly.c_out)
+        else:
+            yshape = (Ly.batch, Ly.c_out, Ly.height + 2 * Ly.pad - Ly.kernel + 1,
+                      Ly.width + 2 * Ly.pad - Ly.kernel + 1)
+        g0, g1 = shares(yshape)
+        data.append({"W": W, "x0": x0, "x1": x1, "g0": g0, "g1": g1})
+    products = sum(p.sizes.products * (2 if r == he.ROLE_WGRAD else 1) for (r, _), p in zip(entries, plans))
+    out = {"layers": len(layers), "entries": len(entries), "products_per_step": products}
+
+    # per-layer calls
+    bufs = []
+    for (r, Ly), p in zip(entries, plans):
+        S = p.sizes
+        y = [torch.empty(S.out_elems, dtype=torch.int64, device=dev) for _ in range(2)]
+        ws = p.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_backward, S.ws_decrypt))
+        if r == he.ROLE_WGRAD:
+            bufs.append((p.new_ct(S.ct_in), p.new_ct(S.pt), p.new_ct(S.ct_out), y[0], y[1], ws))
+        else:
+            bufs.append((p.new_pt(S.pt), p.new_ct(S.ct_in), p.new_ct(S.ct_out), y[0], y[1], ws))
+
+    def per_layer(step):
+        for i, ((r, Ly), p, d, b) in enumerate(zip(entries, plans, data, bufs)):
+            e, m = 1000 + i + (step << 32), 5000 + i + (step << 32)
+            if r == he.ROLE_WGRAD:
+                ct_x1, ct_g1, ct_out, y0, y1, ws = b
+                he.encrypt_share(ctx, sk, p, he.OPERAND_INPUT, d["x1"], e, ct_x1, ws)
+                he.encrypt_share(ctx, sk, p, he.OPERAND_KERNEL, d["g1"], e + (1 << 31), ct_g1, ws)
+                he.he_linear_backward(ctx, None, p, None, None, ct_x1, ct_g1, d["g0"], d["x0"], 0, m, None, None,
+                                      ct_out, y0, ws)
+            else:
+                pt, ct_in, ct_out, y0, y1, ws = b
+                v0, v1 = (d["x0"], d["x1"]) if r == he.ROLE_FWD else (d["g0"], d["g1"])
+                he.encode_weights(ctx, p, he.OPERAND_KERNEL, d["W"], pt)
+                he.encrypt_share(ctx, sk, p, he.OPERAND_INPUT, v1, e, ct_in, ws)
+                if r == he.ROLE_FWD:
+                    he.he_linear_forward(ctx, p, ct_in, pt, v0, None, m, ct_out, y0, ws)
+                else:
+                    he.he_linear_backward(ctx, p, None, ct_in, pt, None, None, v0, None, m, 0, ct_out, y0, None,
+                                          None, ws)
+            he.decrypt_to_share(ctx, sk, p, ct_out, y1, False, ws)
+    per_layer(0)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for r in range(reps):
+        per_layer(r + 1)
+    b.record(stream)
+    b.synchronize()
+    ms_pl = a.elapsed_time(b) / reps
+    out["per_layer_calls"] = {"ms_per_step": ms_pl, "products_per_s": products / (ms_pl * 1e-3)}
+    del bufs
+    torch.cuda.empty_cache()
+
+    # one batch, one captured graph
+    batch = he.Batch(ctx, plans)
+    outs = []
+    for i, ((r, Ly), p, d) in enumerate(zip(entries, plans, data)):
+        y0, y1 = (torch.empty(p.sizes.out_elems, dtype=torch.int64, device=dev) for _ in range(2))
+        outs.append((y0, y1))
+        if r == he.ROLE_WGRAD:
+            batch.bind_wgrad(i, d["g0"], d["g1"], d["x0"], d["x1"], y0, y1)
+        elif r == he.ROLE_FWD:
+            batch.bind(i, d["W"], d["x1"], d["x0"], None, y0, y1)
+        else:
+            batch.bind(i, d["W"], d["g1"], d["g0"], None, y0, y1)
+    ws = torch.empty((batch.workspace_bytes + 7) // 8, dtype=torch.int64, device=dev)
+    batch.commit(sk, ws, 1000, 5000)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.forward(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.forward()
+    graph.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for r in range(reps):
+        graph.replay()
+    b.record(stream)
+    b.synchronize()
+    ms_b = a.elapsed_time(b) / reps
+    out["batched_graph"] = {"ms_per_step": ms_b, "products_per_s": products / (ms_b * 1e-3),
+                            "workspace_GB": round(batch.workspace_bytes / 1e9, 2)}
+    out["status_ok"] = ctx.sync_status() == 0
+    del graph, batch, ws
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def training_step(he, device: int, reps: int = 3):
     """Secure fwd + bwd of the 3-layer CNN (conv3x3 3->16, ReLU, conv3x3 16->32,
     avgpool 2, FC 8192->10; batch 64, 32x32x3, N = 8192) through HeLinearFn."""
@@ -612,7 +730,7 @@ def compact_send(he, device: int, reps: int = 10):
     return out
 
 
-EXTRAS = {"batched_uneven": batched_uneven, "training_step_cnn": training_step,
+EXTRAS = {"batched_uneven": batched_uneven, "batched_fwd_bwd": batched_fwd_bwd, "training_step_cnn": training_step,
           "large_conv_128_fwd_bwd": large_conv, "pencil_plus_fwd_m8": pencil_plus,
           "paper_table5_layers_b64": table5_layers, "public_key_and_flooding": pk_and_flooding,
           "compact_send_form": compact_send}
