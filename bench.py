@@ -454,6 +454,20 @@ def batched_fwd_bwd(he, device: int, reps: int = 5):
                             "workspace_GB": round(batch.workspace_bytes / 1e9, 2)}
     out["status_ok"] = ctx.sync_status() == 0
     del graph, batch, ws
+    torch.cuda.empty_cache()
+    # autotuned: partitions per (shape, role) and the multiply-accumulate's columns
+    t0 = time.perf_counter()
+    e_layers, e_roles = [Ly for _, Ly in entries], [r for r, _ in entries]
+    best = tuner.tune_batch(ctx, sk, e_layers, topk=3, reps=3, radices=(4,), columns=(2, 4, 8), stagings=(1,),
+                            roles=e_roles)
+    tune_s = time.perf_counter() - t0
+    gb = tuner.GraphBatch(ctx, sk, e_layers, best["partitions"], roles=e_roles)
+    ms_t = gb.time(reps)
+    out["batched_graph_autotuned"] = {"ms_per_step": ms_t, "products_per_s": gb.products / (ms_t * 1e-3),
+                                      "products_per_step": gb.products, "mac_columns": best["mac_columns"],
+                                      "tuning_seconds": round(tune_s, 1)}
+    out["status_ok"] = out["status_ok"] and ctx.sync_status() == 0
+    del gb
     ctx.close()
     torch.cuda.empty_cache()
     return out

@@ -288,3 +288,47 @@ def test_batch_bind_checks_roles(he):
         batch.bind_wgrad(1, t, t, t, t, t, t)       # a DGRAD entry takes bind
     batch.bind(1, t, t, t, None, t, t)
     batch.bind_wgrad(0, t, t, t, t, t, t)
+
+
+def test_autotuner_over_forward_and_backward_roles(he):
+    """tune_batch with a training step's roles: partitions chosen per (shape,
+    role), and every entry of the tuned batch reconstructs its ring product."""
+    import numpy as np
+    from oracle import protocol
+    from oracle.protocol import Layer as OLayer
+    from paper_2403_11166_gb300 import tuner
+    from tests.gpu_util import to_np
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(10)
+    L = he.Layer(he.CONV, 2, 4, 3, 6, 6, 3, 1)
+    roles = [he.ROLE_FWD, he.ROLE_DGRAD, he.ROLE_WGRAD]
+    best = tuner.tune_batch(ctx, sk, [L] * 3, topk=2, reps=1, radices=(4,), columns=(2, 4), stagings=(1,),
+                            roles=roles)
+    gb = tuner.GraphBatch(ctx, sk, [L] * 3, best["partitions"], capture=False, roles=roles)
+    gb.batch.set_step(0)
+    gb.run()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    ol = OLayer("conv", B=2, Ci=4, Co=3, h=6, w=6, s=3, pad=1)
+    tm = np.uint64((1 << 41) - 1)
+
+    def add(*xs):
+        with np.errstate(over="ignore"):
+            acc = np.zeros_like(np.asarray(xs[0], dtype=np.uint64))
+            for x in xs:
+                acc = acc + np.asarray(x, dtype=np.uint64)
+            return acc & tm
+    for p, r, part in zip(gb.plans, roles, best["partitions"]):
+        assert p.part == tuple(part)
+    W, x0, x1, y0, y1 = gb.bufs[0]
+    x = add(to_np(x0), to_np(x1)).reshape(ol.x_shape())
+    assert (add(to_np(y0), to_np(y1)) == protocol.ring_op(ol, "fwd", to_np(W), x, 41).reshape(-1)).all()
+    W, x0, x1, g0, g1, y0, y1 = gb.bufs[1]
+    gy = add(to_np(g0), to_np(g1)).reshape(ol.y_shape())
+    assert (add(to_np(y0), to_np(y1)) == protocol.ring_op(ol, "dgrad", to_np(W), gy, 41).reshape(-1)).all()
+    W, x0, x1, g0, g1, y0, y1 = gb.bufs[2]
+    x = add(to_np(x0), to_np(x1)).reshape(ol.x_shape())
+    gy = add(to_np(g0), to_np(g1)).reshape(ol.y_shape())
+    local = add(protocol.ring_op(ol, "wgrad", to_np(g1).reshape(ol.y_shape()), to_np(x1).reshape(ol.x_shape()), 41),
+                protocol.ring_op(ol, "wgrad", to_np(g0).reshape(ol.y_shape()), to_np(x0).reshape(ol.x_shape()), 41))
+    assert (add(to_np(y0), to_np(y1), local.reshape(-1)) == protocol.ring_op(ol, "wgrad", gy, x, 41).reshape(-1)).all()
