@@ -71,6 +71,31 @@ def test_intt_matches_oracle(he, cfg):
             assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all()
 
 
+@pytest.mark.parametrize("log_n,radix", [(14, 4), (14, 5), (13, 5), (12, 5)])
+def test_both_register_radices_match_oracle(he, log_n, radix):
+    """The NTT radix knob (2^4 or 2^5 coefficients per thread) changes only the
+    schedule: forward and inverse transforms equal the oracle's for either."""
+    cfg = (log_n, 2, 60)
+    ctx = he.Context(*cfg)
+    ctx.tune(he.TUNE_NTT_LOG_RADIX, radix)
+    p = BfvParams(log_n=log_n, num_primes=2, prime_bits=60)
+    a = _random_polys(p, 2, 300 + log_n + radix)
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=False)
+    got = to_np(d)
+    for i in range(a.shape[0]):
+        for j, (q, psi) in enumerate(zip(p.primes, p.psis)):
+            want = ntt_radix2([int(x) for x in a[i, j]], q, psi)
+            assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all(), (i, j)
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=True)
+    got = to_np(d)
+    for i in range(a.shape[0]):
+        for j, (q, psi) in enumerate(zip(p.primes, p.psis)):
+            want = intt_radix2([int(x) for x in a[i, j]], q, psi)
+            assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all(), (i, j)
+
+
 def test_large_batch_roundtrip(he):
     """Full-size sweep shape (N = 8192, 3 limbs) on a batch that spans many waves:
     INTT(NTT(a)) = a everywhere, NTT spot-checked against the oracle."""
