@@ -24,8 +24,8 @@ def test_primes_are_largest_ntt_friendly(n, bits, count):
         assert q % (2 * n) == 1 and q < top
 
 
-def test_survey_primes():
-    # values quoted in the workload description for N=4096 (54-bit) and N=8192 (60-bit)
+def test_workload_primes():
+    # the moduli of the two workloads: N = 4096 with two primes below 2^54, N = 8192 with three below 2^60
     assert ntt_primes(54, 2, 8192) == [0x3ffffffffd6001, 0x3ffffffffd2001]
     assert ntt_primes(60, 3, 16384) == [0xfffffffffffc001, 0xffffffffffe8001, 0xffffffffffd8001]
 
