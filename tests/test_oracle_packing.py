@@ -107,3 +107,40 @@ def test_matrix_encoding_closed_form():
     Wt = Wm[:, :, None, None]
     assert packing.pack_input(V, g, part, n, 0, 0) == pv
     assert packing.pack_weight(Wt, g, part, n, 0, 0) == pw
+
+
+def test_appendix_a_exponents_golden():
+    """The oracle's encodings put every entry at the exponent App. A's formulas
+    give, evaluated by hand in tests/golden/appendix_a_packing.txt (matrix
+    product as the 1 x 1 case of the convolution geometry)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "appendix_a_packing.txt")
+    section, part = None, None
+    checked = 0
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "mat":
+            n_o, n_i, B = (int(x) for x in f[1:])
+            section, part = "mat", Partition(B, n_i, n_o, 1, 1, 1, 1)
+            continue
+        if f[0] == "conv":
+            B, c_o, c_i, h, w, s = (int(x) for x in f[1:])
+            section, part = "conv", Partition(B, c_i, c_o, h - s + 1, w - s + 1, s, s)
+            assert part.window() == (h, w)
+            continue
+        idx, want = [int(x) for x in f[1:-1]], int(f[-1])
+        if section == "mat":
+            if f[0] == "v":      # v_jk
+                got = packing.index_v(part, idx[1], idx[0], 0, 0)
+            elif f[0] == "W":    # W_ij
+                got = packing.index_w(part, idx[0], idx[1], 0, 0)
+            else:                # y_ik
+                got = packing.index_y(part, idx[1], idx[0], 0, 0)
+        else:
+            fn = {"v": packing.index_v, "W": packing.index_w, "y": packing.index_y}[f[0]]
+            got = fn(part, *idx)
+        assert got == want, line
+        checked += 1
+    assert checked == 31
