@@ -558,6 +558,7 @@ def pencil_plus(he, device: int, m: int = 8, reps: int = 3):
     U = torch.as_tensor(inputs.uniform_zt(g, (m * LAYER["c_out"], LAYER["c_in"], 3, 3)).view(np.int64), device=dev)
     V = torch.as_tensor(inputs.uniform_zt(g, (m * LAYER["batch"],) + xs[1:]).view(np.int64), device=dev)
     pp = prep.PrepProduct(ctx, sk, Ly, he.ROLE_FWD, m)
+    pp.preprocess(U, V, 89, 90)   # warm-up (module loading, first-touch of the workspaces); timed below
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
@@ -576,10 +577,16 @@ def pencil_plus(he, device: int, m: int = 8, reps: int = 3):
         b.record()
         b.synchronize()
         t.append(a.elapsed_time(b))
+    # one more online pass with the library's per-kernel events (serialised on the stream)
+    ctx.profile(True)
+    pp.online(W, x1, k, l)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    kern = {name: {"launches": n, "ms": round(ms, 4)} for name, (n, ms) in ctx.profile_read().items() if n}
     assert ctx.sync_status() == 0
     out = {"m": m, "preprocessing_ms": prep_ms, "preprocessing_products": pp.products,
            "online_ms": statistics.median(t), "online_products_equivalent": pp.plan_one.sizes.products,
-           "online_he_free": True}
+           "online_he_free": True, "online_kernels": kern}
     del pp
     ctx.close()
     torch.cuda.empty_cache()

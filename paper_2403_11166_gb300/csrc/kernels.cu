@@ -947,44 +947,84 @@ __device__ __forceinline__ void ring_store(const RingParams& P, int a, int o, in
   P.out[flat] = acc & P.t_mask;
 }
 
-// Short reductions: thread = output position (a, i, j) x RT consecutive output
-// channels o; the reduction runs over (c, u, v) in nested loops (no divisions),
-// each input value loaded once for the RT channels; the kernel values are the
-// same for every thread of the CTA (one channel tile per grid row: broadcast).
-#define RING_OT 4
+// Short reductions: thread = RING_PT consecutive output positions (a, i, j) x
+// RING_OT consecutive output channels o; the reduction runs over (c, u, v) in
+// nested loops (no divisions), each kernel value loaded once for the thread's
+// RING_PT positions and each input value once for its RING_OT channels (the
+// kernel values are the same for every thread of the CTA: one channel tile per
+// grid row, broadcast loads).  Channels past Co multiply a zero kernel value.
+// RING_OT = 8 channels (measured 11 % faster than 4 on a 16-channel layer) when
+// Co >= 8, else 4; 8 positions per thread measured slower.
+#define RING_PT 4
+template <int RING_OT>
 __global__ void __launch_bounds__(128) k_ring_tile(RingParams P) {
-  const long long HWo = (long long)P.Ho * P.Wo;
-  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long npos = P.outs / P.kbound.x;   // B * Ho * Wo
+  const long long pos0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * RING_PT;
+  if (pos0 >= npos) return;
   const int o0 = blockIdx.y * RING_OT;
   const int Co = P.kbound.x, Ci = P.kbound.y, KH = P.kbound.z, KW = P.kbound.w;
-  if (pos >= P.outs / Co) return;
-  const int a = (int)(pos / HWo);
-  const int p = (int)(pos - (long long)a * HWo);
-  const int i = p / P.Wo, j = p - (p / P.Wo) * P.Wo;
+  const long long HWo = (long long)P.Ho * P.Wo;
   const int no = min(RING_OT, Co - o0);
-  u64 acc[RING_OT];
+  int pa[RING_PT], pi[RING_PT], pj[RING_PT];
+  const u64* vb[RING_PT];
 #pragma unroll
-  for (int t = 0; t < RING_OT; ++t) acc[t] = 0;
-  const u64* vb = P.v.ptr + P.v.base + a * P.v.s0;
+  for (int q = 0; q < RING_PT; ++q) {
+    const long long pos = pos0 + q < npos ? pos0 + q : pos0;   // a dead slot repeats the first (not stored)
+    pa[q] = (int)(pos / HWo);
+    const int rem = (int)(pos - (long long)pa[q] * HWo);
+    pi[q] = rem / P.Wo;
+    pj[q] = rem - pi[q] * P.Wo;
+    vb[q] = P.v.ptr + P.v.base + pa[q] * P.v.s0;
+  }
+  u64 acc[RING_PT][RING_OT];
+#pragma unroll
+  for (int q = 0; q < RING_PT; ++q)
+#pragma unroll
+    for (int t = 0; t < RING_OT; ++t) acc[q][t] = 0;
+  // Index arithmetic stays out of the innermost loop: row pointers per (c, u),
+  // then pointer increments along v (the strides are 64-bit).
   const u64* wb = P.w.ptr + P.w.base + (i64)o0 * P.w.s0;
-  for (int c = 0; c < Ci; ++c) {
-    for (int u = 0; u < KH; ++u) {
-      const int rr = i + u - P.v.pr;
-      if ((unsigned)rr >= (unsigned)P.v.hr) continue;
-      for (int v = 0; v < KW; ++v) {
-        const int ss = j + v - P.v.ps;
-        if ((unsigned)ss >= (unsigned)P.v.wr) continue;
-        const u64 x = __ldg(vb + c * P.v.s1 + rr * P.v.s2 + ss * P.v.s3);
-        const u64* w = wb + c * P.w.s1 + u * P.w.s2 + v * P.w.s3;
+  i64 woff[RING_OT];
 #pragma unroll
-        for (int t = 0; t < RING_OT; ++t)
-          if (t < no) acc[t] += x * __ldg(w + t * P.w.s0);
+  for (int t = 0; t < RING_OT; ++t) woff[t] = t < no ? t * P.w.s0 : 0;
+  int col0[RING_PT];
+#pragma unroll
+  for (int q = 0; q < RING_PT; ++q) col0[q] = pj[q] - P.v.ps;
+  for (int c = 0; c < Ci; ++c) {
+    const u64* wc = wb + c * P.w.s1;
+    for (int u = 0; u < KH; ++u) {
+      const u64* xp[RING_PT];
+      bool rok[RING_PT];
+#pragma unroll
+      for (int q = 0; q < RING_PT; ++q) {
+        const int rr = pi[q] + u - P.v.pr;
+        rok[q] = (unsigned)rr < (unsigned)P.v.hr;
+        xp[q] = vb[q] + c * P.v.s1 + (rok[q] ? rr : 0) * P.v.s2 + col0[q] * P.v.s3;
+      }
+      const u64* wp = wc + u * P.w.s2;
+      for (int v = 0; v < KW; ++v) {
+        u64 wv[RING_OT];
+#pragma unroll
+        for (int t = 0; t < RING_OT; ++t) wv[t] = t < no ? __ldg(wp + woff[t]) : 0ull;
+#pragma unroll
+        for (int q = 0; q < RING_PT; ++q) {
+          if (rok[q] && (unsigned)(col0[q] + v) < (unsigned)P.v.wr) {
+            const u64 x = __ldg(xp[q]);
+#pragma unroll
+            for (int t = 0; t < RING_OT; ++t) acc[q][t] += x * wv[t];
+          }
+          xp[q] += P.v.s3;
+        }
+        wp += P.w.s3;
       }
     }
   }
 #pragma unroll
-  for (int t = 0; t < RING_OT; ++t)
-    if (t < no) ring_store(P, a, o0 + t, i, j, acc[t]);
+  for (int q = 0; q < RING_PT; ++q)
+    if (pos0 + q < npos)
+#pragma unroll
+      for (int t = 0; t < RING_OT; ++t)
+        if (t < no) ring_store(P, pa[q], o0 + t, pi[q], pj[q], acc[q][t]);
 }
 
 // Long reductions (grad_W: over batch x output positions): one CTA per output,
@@ -1028,11 +1068,15 @@ cudaError_t launch_ring(const RingParams& P, cudaStream_t s) {
     k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P);
   } else {
     const long long positions = P.outs / P.kbound.x;
-    const unsigned gx = (unsigned)((positions + 127) / 128);
-    const unsigned gy = (unsigned)((P.kbound.x + RING_OT - 1) / RING_OT);
+    const unsigned gx = (unsigned)((positions + 128 * RING_PT - 1) / (128 * RING_PT));
+    const int ot = P.kbound.x >= 8 ? 8 : 4;
+    const unsigned gy = (unsigned)((P.kbound.x + ot - 1) / ot);
     if (gy > 65535) return cudaErrorInvalidValue;
     (void)R;
-    k_ring_tile<<<dim3(gx, gy), 128, 0, s>>>(P);
+    if (ot == 8)
+      k_ring_tile<8><<<dim3(gx, gy), 128, 0, s>>>(P);
+    else
+      k_ring_tile<4><<<dim3(gx, gy), 128, 0, s>>>(P);
   }
   return cudaGetLastError();
 }

@@ -77,6 +77,35 @@ def test_lincomb_rejects_bad_arguments():
     assert e.value.code == -1
 
 
+@pytest.mark.parametrize("count,inner,outer,tstride,off,terms,negate,with_addend", [
+    (1000, 1000, 0, 1000, 0, 8, False, False),      # contiguous terms
+    (777, 64, 200, 13000, 5, 8, True, True),        # strided rows, partial last row, negated
+    (70000, 16384, 65536, 16384, 3, 64, False, True),  # many rows, the maximum term count
+    (5, 1, 3, 7, 2, 1, True, False),                 # one element per row
+])
+def test_lincomb_matches_definition(count, inner, outer, tstride, off, terms, negate, with_addend):
+    """out[e] = addend[e] +/- sum_i k_i src[off + (e // inner) outer + e % inner + i tstride] mod 2^41."""
+    from paper_2403_11166_gb300 import he
+    ctx = he.Context(12, 2, 54)
+    g = np.random.default_rng(count + terms)
+    rows = -(-count // inner)
+    need = off + (rows - 1) * outer + inner + (terms - 1) * tstride
+    src = g.integers(0, 1 << 41, need, dtype=np.uint64)
+    k = [int(x) for x in g.integers(0, 1 << 41, terms, dtype=np.uint64)]
+    add = g.integers(0, 1 << 41, count, dtype=np.uint64) if with_addend else None
+    out = torch.full((count,), -1, dtype=torch.int64, device="cuda")
+    he.pencil_lincomb(ctx, to_dev(src), k, count, out, addend=None if add is None else to_dev(add), negate=negate,
+                      src_offset=off, inner=inner, outer_stride=outer, term_stride=tstride)
+    torch.cuda.synchronize()
+    want = []
+    for e in range(count):
+        base = off + (e // inner) * outer + e % inner
+        acc = sum(k[i] * int(src[base + i * tstride]) for i in range(terms))
+        a = int(add[e]) if add is not None else 0
+        want.append(((a - acc) if negate else (a + acc)) % (1 << 41))
+    assert (to_np(out) == np.array(want, dtype=np.uint64)).all()
+
+
 def test_alg4_linear_layer_with_preprocessing():
     """Alg. 4 for one conv layer: forward shares from P_Online(o, W, <X>_1) plus the
     MO's local W o <X>_0 + b reconstruct W o X + b; grad_X shares from
