@@ -954,10 +954,11 @@ __device__ __forceinline__ void ring_store(const RingParams& P, int a, int o, in
 // kernel values are the same for every thread of the CTA: one channel tile per
 // grid row, broadcast loads).  Channels past Co multiply a zero kernel value.
 // RING_OT = 8 channels (measured 11 % faster than 4 on a 16-channel layer) when
-// Co >= 8, else 4; 8 positions per thread measured slower.
+// Co >= 8, else 4; 8 positions per thread measured slower; capped at 128
+// registers (4 CTAs per SM, measured 6 % faster than 146 registers).
 #define RING_PT 4
 template <int RING_OT>
-__global__ void __launch_bounds__(128) k_ring_tile(RingParams P) {
+__global__ void __launch_bounds__(128, 4) k_ring_tile(RingParams P) {
   const long long npos = P.outs / P.kbound.x;   // B * Ho * Wo
   const long long pos0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * RING_PT;
   if (pos0 >= npos) return;
