@@ -376,6 +376,15 @@ int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* plan, const uint64_t* g, 
 int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner, int64_t outer_stride,
                    int64_t term_stride, const uint64_t* scalars, int32_t terms, const uint64_t* addend,
                    int32_t negate, uint64_t* out, int64_t count, void* stream);
+/* The same with two term indices (a double sum over m x m blocks in one pass,
+ * e.g. the shares sum_{i,j} l_j k_i <u'_i o v'_j> of Alg. 3's online phase):
+ *   out[e] = addend[e] + s * sum_{i2 < terms2} sum_{i < terms}
+ *            scalars[i2 * terms + i] * src[src_offset + (e / inner) * outer_stride
+ *            + (e % inner) + i * term_stride + i2 * term_stride2]  mod t,
+ * terms * terms2 <= 64 scalars.  Errors as pencil_lincomb (also terms2 < 1). */
+int pencil_lincomb2(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner, int64_t outer_stride,
+                    int64_t term_stride, int32_t terms, int64_t term_stride2, int32_t terms2, const uint64_t* scalars,
+                    const uint64_t* addend, int32_t negate, uint64_t* out, int64_t count, void* stream);
 
 /* In-place batched negacyclic NTT (inverse = 0) or INTT (inverse = 1) of
  * `count` polynomials laid out [count][L][N], canonical in and out (Sec. 5 "NTT"). */

@@ -1301,12 +1301,14 @@ extern "C" int pencil_ring_linear(PencilCtx* ctx, const PencilPlan* P, const uin
   return PENCIL_OK;
 }
 
-extern "C" int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner,
-                              int64_t outer_stride, int64_t term_stride, const uint64_t* scalars, int32_t terms,
-                              const uint64_t* addend, int32_t negate, uint64_t* out, int64_t count, void* stream) {
-  if (!ctx || !src || !out || count < 0 || inner < 1 || src_offset < 0 || outer_stride < 0 || term_stride < 0)
+static int lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner, int64_t outer_stride,
+                   int64_t term_stride, int32_t terms, int64_t term_stride2, int32_t terms2, const uint64_t* scalars,
+                   const uint64_t* addend, int32_t negate, uint64_t* out, int64_t count, void* stream) {
+  if (!ctx || !src || !out || count < 0 || inner < 1 || src_offset < 0 || outer_stride < 0 || term_stride < 0 ||
+      term_stride2 < 0)
     return PENCIL_E_ARG;
-  if (terms < 0 || terms > PENCIL_LINCOMB_MAX_TERMS || (terms > 0 && !scalars)) return PENCIL_E_ARG;
+  if (terms < 0 || terms2 < 1 || (long long)terms * terms2 > PENCIL_LINCOMB_MAX_TERMS || (terms > 0 && !scalars))
+    return PENCIL_E_ARG;
   DeviceGuard guard(ctx->device);
   LincombP P;
   memset(&P, 0, sizeof(P));
@@ -1315,17 +1317,34 @@ extern "C" int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_o
   P.inner = inner;
   P.outer = outer_stride;
   P.tstride = term_stride;
+  P.tstride2 = term_stride2;
   P.count = count;
   P.addend = addend;
   P.out = out;
   P.terms = terms;
+  P.terms2 = terms2;
   P.negate = negate ? 1 : 0;
-  for (int i = 0; i < terms; ++i) P.k[i] = scalars[i];
+  for (int i = 0; i < terms * terms2; ++i) P.k[i] = scalars[i];
   {
     PROF(ctx, PENCIL_K_LINCOMB, (cudaStream_t)stream);
     CUDA_TRY(launch_lincomb(P, ctx->dev.t_mask, (cudaStream_t)stream));
   }
   return PENCIL_OK;
+}
+
+extern "C" int pencil_lincomb(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner,
+                              int64_t outer_stride, int64_t term_stride, const uint64_t* scalars, int32_t terms,
+                              const uint64_t* addend, int32_t negate, uint64_t* out, int64_t count, void* stream) {
+  return lincomb(ctx, src, src_offset, inner, outer_stride, term_stride, terms, 0, 1, scalars, addend, negate, out,
+                 count, stream);
+}
+
+extern "C" int pencil_lincomb2(PencilCtx* ctx, const uint64_t* src, int64_t src_offset, int64_t inner,
+                               int64_t outer_stride, int64_t term_stride, int32_t terms, int64_t term_stride2,
+                               int32_t terms2, const uint64_t* scalars, const uint64_t* addend, int32_t negate,
+                               uint64_t* out, int64_t count, void* stream) {
+  return lincomb(ctx, src, src_offset, inner, outer_stride, term_stride, terms, term_stride2, terms2, scalars, addend,
+                 negate, out, count, stream);
 }
 
 extern "C" int pencil_bias_grad(PencilCtx* ctx, const PencilPlan* P, const uint64_t* g, uint64_t* out,

@@ -1112,14 +1112,18 @@ cudaError_t launch_bias_grad(const u64* g, int B, int Co, long long hw, u64 t_ma
 // ------------------------------------------------------------------ linear combinations of shares
 // Online phase of the preprocessing protocol (Alg. 3): masked operands and
 // shares are linear combinations over Z_t, t = 2^t_bits (u64 wrap-around is
-// exact mod t):  out[e] = addend[e] (+ or -) sum_i k_i src[off + (e / inner) outer
-// + e % inner + i tstride].
+// exact mod t):  out[e] = addend[e] (+ or -) sum_{i2, i} k[i2 terms + i]
+// src[off + (e / inner) outer + e % inner + i tstride + i2 tstride2].
 __global__ void k_lincomb(LincombP P, u64 t_mask) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < P.count; e += stride) {
     const long long base = P.off + (e / P.inner) * P.outer + e % P.inner;
     u64 acc = 0;
-    for (int i = 0; i < P.terms; ++i) acc += P.k[i] * __ldg(P.src + base + i * P.tstride);
+    for (int i2 = 0; i2 < P.terms2; ++i2) {
+      const u64* src = P.src + base + i2 * P.tstride2;
+      const u64* k = P.k + i2 * P.terms;
+      for (int i = 0; i < P.terms; ++i) acc += k[i] * __ldg(src + i * P.tstride);
+    }
     u64 v = P.addend ? __ldg(P.addend + e) : 0ull;
     v = P.negate ? v - acc : v + acc;
     P.out[e] = v & t_mask;

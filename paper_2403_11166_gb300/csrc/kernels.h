@@ -34,10 +34,11 @@ struct MacParams {
 struct LincombP {
   const u64* src;
   long long off, inner, outer, tstride, count;
+  long long tstride2;  // stride of the second term index (terms2 of them; 1: one-index form)
   const u64* addend;   // nullable
   u64* out;
-  int terms, negate;
-  u64 k[PENCIL_LINCOMB_MAX_TERMS];
+  int terms, terms2, negate;
+  u64 k[PENCIL_LINCOMB_MAX_TERMS];   // k[i2 * terms + i]
 };
 cudaError_t launch_lincomb(const LincombP& P, u64 t_mask, cudaStream_t s);
 

@@ -37,7 +37,7 @@ EXPORTS = ("pencil_ctx_create", "pencil_ctx_destroy", "pencil_ctx_primes", "penc
            "pencil_plan_candidates", "he_linear_forward_prepare", "he_linear_forward_apply", "pencil_plan_slice",
            "pencil_lincomb", "pencil_ctx_flooding", "pencil_pk_keygen", "pencil_pk_destroy",
            "encrypt_share_pk", "compact_returned", "decrypt_compact_to_share",
-           "pencil_batch_bind_wgrad")
+           "pencil_batch_bind_wgrad", "pencil_lincomb2")
 BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT, BATCH_CT_KERNEL = 0, 1, 2, 3
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
@@ -99,6 +99,7 @@ def _load():
         "pencil_plan_destroy": [P],
         "pencil_plan_slice": [P, I32, I32, ctypes.POINTER(P)],
         "pencil_lincomb": [P, P, I64, I64, I64, I64, P, I32, P, I32, P, I64, P],
+        "pencil_lincomb2": [P, P, I64, I64, I64, I64, I32, I64, I32, P, P, I32, P, I64, P],
         "pencil_ctx_flooding": [P, I32],
         "pencil_pk_keygen": [P, P, U64, ctypes.POINTER(P), P],
         "pencil_pk_destroy": [P],
@@ -385,6 +386,17 @@ def pencil_lincomb(ctx: Context, src, scalars, count: int, out, addend=None, neg
     _check(lib.pencil_lincomb(ctx.h, _ptr(src), src_offset, count if inner is None else inner, outer_stride,
                               term_stride, ks, len(scalars), _ptr(addend), int(negate), _ptr(out), count,
                               _stream(stream)), "pencil_lincomb")
+
+
+def pencil_lincomb2(ctx: Context, src, scalars, terms: int, terms2: int, count: int, out, addend=None,
+                    negate: bool = False, src_offset: int = 0, inner: int = None, outer_stride: int = 0,
+                    term_stride: int = 0, term_stride2: int = 0, stream=None):
+    """out[e] = addend[e] +/- sum_{i2, i} scalars[i2 * terms + i] src[src_offset + (e // inner) outer_stride
+    + e % inner + i term_stride + i2 term_stride2] mod t (see pencil_lincomb2 in the header)."""
+    ks = (ctypes.c_uint64 * max(1, len(scalars)))(*[int(v) for v in scalars])
+    _check(lib.pencil_lincomb2(ctx.h, _ptr(src), src_offset, count if inner is None else inner, outer_stride,
+                               term_stride, terms, term_stride2, terms2, ks, _ptr(addend), int(negate), _ptr(out),
+                               count, _stream(stream)), "pencil_lincomb2")
 
 
 def he_linear_backward(ctx: Context, plan_dgrad, plan_wgrad, ct_gy1_d, pt_wt, ct_x1_w, ct_gy1_w, gy0, x0,

@@ -162,20 +162,36 @@ class PrepProduct:
         self._comb(self.u_masks, k, self.n_u, ut, self.u_st, addend=u, negate=True, stream=stream)
         vt = torch.empty(self.n_v, dtype=torch.int64, device=dev)     # DO: v~ = v - sum_j l_j v'_j
         self._comb(self.v_masks, l, self.n_v, vt, self.v_st, addend=v, negate=True, stream=stream)
+        R = torch.empty(m * n_out, dtype=torch.int64, device=dev)
+        self._ring(self.ring_all, self.plan_all, ut, self.v_masks, R, stream=stream)               # DO: u~ o v'_j
+        z0 = torch.empty(n_out, dtype=torch.int64, device=dev)
+        z1 = torch.empty_like(z0)
+        self._ring(self.ring_one, self.plan_one, u, vt, z0, stream=stream)                          # MO: u o v~
+        if m * m <= 64:
+            # <u o v>_0 = u o v~ + sum_{i,j} l_j k_i S0[i, j]   (MO)
+            # <u o v>_1 = sum_j l_j (u~ o v'_j) + sum_{i,j} l_j k_i S1[i, j]   (DO)
+            # (the same sums as the per-j shares <u o v'_j> below, regrouped: one pass over each S)
+            tm = (1 << self.ctx.t_bits) - 1
+            lk = [(int(l[j]) * int(k[i])) & tm for j in range(m) for i in range(m)]
+            b0, b1, r0, r1 = self.blk(0), self.blk(1), self.ring_blk(0), self.ring_blk(1)
+            he.pencil_lincomb2(self.ctx, self.S0, lk, m, m, n_out, z0, addend=z0, src_offset=b0.off, inner=b0.inner,
+                               outer_stride=b0.outer, term_stride=b0.term, term_stride2=b1.off - b0.off,
+                               stream=stream)
+            he.pencil_lincomb(self.ctx, R, l, n_out, z1, src_offset=r0.off, inner=r0.inner, outer_stride=r0.outer,
+                              term_stride=r1.off - r0.off, stream=stream)
+            he.pencil_lincomb2(self.ctx, self.S1, lk, m, m, n_out, z1, addend=z1, src_offset=b0.off, inner=b0.inner,
+                               outer_stride=b0.outer, term_stride=b0.term, term_stride2=b1.off - b0.off,
+                               stream=stream)
+            return ut, vt, z0, z1
         # shares of u o v'_j for every j (j-major, each in the operator's output layout)
         A0 = torch.empty(m * n_out, dtype=torch.int64, device=dev)
         A1 = torch.empty_like(A0)
-        R = torch.empty(m * n_out, dtype=torch.int64, device=dev)
-        self._ring(self.ring_all, self.plan_all, ut, self.v_masks, R, stream=stream)               # DO: u~ o v'_j
         for j in range(m):
             a0, a1 = A0[j * n_out:(j + 1) * n_out], A1[j * n_out:(j + 1) * n_out]
             self._comb(self.S0, k, n_out, a0, self.blk(j), stream=stream)                          # MO
             self._comb(R, [1], n_out, a1, self.ring_blk(j), stream=stream)                          # DO
             self._comb(self.S1, k, n_out, a1, self.blk(j), addend=a1, stream=stream)
         # shares of u o v
-        z0 = torch.empty(n_out, dtype=torch.int64, device=dev)
-        z1 = torch.empty_like(z0)
-        self._ring(self.ring_one, self.plan_one, u, vt, z0, stream=stream)                          # MO: u o v~
         he.pencil_lincomb(self.ctx, A0, l, n_out, z0, addend=z0, term_stride=n_out, stream=stream)
         he.pencil_lincomb(self.ctx, A1, l, n_out, z1, term_stride=n_out, stream=stream)            # DO
         return ut, vt, z0, z1

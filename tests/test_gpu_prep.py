@@ -30,6 +30,7 @@ def _shapes(L, role):
     (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), WGRAD, 2),
     (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), oprep.WGRAD_REV, 2),
     (Layer("fc", B=3, Ci=10, Co=4), WGRAD, 3),
+    (Layer("fc", B=3, Ci=10, Co=4), FWD, 9),       # m^2 > 64: the online phase's per-j form
 ])
 def test_prep_protocol_matches_oracle(L, role, m):
     from paper_2403_11166_gb300 import he, prep
@@ -104,6 +105,36 @@ def test_lincomb_matches_definition(count, inner, outer, tstride, off, terms, ne
         a = int(add[e]) if add is not None else 0
         want.append(((a - acc) if negate else (a + acc)) % (1 << 41))
     assert (to_np(out) == np.array(want, dtype=np.uint64)).all()
+
+
+@pytest.mark.parametrize("count,inner,outer,t1,n1,t2,n2,off", [
+    (3000, 3000, 0, 3000, 8, 24000, 8, 0),          # m x m contiguous blocks (64 scalars)
+    (517, 40, 120, 40, 3, 9000, 5, 7),              # strided rows, partial last row
+    (100, 100, 0, 1, 1, 100, 1, 0),                 # one term
+])
+def test_lincomb2_matches_definition(count, inner, outer, t1, n1, t2, n2, off):
+    from paper_2403_11166_gb300 import he
+    ctx = he.Context(12, 2, 54)
+    g = np.random.default_rng(count + n1 * n2)
+    rows = -(-count // inner)
+    need = off + (rows - 1) * outer + inner + (n1 - 1) * t1 + (n2 - 1) * t2
+    src = g.integers(0, 1 << 41, need, dtype=np.uint64)
+    k = [int(x) for x in g.integers(0, 1 << 41, n1 * n2, dtype=np.uint64)]
+    add = g.integers(0, 1 << 41, count, dtype=np.uint64)
+    out = torch.full((count,), -1, dtype=torch.int64, device="cuda")
+    he.pencil_lincomb2(ctx, to_dev(src), k, n1, n2, count, out, addend=to_dev(add), src_offset=off, inner=inner,
+                       outer_stride=outer, term_stride=t1, term_stride2=t2)
+    torch.cuda.synchronize()
+    want = []
+    for e in range(count):
+        base = off + (e // inner) * outer + e % inner
+        acc = sum(k[i2 * n1 + i] * int(src[base + i * t1 + i2 * t2]) for i2 in range(n2) for i in range(n1))
+        want.append((int(add[e]) + acc) % (1 << 41))
+    assert (to_np(out) == np.array(want, dtype=np.uint64)).all()
+    with pytest.raises(he.PencilError):
+        he.pencil_lincomb2(ctx, to_dev(src), [1] * 65, 65, 1, count, out)
+    with pytest.raises(he.PencilError):
+        he.pencil_lincomb2(ctx, to_dev(src), [1] * 8, 8, 0, count, out)
 
 
 def test_alg4_linear_layer_with_preprocessing():
