@@ -500,8 +500,16 @@ def training_step(he, device: int, reps: int = 3):
         b.record()
         b.synchronize()
         t.append(a.elapsed_time(b))
-    return {"ms_per_step": statistics.median(t), "batch": 64,
-            "ciphertext_MB_per_step": round((sess.bytes_do_to_mo + sess.bytes_mo_to_do) / reps / 1e6, 1)}
+    out = {"ms_per_step": statistics.median(t), "batch": 64,
+           "ciphertext_MB_per_step": round((sess.bytes_do_to_mo + sess.bytes_mo_to_do) / reps / 1e6, 1)}
+    # one more step with the library's per-kernel events (the HE and ring kernels; the rest is PyTorch)
+    sess.ctx.profile(True)
+    step()
+    torch.cuda.synchronize()
+    sess.ctx.profile(False)
+    out["library_kernels"] = {name: {"launches": n, "ms": round(ms, 4)}
+                              for name, (n, ms) in sess.ctx.profile_read().items() if n}
+    return out
 
 
 def large_conv(he, device: int, reps: int = 3):

@@ -1062,11 +1062,79 @@ __global__ void __launch_bounds__(256) k_ring_block(RingParams P) {
   }
 }
 
+// Long reductions with a short output (grad_W's HO x WO kernel offsets, at
+// most 5 x 5): one CTA per (a, o) keeps all HO * WO outputs in registers, so
+// each kernel value (grad_Y) is loaded once for all of them and the input rows
+// around it come from L1; (u, v) advance by the block size without a division.
+template <int HO, int WO>
+__global__ void __launch_bounds__(256) k_ring_wgrad(RingParams P) {
+  const int Co = P.kbound.x, Ci = P.kbound.y, KH = P.kbound.z, KW = P.kbound.w;
+  const int o = (int)(blockIdx.x % (unsigned)Co);
+  const int a = (int)(blockIdx.x / (unsigned)Co);
+  const int UV = KH * KW;
+  u64 acc[HO * WO];
+#pragma unroll
+  for (int t = 0; t < HO * WO; ++t) acc[t] = 0;
+  const u64* vb = P.v.ptr + P.v.base + a * P.v.s0;
+  const u64* wb = P.w.ptr + P.w.base + (i64)o * P.w.s0;
+  const int su = (int)blockDim.x / KW, sv = (int)blockDim.x - su * KW;
+  const int u0 = (int)threadIdx.x / KW, v0 = (int)threadIdx.x - u0 * KW;
+  for (int c = 0; c < Ci; ++c) {
+    const u64* vc = vb + c * P.v.s1;
+    const u64* wc = wb + c * P.w.s1;
+    int u = u0, v = v0;
+    for (int q = threadIdx.x; q < UV; q += blockDim.x) {
+      const u64 g = __ldg(wc + u * P.w.s2 + v * P.w.s3);
+#pragma unroll
+      for (int i = 0; i < HO; ++i) {
+        const int rr = i + u - P.v.pr;
+        if ((unsigned)rr >= (unsigned)P.v.hr) continue;
+        const u64* row = vc + rr * P.v.s2;
+#pragma unroll
+        for (int j = 0; j < WO; ++j) {
+          const int ss = j + v - P.v.ps;
+          if ((unsigned)ss < (unsigned)P.v.wr) acc[i * WO + j] += g * __ldg(row + ss * P.v.s3);
+        }
+      }
+      u += su;
+      v += sv;
+      if (v >= KW) {
+        v -= KW;
+        ++u;
+      }
+    }
+  }
+  __shared__ u64 part[8][HO * WO];   // 256 threads = 8 warps
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < HO * WO; ++t) {
+    u64 x = acc[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) part[warp][t] = x;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < HO * WO) {
+    u64 sum = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += part[w][threadIdx.x];
+    ring_store(P, a, o, (int)threadIdx.x / WO, (int)threadIdx.x % WO, sum);
+  }
+}
+
 cudaError_t launch_ring(const RingParams& P, cudaStream_t s) {
   const long long R = (long long)P.kbound.y * P.kbound.z * P.kbound.w;
   if (P.outs == 0) return cudaSuccess;
   if ((long long)P.kbound.z * P.kbound.w >= 256 && P.outs <= (1ll << 31) - 1) {
-    k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P);
+    const long long pairs = P.outs / ((long long)P.Ho * P.Wo);   // (a, o) pairs
+    if (P.Ho == 3 && P.Wo == 3)
+      k_ring_wgrad<3, 3><<<(unsigned)pairs, 256, 0, s>>>(P);
+    else if (P.Ho == 5 && P.Wo == 5)
+      k_ring_wgrad<5, 5><<<(unsigned)pairs, 256, 0, s>>>(P);
+    else if (P.Ho == 1 && P.Wo == 1)
+      k_ring_wgrad<1, 1><<<(unsigned)pairs, 256, 0, s>>>(P);
+    else
+      k_ring_block<<<(unsigned)P.outs, 256, 0, s>>>(P);
   } else {
     const long long positions = P.outs / P.kbound.x;
     const unsigned gx = (unsigned)((positions + 128 * RING_PT - 1) / (128 * RING_PT));
