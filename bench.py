@@ -1113,7 +1113,7 @@ def run_ours(args):
     }
     if not args.no_extras and world == 1:
         line["workloads"] = extras(he, local)
-    if not args.no_sweep:
+    if not args.no_sweep and world == 1:   # (a multi-GPU run keeps to the timed layer step)
         line["ntt_sweep"] = ntt_sweep(he, local, args.sweep_polys, args.sweep_points, args.sweep_reps,
                                       args.ntt_log_radix)
     if world == 1 and not args.no_cpu_baseline:
