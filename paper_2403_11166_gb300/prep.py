@@ -22,7 +22,7 @@ All tensors are int64 storage of Z_t values in the user's layouts.
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Optional, Sequence, Tuple
+from typing import Callable, Optional, Sequence, Tuple
 
 import torch
 
@@ -44,55 +44,74 @@ def _layer(kind, B, Ci, Co, H, W, s, pad) -> he.Layer:
     return he.Layer(kind, B, Ci, Co, H, W, s, pad)
 
 
+@dataclass
+class Layout:
+    """Where Alg. 3's operands and shares live for one operator: the stacked
+    layer of the m^2 preprocessing products, the operand / mask / share sizes,
+    and strided descriptors (mask i of u at u_st + i * u_st.term; share block
+    (i, j) of the stacked output at blk(j) + i * blk(j).term, blk(j).off linear
+    in j; ring block j at ring_blk(j))."""
+    stacked: he.Layer
+    he_role: int
+    n_u: int
+    n_v: int
+    n_out: int
+    u_st: Strided
+    v_st: Strided
+    blk: Callable[[int], Strided]
+    ring_all: tuple
+    ring_blk: Callable[[int], Strided]
+    ring_one: tuple
+
+
+def layout(layer: he.Layer, role: int, m: int) -> Layout:
+    Lr = layer
+    kind, B, Ci, Co, H, W, s, pad = Lr.kind, Lr.batch, Lr.c_in, Lr.c_out, Lr.height, Lr.width, Lr.kernel, Lr.pad
+    conv = kind == he.CONV
+    Ho, Wo = (H + 2 * pad - s + 1, W + 2 * pad - s + 1) if conv else (1, 1)
+    HW, HoWo, ss = (H * W, Ho * Wo, s * s) if conv else (1, 1, 1)
+    if role == he.ROLE_FWD:
+        n_u, n_v, n_out = Co * Ci * ss, B * Ci * HW, B * Co * HoWo
+        return Layout(_layer(kind, m * B, Ci, m * Co, H, W, s, pad), he.ROLE_FWD, n_u, n_v, n_out,
+                      Strided(0, n_u, 0, n_u), Strided(0, n_v, 0, n_v),
+                      lambda j: Strided(j * B * m * Co * HoWo, Co * HoWo, m * Co * HoWo, Co * HoWo),
+                      (_layer(kind, m * B, Ci, Co, H, W, s, pad), he.ROLE_FWD, "uv"),
+                      lambda j: Strided(j * n_out, n_out, 0, 0), (Lr, he.ROLE_FWD, "uv"))
+    if role == he.ROLE_DGRAD:
+        n_u, n_v, n_out = Co * Ci * ss, B * Co * HoWo, B * Ci * HW
+        return Layout(_layer(kind, m * B, m * Ci, Co, H, W, s, pad), he.ROLE_DGRAD, n_u, n_v, n_out,
+                      Strided(0, Ci * ss, m * Ci * ss, Ci * ss), Strided(0, n_v, 0, n_v),
+                      lambda j: Strided(j * B * m * Ci * HW, Ci * HW, m * Ci * HW, Ci * HW),
+                      (_layer(kind, m * B, Ci, Co, H, W, s, pad), he.ROLE_DGRAD, "uv"),
+                      lambda j: Strided(j * n_out, n_out, 0, 0), (Lr, he.ROLE_DGRAD, "uv"))
+    if role == he.ROLE_WGRAD:
+        n_u, n_v, n_out = B * Co * HoWo, B * Ci * HW, Co * Ci * ss
+        return Layout(_layer(kind, B, m * Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD, n_u, n_v, n_out,
+                      Strided(0, Co * HoWo, m * Co * HoWo, Co * HoWo), Strided(0, Ci * HW, m * Ci * HW, Ci * HW),
+                      lambda j: Strided(j * Ci * ss, Ci * ss, m * Ci * ss, Co * m * Ci * ss),
+                      (_layer(kind, B, m * Ci, Co, H, W, s, pad), he.ROLE_WGRAD, "uv"),
+                      lambda j: Strided(j * Ci * ss, Ci * ss, m * Ci * ss, 0), (Lr, he.ROLE_WGRAD, "uv"))
+    if role == WGRAD_REV:
+        n_u, n_v, n_out = B * Ci * HW, B * Co * HoWo, Co * Ci * ss
+        return Layout(_layer(kind, B, m * Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD, n_u, n_v, n_out,
+                      Strided(0, Ci * HW, m * Ci * HW, Ci * HW), Strided(0, Co * HoWo, m * Co * HoWo, Co * HoWo),
+                      lambda j: Strided(j * Co * m * Ci * ss, Ci * ss, m * Ci * ss, Ci * ss),
+                      (_layer(kind, B, Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD, "vu"),
+                      lambda j: Strided(j * n_out, n_out, 0, 0), (Lr, he.ROLE_WGRAD, "vu"))
+    raise ValueError(role)
+
+
 class PrepProduct:
     """Alg. 3 for one operator of `layer` with m masks per party."""
 
     def __init__(self, ctx: he.Context, sk: he.SecretKey, layer: he.Layer, role: int, m: int,
                  part: Optional[tuple] = None):
         self.ctx, self.sk, self.layer, self.role, self.m = ctx, sk, layer, role, m
-        Lr = layer
-        kind, B, Ci, Co, H, W, s, pad = Lr.kind, Lr.batch, Lr.c_in, Lr.c_out, Lr.height, Lr.width, Lr.kernel, Lr.pad
-        conv = kind == he.CONV
-        Ho, Wo = (H + 2 * pad - s + 1, W + 2 * pad - s + 1) if conv else (1, 1)
-        HW, HoWo, ss = (H * W, Ho * Wo, s * s) if conv else (1, 1, 1)
-        if role == he.ROLE_FWD:
-            self.stacked, self.he_role = _layer(kind, m * B, Ci, m * Co, H, W, s, pad), he.ROLE_FWD
-            self.n_u, self.n_v, self.n_out = Co * Ci * ss, B * Ci * HW, B * Co * HoWo
-            self.u_st = Strided(0, self.n_u, 0, self.n_u)
-            self.v_st = Strided(0, self.n_v, 0, self.n_v)
-            self.blk = lambda j: Strided(j * B * m * Co * HoWo, Co * HoWo, m * Co * HoWo, Co * HoWo)
-            self.ring_all = (_layer(kind, m * B, Ci, Co, H, W, s, pad), he.ROLE_FWD, "uv")
-            self.ring_blk = lambda j: Strided(j * self.n_out, self.n_out, 0, 0)
-            self.ring_one = (Lr, he.ROLE_FWD, "uv")
-        elif role == he.ROLE_DGRAD:
-            self.stacked, self.he_role = _layer(kind, m * B, m * Ci, Co, H, W, s, pad), he.ROLE_DGRAD
-            self.n_u, self.n_v, self.n_out = Co * Ci * ss, B * Co * HoWo, B * Ci * HW
-            self.u_st = Strided(0, Ci * ss, m * Ci * ss, Ci * ss)
-            self.v_st = Strided(0, self.n_v, 0, self.n_v)
-            self.blk = lambda j: Strided(j * B * m * Ci * HW, Ci * HW, m * Ci * HW, Ci * HW)
-            self.ring_all = (_layer(kind, m * B, Ci, Co, H, W, s, pad), he.ROLE_DGRAD, "uv")
-            self.ring_blk = lambda j: Strided(j * self.n_out, self.n_out, 0, 0)
-            self.ring_one = (Lr, he.ROLE_DGRAD, "uv")
-        elif role == he.ROLE_WGRAD:
-            self.stacked, self.he_role = _layer(kind, B, m * Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD
-            self.n_u, self.n_v, self.n_out = B * Co * HoWo, B * Ci * HW, Co * Ci * ss
-            self.u_st = Strided(0, Co * HoWo, m * Co * HoWo, Co * HoWo)
-            self.v_st = Strided(0, Ci * HW, m * Ci * HW, Ci * HW)
-            self.blk = lambda j: Strided(j * Ci * ss, Ci * ss, m * Ci * ss, Co * m * Ci * ss)
-            self.ring_all = (_layer(kind, B, m * Ci, Co, H, W, s, pad), he.ROLE_WGRAD, "uv")
-            self.ring_blk = lambda j: Strided(j * Ci * ss, Ci * ss, m * Ci * ss, 0)
-            self.ring_one = (Lr, he.ROLE_WGRAD, "uv")
-        elif role == WGRAD_REV:
-            self.stacked, self.he_role = _layer(kind, B, m * Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD
-            self.n_u, self.n_v, self.n_out = B * Ci * HW, B * Co * HoWo, Co * Ci * ss
-            self.u_st = Strided(0, Ci * HW, m * Ci * HW, Ci * HW)
-            self.v_st = Strided(0, Co * HoWo, m * Co * HoWo, Co * HoWo)
-            self.blk = lambda j: Strided(j * Co * m * Ci * ss, Ci * ss, m * Ci * ss, Ci * ss)
-            self.ring_all = (_layer(kind, B, Ci, m * Co, H, W, s, pad), he.ROLE_WGRAD, "vu")
-            self.ring_blk = lambda j: Strided(j * self.n_out, self.n_out, 0, 0)
-            self.ring_one = (Lr, he.ROLE_WGRAD, "vu")
-        else:
-            raise ValueError(role)
+        lay = layout(layer, role, m)
+        self.stacked, self.he_role = lay.stacked, lay.he_role
+        self.n_u, self.n_v, self.n_out = lay.n_u, lay.n_v, lay.n_out
+        self.u_st, self.v_st, self.blk = lay.u_st, lay.v_st, lay.blk
+        self.ring_all, self.ring_blk, self.ring_one = lay.ring_all, lay.ring_blk, lay.ring_one
         self.plan_s = he.Plan(ctx, self.stacked, self.he_role, part)
         self.plan_all = he.Plan(ctx, self.ring_all[0], self.ring_all[1], None)
         self.plan_one = he.Plan(ctx, self.ring_one[0], self.ring_one[1], None)
