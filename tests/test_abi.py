@@ -61,3 +61,13 @@ def test_binding_status_checks_are_well_formed():
     src = open(os.path.join(ROOT, "paper_2403_11166_gb300", "he.py")).read()
     calls = [n for n in ast.walk(ast.parse(src)) if isinstance(n, ast.Call) and getattr(n.func, "id", None) == "_check"]
     assert calls and all(len(c.args) == 2 and isinstance(c.args[1], ast.Constant) for c in calls)
+
+
+def test_profiler_ids_match_binding_names():
+    """PENCIL_K_* of the header, in order, are the binding's KERNEL_NAMES."""
+    text = open(HEADER).read()
+    body = re.search(r"PENCIL_K_NTT_RAW = 0,(.*?)PENCIL_K_COUNT", text, flags=re.S).group(1)
+    ids = ["PENCIL_K_NTT_RAW"] + [x.strip() for x in body.split(",") if x.strip()]
+    src = open(os.path.join(ROOT, "paper_2403_11166_gb300", "he.py")).read()
+    names = re.findall(r'"(\w+)"', re.search(r"KERNEL_NAMES = \((.*?)\)", src, flags=re.S).group(1))
+    assert [i[len("PENCIL_K_"):].lower() for i in ids] == names
