@@ -89,8 +89,19 @@ int pencil_ctx_primes(const PencilCtx* ctx, uint64_t* primes, uint64_t* psis);
  * PENCIL_TUNE_MAC_STAGING (columns 2, 4, 8): 0 = every thread copies its own
  * operand words a few input blocks ahead (cp.async ring); 1 = one producer
  * warp per CTA copies whole 1 KB operand rows with bulk asynchronous copies
- * (cp.async.bulk + mbarrier), the other warps only multiply. */
-enum { PENCIL_TUNE_NTT_LOG_RADIX = 0, PENCIL_TUNE_MAC_COLUMNS = 1, PENCIL_TUNE_MAC_STAGING = 2 };
+ * (cp.async.bulk + mbarrier), the other warps only multiply.
+ * PENCIL_TUNE_NTT_ARITH: butterfly arithmetic of the NTT kernels: 0 = Shoup
+ * products with Harvey's lazy butterflies (any prime); 1 = pseudo-Mersenne
+ * products (y w = y0 w + y1 (2^32 w mod q), folded with 2^60 = c and
+ * 2^64 = 16 c mod q) with lazily growing values, for contexts whose primes are
+ * all q = 2^60 - c with c < 2^24 (every 60-bit parameter set; the default
+ * there), PENCIL_E_PARAMS otherwise. */
+enum {
+  PENCIL_TUNE_NTT_LOG_RADIX = 0,
+  PENCIL_TUNE_MAC_COLUMNS = 1,
+  PENCIL_TUNE_MAC_STAGING = 2,
+  PENCIL_TUNE_NTT_ARITH = 3
+};
 
 /* Noise flooding of the ciphertexts the MO returns (circuit privacy; the paper
  * is silent, no counterpart): with bits > 0, every later he_linear_forward(_prepare)

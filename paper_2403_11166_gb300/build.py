@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpencil_he.so")
-SOURCES = ["ntt12.cu", "ntt13.cu", "ntt14.cu", "kernels.cu", "capi.cu"]
+SOURCES = ["ntt13f.cu", "ntt14f.cu", "ntt12f.cu", "ntt13.cu", "ntt14.cu", "ntt12.cu", "kernels.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

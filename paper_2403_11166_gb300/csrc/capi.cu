@@ -157,6 +157,8 @@ struct PencilCtx {
   DevCtx dev;
   ulonglong2* tw_fwd = nullptr;
   ulonglong2* tw_inv = nullptr;
+  ulonglong2* tw_fwd_f = nullptr;   // fold tables (w, w 2^32 mod q), when every prime allows them
+  ulonglong2* tw_inv_f = nullptr;
   int* status = nullptr;
 };
 
@@ -298,6 +300,10 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   d.t_bits = p.t_bits;
   d.t_mask = (1ull << p.t_bits) - 1;
   std::vector<ulonglong2> tf((size_t)d.L * n), ti((size_t)d.L * n);
+  // pseudo-Mersenne fold butterflies need q_j = 2^60 - c with c < 2^24 for every limb
+  bool fold_ok = true;
+  for (u64 q : qs) fold_ok = fold_ok && q < (1ull << 60) && q > (1ull << 60) - (1ull << 24);
+  std::vector<ulonglong2> tff(fold_ok ? (size_t)d.L * n : 0), tif(fold_ok ? (size_t)d.L * n : 0);
   for (int j = 0; j < d.L; ++j) {
     const u64 q = qs[j];
     const u64 psi = min_root_2n(q, 2ull * n);
@@ -308,6 +314,10 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
       const u64 w = powmod(psi, r, q), wi = powmod(psi_inv, r, q);
       tf[(size_t)j * n + k] = make_ulonglong2(w, shoup(w, q));
       ti[(size_t)j * n + k] = make_ulonglong2(wi, shoup(wi, q));
+      if (fold_ok) {
+        tff[(size_t)j * n + k] = make_ulonglong2(w, (u64)((((u128)w) << 32) % q));
+        tif[(size_t)j * n + k] = make_ulonglong2(wi, (u64)((((u128)wi) << 32) % q));
+      }
     }
     LimbConst& lc = d.limb[j];
     lc.q = q;
@@ -344,18 +354,27 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   cudaError_t e1 = cudaMalloc(&ctx->tw_fwd, tf.size() * sizeof(ulonglong2));
   cudaError_t e2 = cudaMalloc(&ctx->tw_inv, ti.size() * sizeof(ulonglong2));
   cudaError_t e3 = cudaMalloc(&ctx->status, sizeof(int));
-  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+  cudaError_t e4 = fold_ok ? cudaMalloc(&ctx->tw_fwd_f, tff.size() * sizeof(ulonglong2)) : cudaSuccess;
+  cudaError_t e5 = fold_ok ? cudaMalloc(&ctx->tw_inv_f, tif.size() * sizeof(ulonglong2)) : cudaSuccess;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
     pencil_ctx_destroy(ctx);
     return PENCIL_E_CUDA;
   }
   if (cudaMemcpy(ctx->tw_fwd, tf.data(), tf.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_inv, ti.data(), ti.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (fold_ok && cudaMemcpy(ctx->tw_fwd_f, tff.data(), tff.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) !=
+                      cudaSuccess) ||
+      (fold_ok && cudaMemcpy(ctx->tw_inv_f, tif.data(), tif.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice) !=
+                      cudaSuccess) ||
       cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess || upload_cdt() != cudaSuccess) {
     pencil_ctx_destroy(ctx);
     return PENCIL_E_CUDA;
   }
   d.tw_fwd = ctx->tw_fwd;
   d.tw_inv = ctx->tw_inv;
+  d.tw_fwd_f = ctx->tw_fwd_f;
+  d.tw_inv_f = ctx->tw_inv_f;
+  d.ntt_arith = fold_ok ? 1 : 0;
   d.status = ctx->status;
   *out = ctx;
   return PENCIL_OK;
@@ -371,6 +390,8 @@ extern "C" int pencil_ctx_destroy(PencilCtx* ctx) {
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   cudaFree(ctx->tw_fwd);
   cudaFree(ctx->tw_inv);
+  cudaFree(ctx->tw_fwd_f);
+  cudaFree(ctx->tw_inv_f);
   cudaFree(ctx->status);
   delete ctx;
   return PENCIL_OK;
@@ -402,6 +423,12 @@ extern "C" int pencil_ctx_tune(PencilCtx* ctx, int32_t knob, int32_t value) {
     ctx->dev.mac_staging = value;
     return PENCIL_OK;
   }
+  if (knob == PENCIL_TUNE_NTT_ARITH) {
+    if (value != 0 && value != 1) return PENCIL_E_ARG;
+    if (value == 1 && !ctx->tw_fwd_f) return PENCIL_E_PARAMS;   // some prime is not 2^60 - c, c < 2^24
+    ctx->dev.ntt_arith = value;
+    return PENCIL_OK;
+  }
   return PENCIL_E_ARG;
 }
 
@@ -424,6 +451,10 @@ extern "C" int pencil_ctx_get_tune(const PencilCtx* ctx, int32_t knob, int32_t* 
   }
   if (knob == PENCIL_TUNE_MAC_COLUMNS) {
     *value = ctx->dev.mac_nt;
+    return PENCIL_OK;
+  }
+  if (knob == PENCIL_TUNE_NTT_ARITH) {
+    *value = ctx->dev.ntt_arith;
     return PENCIL_OK;
   }
   if (knob == PENCIL_TUNE_MAC_STAGING) {

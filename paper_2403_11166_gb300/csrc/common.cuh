@@ -35,6 +35,9 @@ struct DevCtx {
   LimbConst limb[PENCIL_MAX_LIMBS];
   const ulonglong2* tw_fwd;  // [L][N] (psi^brv(k), Shoup companion)
   const ulonglong2* tw_inv;  // [L][N] (psi^-brv(k), Shoup companion)
+  int ntt_arith;             // butterflies of the NTT kernels: 0 Shoup / Harvey, 1 pseudo-Mersenne folds
+  const ulonglong2* tw_fwd_f;  // [L][N] (psi^brv(k), psi^brv(k) 2^32 mod q)   (null unless every
+  const ulonglong2* tw_inv_f;  // [L][N] (psi^-brv(k), psi^-brv(k) 2^32 mod q)  q_j = 2^60 - c, c < 2^24)
   int* status;               // device status word (atomicOr of error bits)
   int mac_split;             // 1: every q_j < 2^60 with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
   int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
@@ -181,6 +184,51 @@ __device__ __forceinline__ void gs_butterfly(u64& x, u64& y, u64 w, u64 ws, u64 
   u64 d = x - y + q2;
   x = s;
   y = mul_shoup_lazy(d, w, ws, q);
+}
+
+// ------------------------------------------------------------------ pseudo-Mersenne twiddle products
+// For q = 2^60 - c with c < 2^24 (every prime of the 60-bit parameter sets):
+// 2^60 = c60 = c and 2^64 = c64 = 16 c (mod q).  Beside each twiddle w the table
+// holds w32 = w 2^32 mod q, so that for y = y1 2^32 + y0 (any y < 2^64)
+//   y w = y0 w + y1 w32 (mod q),
+// a sum S < 2^93 of four 32x32->64 partial products (no quotient estimate).  With
+// S = sh 2^64 + sm 2^60 + sl (sh <= 2^29 + 1, sm < 16, sl < 2^60) the folds
+//   S = sl + sm c60 + sh c64 (mod q) < 2^60 + 2^57 + 2^30 < 1.13 q
+// leave a lazy residue; the products are six 32x32->64 multiply-adds and a few
+// 32-bit ALU operations, against eight such products and four 32-bit
+// multiply-adds for a Shoup product.
+__device__ __forceinline__ u64 mul_fold(u64 y, u64 w, u64 w32, u32 c60, u32 c64) {
+  const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
+  // S = y0 wl + y1 w32l + 2^32 (y0 wh + y1 w32h)   (l, h: low and high 32-bit halves)
+  const u64 p1 = (u64)y1 * (u32)w32;                           // y1 w32l
+  const u64 p0 = (u64)y0 * (u32)w + (u32)p1;                   // y0 wl + lo(p1) < 2^64 - 2^32
+  u64 m = (u64)y1 * (u32)(w32 >> 32) + (p1 >> 32);             // < 2^60 + 2^32
+  m = (u64)y0 * (u32)(w >> 32) + m;                            // < 2^61 + 2^32
+  m += p0 >> 32;                                               // S = m 2^32 + lo(p0), m < 2^61 + 2^33
+  const u32 ml = (u32)m;
+  const u64 t = (u64)(ml >> 28) * c60 + (((u64)(ml & 0x0FFFFFFFu) << 32) | (u32)p0);   // sl + sm c60
+  return (u64)(u32)(m >> 32) * c64 + t;                                                 // + sh c64
+}
+
+// v mod q, lazily: any v < 2^64 -> (v mod 2^60) + (v >> 60) c60 < 2^60 + 2^28 (< 2 q).
+__device__ __forceinline__ u64 fold60(u64 v, u32 c60) {
+  return (u64)(u32)(v >> 60) * c60 + (v & 0x0FFFFFFFFFFFFFFFull);
+}
+
+// Cooley-Tukey butterfly with a lazy pseudo-Mersenne product: x, y < B q ->
+// x + w y < (B + 1.13) q, x - w y + 2 q < (B + 2) q (no correction step).
+__device__ __forceinline__ void ct_fold(u64& x, u64& y, const ulonglong2 w, u32 c60, u32 c64, u64 q2) {
+  const u64 t = mul_fold(y, w.x, w.y, c60, c64);
+  y = x + q2 - t;
+  x = x + t;
+}
+
+// Gentleman-Sande butterfly: x, y < B q <= cq, cq + B q < 2^64 ->
+// x + y < 2 B q, (x - y + cq) w < 1.13 q.
+__device__ __forceinline__ void gs_fold(u64& x, u64& y, const ulonglong2 w, u32 c60, u32 c64, u64 cq) {
+  const u64 d = x + cq - y;
+  x = x + y;
+  y = mul_fold(d, w.x, w.y, c60, c64);
 }
 
 // [0, 8q) -> [0, q)

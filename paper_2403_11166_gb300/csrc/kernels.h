@@ -133,47 +133,55 @@ cudaError_t batch_mac_blocks(const DevCtx& ctx, int nt, int has_dual, int* block
 cudaError_t launch_mul_probe(int which, long long iters, int blocks, int threads, u64 seed, u64* sink,
                              cudaStream_t s);
 
-PENCIL_NTT_INSTANTIATE(extern, 12)
-PENCIL_NTT_INSTANTIATE(extern, 13)
-PENCIL_NTT_INSTANTIATE(extern, 14)
+PENCIL_NTT_INSTANTIATE(extern, 12, false)
+PENCIL_NTT_INSTANTIATE(extern, 13, false)
+PENCIL_NTT_INSTANTIATE(extern, 14, false)
+PENCIL_NTT_INSTANTIATE(extern, 12, true)
+PENCIL_NTT_INSTANTIATE(extern, 13, true)
+PENCIL_NTT_INSTANTIATE(extern, 14, true)
 
-// Dispatch on log2(N) and the context's radix (log2 of coefficients per thread).
+// Dispatch on log2(N), the context's radix (log2 of coefficients per thread) and
+// its butterfly arithmetic (Shoup / Harvey, or pseudo-Mersenne folds).
 template <class Mode, bool INV>
 cudaError_t ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const int2* items, long long count,
                       const u64* step, cudaStream_t s) {
+#define PENCIL_NTT_MULTI_CASE(LOGN)                                                                          \
+  case LOGN:                                                                                                 \
+    if (ctx.ntt_arith)                                                                                       \
+      return r4 ? launch_ntt_multi<LOGN, 4, Mode, INV, true>(ctx, Ps, items, count, step, s)                 \
+                : launch_ntt_multi<LOGN, 5, Mode, INV, true>(ctx, Ps, items, count, step, s);                \
+    return r4 ? launch_ntt_multi<LOGN, 4, Mode, INV, false>(ctx, Ps, items, count, step, s)                  \
+              : launch_ntt_multi<LOGN, 5, Mode, INV, false>(ctx, Ps, items, count, step, s);
   const bool r4 = ctx.ntt_loge == 4;
   switch (ctx.log_n) {
-    case 12:
-      return r4 ? launch_ntt_multi<12, 4, Mode, INV>(ctx, Ps, items, count, step, s)
-                : launch_ntt_multi<12, 5, Mode, INV>(ctx, Ps, items, count, step, s);
-    case 13:
-      return r4 ? launch_ntt_multi<13, 4, Mode, INV>(ctx, Ps, items, count, step, s)
-                : launch_ntt_multi<13, 5, Mode, INV>(ctx, Ps, items, count, step, s);
-    case 14:
-      return r4 ? launch_ntt_multi<14, 4, Mode, INV>(ctx, Ps, items, count, step, s)
-                : launch_ntt_multi<14, 5, Mode, INV>(ctx, Ps, items, count, step, s);
+    PENCIL_NTT_MULTI_CASE(12)
+    PENCIL_NTT_MULTI_CASE(13)
+    PENCIL_NTT_MULTI_CASE(14)
     default:
       return cudaErrorInvalidValue;
   }
+#undef PENCIL_NTT_MULTI_CASE
 }
 
 // Transforms polynomials [first, first + count) of the mode's arrays.
 template <class Mode, bool INV>
 cudaError_t ntt(const DevCtx& ctx, const typename Mode::Params& P, int count, cudaStream_t s, int first = 0) {
+#define PENCIL_NTT_CASE(LOGN)                                                                                \
+  case LOGN:                                                                                                 \
+    if (ctx.ntt_arith)                                                                                       \
+      return r4 ? launch_ntt<LOGN, 4, Mode, INV, true>(ctx, P, first, count, s)                              \
+                : launch_ntt<LOGN, 5, Mode, INV, true>(ctx, P, first, count, s);                             \
+    return r4 ? launch_ntt<LOGN, 4, Mode, INV, false>(ctx, P, first, count, s)                               \
+              : launch_ntt<LOGN, 5, Mode, INV, false>(ctx, P, first, count, s);
   const bool r4 = ctx.ntt_loge == 4;
   switch (ctx.log_n) {
-    case 12:
-      return r4 ? launch_ntt<12, 4, Mode, INV>(ctx, P, first, count, s)
-                : launch_ntt<12, 5, Mode, INV>(ctx, P, first, count, s);
-    case 13:
-      return r4 ? launch_ntt<13, 4, Mode, INV>(ctx, P, first, count, s)
-                : launch_ntt<13, 5, Mode, INV>(ctx, P, first, count, s);
-    case 14:
-      return r4 ? launch_ntt<14, 4, Mode, INV>(ctx, P, first, count, s)
-                : launch_ntt<14, 5, Mode, INV>(ctx, P, first, count, s);
+    PENCIL_NTT_CASE(12)
+    PENCIL_NTT_CASE(13)
+    PENCIL_NTT_CASE(14)
     default:
       return cudaErrorInvalidValue;
   }
+#undef PENCIL_NTT_CASE
 }
 
 }  // namespace pencil

@@ -204,44 +204,376 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
 }
 
-// CTA (x, limb) transforms polynomial first + x.
-template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
-    k_ntt_fwd(DevCtx ctx, typename Mode::Params P, int first) {
-  extern __shared__ u64 sm[];
-  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
+// ------------------------------------------------------------------ pseudo-Mersenne engine
+// The same transforms for primes q = 2^60 - c (c < 2^24) with ct_fold / gs_fold
+// butterflies (common.cuh): no correction step inside a butterfly; values grow
+// lazily and are folded (fold60) only where the bound requires it:
+//  * forward: a stage adds less than 2q to the bound, so the registers are
+//    folded once per round of at most 5 stages (bound < 11.01 q < 2^64) and
+//    brought to [0, q) (fold, one conditional subtraction) before the epilogue;
+//  * inverse: a stage doubles the bound of its sums, so the sums of every
+//    second stage (counted from the first inverse stage) are folded; inputs
+//    stay below 2.26 q and the subtraction constant is 2q or 4q.
+// Shared memory holds the N words with two spare words after every 32
+// (slot ph(x)): every round's accesses are conflict-free and a thread's words of
+// one round sit at compile-time offsets from one base address.  The last
+// forward round of at most 2 stages runs inside the epilogue on groups of 2 or 4
+// consecutive slots read from shared memory, and the first inverse round of at
+// most 2 stages inside the prologue, which saves a shared-memory round trip
+// (N = 8192 with radix 2^4: rounds of 4, 4, 4 and 1 stages).
+
+__device__ __forceinline__ constexpr int ph(int x) { return x + 2 * (x >> 5); }
+
+template <int LOGN, int LOGE>
+struct FCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int E = 1 << LOGE;
+  static constexpr int T = N >> LOGE;
+  static constexpr int R = (LOGN + LOGE - 1) / LOGE;    // rounds
+  static constexpr int SL = (R - 1) * LOGE;              // first stage of the last round
+  static constexpr int KL = LOGN - SL;                   // its stages, 1 .. LOGE
+  static constexpr bool FUSE = KL <= 2;
+  static constexpr size_t SMEM = (size_t)(N + 2 * (N >> 5)) * sizeof(u64);
+  static constexpr int MIN_BLOCKS = (T <= 512 && 2 * SMEM <= 227 * 1024) ? 2 : 1;
+};
+
+// Round S0 of the fold engine: K stages on G groups of 2^K words per thread;
+// group gg of thread tau is at positions base + l 2^LOGD, slot ph(base) + ph(l 2^LOGD).
+template <int LOGN, int LOGE, int S0>
+struct FRound {
+  static constexpr int K = (LOGN - S0) < LOGE ? (LOGN - S0) : LOGE;
+  static constexpr int G = 1 << (LOGE - K);
+  static constexpr int LOGD = LOGN - S0 - K;
+  static constexpr int T = (1 << LOGN) >> LOGE;
+  static constexpr int E = 1 << LOGE;
+
+  static __device__ __forceinline__ int grp(int tau, int gg) { return gg * T + tau; }
+  static __device__ __forceinline__ int base(int tau, int gg) {
+    const int g = grp(tau, gg);
+    return ph(((g >> LOGD) << (LOGD + K)) + (g & ((1 << LOGD) - 1)));
+  }
+  static __device__ __forceinline__ void load(u64 (&v)[E], const u64* sm, int tau) {
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      const u64* b = sm + base(tau, gg);
+#pragma unroll
+      for (int l = 0; l < (1 << K); ++l) v[gg * (1 << K) + l] = b[ph(l << LOGD)];
+    }
+  }
+  static __device__ __forceinline__ void store(const u64 (&v)[E], u64* sm, int tau) {
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      u64* b = sm + base(tau, gg);
+#pragma unroll
+      for (int l = 0; l < (1 << K); ++l) b[ph(l << LOGD)] = v[gg * (1 << K) + l];
+    }
+  }
+  // Stage J of the round (global stage S0 + J), forward.
+  template <int J>
+  static __device__ __forceinline__ void fwd_stage(u64 (&v)[E], const ulonglong2* __restrict__ tw, int tau, u32 c60,
+                                                   u32 c64, u64 q2) {
+    constexpr int half = 1 << (K - 1 - J);
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      const int B = grp(tau, gg) >> LOGD;
+#pragma unroll
+      for (int i = 0; i < (1 << J); ++i) {
+        const ulonglong2 w = __ldg(tw + (1 << (S0 + J)) + (B << J) + i);
+#pragma unroll
+        for (int r = 0; r < half; ++r) {
+          const int l = gg * (1 << K) + i * 2 * half + r;
+          ct_fold(v[l], v[l + half], w, c60, c64, q2);
+        }
+      }
+    }
+  }
+  // Stage J of the round, inverse; `step` = its position in the inverse order
+  // (LOGN - 1 - (S0 + J)): even steps subtract against 2q, odd ones against 4q
+  // and fold their sums.
+  template <int J>
+  static __device__ __forceinline__ void inv_stage(u64 (&v)[E], const ulonglong2* __restrict__ tw, int tau, u32 c60,
+                                                   u32 c64, u64 q2, u64 q4) {
+    constexpr int half = 1 << (K - 1 - J);
+    constexpr bool odd = ((LOGN - 1 - (S0 + J)) & 1) != 0;
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) {
+      const int B = grp(tau, gg) >> LOGD;
+#pragma unroll
+      for (int i = 0; i < (1 << J); ++i) {
+        const ulonglong2 w = __ldg(tw + (1 << (S0 + J)) + (B << J) + i);
+#pragma unroll
+        for (int r = 0; r < half; ++r) {
+          const int l = gg * (1 << K) + i * 2 * half + r;
+          gs_fold(v[l], v[l + half], w, c60, c64, odd ? q4 : q2);
+          if constexpr (odd) v[l] = fold60(v[l], c60);
+        }
+      }
+    }
+  }
+  template <int... J>
+  static __device__ __forceinline__ void fwd_seq(std::integer_sequence<int, J...>, u64 (&v)[E],
+                                                 const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
+    (fwd_stage<J>(v, tw, tau, c60, c64, q2), ...);
+  }
+  template <int... J>
+  static __device__ __forceinline__ void inv_seq(std::integer_sequence<int, J...>, u64 (&v)[E],
+                                                 const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2, u64 q4) {
+    (inv_stage<K - 1 - J>(v, tw, tau, c60, c64, q2, q4), ...);
+  }
+  static __device__ __forceinline__ void fwd(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
+    fwd_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, c60, c64, q2);
+  }
+  static __device__ __forceinline__ void inv(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2,
+                                             u64 q4) {
+    inv_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, c60, c64, q2, q4);
+  }
+};
+
+// Full forward rounds S0, S0 + LOGE, ... before the last round; round 0 takes its
+// words from registers (the prologue's coefficients tau + l T), the others from
+// shared memory.  Each round folds its words and leaves them in shared memory.
+template <int LOGN, int LOGE, int S0>
+struct FFwdRounds {
+  static __device__ __forceinline__ void run(u64 (&v)[1 << LOGE], u64* sm, const ulonglong2* tw, int tau, u32 c60,
+                                             u32 c64, u64 q2) {
+    using Rd = FRound<LOGN, LOGE, S0>;
+    if constexpr (S0 > 0) Rd::load(v, sm, tau);
+    Rd::fwd(v, tw, tau, c60, c64, q2);
+#pragma unroll
+    for (int l = 0; l < (1 << LOGE); ++l) v[l] = fold60(v[l], c60);
+    if constexpr (S0 > 0) __syncthreads();   // every thread has read the previous layout
+    Rd::store(v, sm, tau);
+    __syncthreads();
+    if constexpr (S0 + LOGE < FCfg<LOGN, LOGE>::SL) FFwdRounds<LOGN, LOGE, S0 + LOGE>::run(v, sm, tw, tau, c60, c64, q2);
+  }
+};
+
+// Inverse rounds from S0 down to 0 (words in shared memory on entry, synced); on
+// return v holds the coefficients tau + l T.
+template <int LOGN, int LOGE, int S0>
+struct FInvRounds {
+  static __device__ __forceinline__ void run(u64 (&v)[1 << LOGE], u64* sm, const ulonglong2* tw, int tau, u32 c60,
+                                             u32 c64, u64 q2, u64 q4) {
+    using Rd = FRound<LOGN, LOGE, S0>;
+    Rd::load(v, sm, tau);
+    Rd::inv(v, tw, tau, c60, c64, q2, q4);
+    if constexpr (S0 > 0) {
+      __syncthreads();
+      Rd::store(v, sm, tau);
+      __syncthreads();
+      FInvRounds<LOGN, LOGE, S0 - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+    }
+  }
+};
+
+// The last forward round's KL stages on one group of W = 2^KL consecutive slots
+// (group index g: positions g W .. g W + W - 1), then canonical values.
+template <int LOGN, int LOGE>
+__device__ __forceinline__ void fold_last_fwd(u64 (&u)[1 << FCfg<LOGN, LOGE>::KL], const ulonglong2* __restrict__ tw,
+                                              int g, u32 c60, u32 c64, u64 q, u64 q2) {
+  using C = FCfg<LOGN, LOGE>;
+  constexpr int W = 1 << C::KL;
+#pragma unroll
+  for (int J = 0; J < C::KL; ++J) {
+    const int half = W >> (J + 1);
+#pragma unroll
+    for (int i = 0; i < (1 << J); ++i) {
+      const ulonglong2 w = __ldg(tw + (1 << (C::SL + J)) + (g << J) + i);
+#pragma unroll
+      for (int r = 0; r < half; ++r) ct_fold(u[i * 2 * half + r], u[i * 2 * half + r + half], w, c60, c64, q2);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < W; ++i) u[i] = csub(fold60(u[i], c60), q);
+}
+
+// The first inverse round's KL stages (inverse steps 0 .. KL - 1) on one group.
+template <int LOGN, int LOGE>
+__device__ __forceinline__ void fold_first_inv(u64 (&u)[1 << FCfg<LOGN, LOGE>::KL],
+                                               const ulonglong2* __restrict__ tw, int g, u32 c60, u32 c64, u64 q2,
+                                               u64 q4) {
+  using C = FCfg<LOGN, LOGE>;
+  constexpr int W = 1 << C::KL;
+#pragma unroll
+  for (int J = C::KL - 1; J >= 0; --J) {
+    const int half = W >> (J + 1);
+    const bool odd = ((LOGN - 1 - (C::SL + J)) & 1) != 0;
+#pragma unroll
+    for (int i = 0; i < (1 << J); ++i) {
+      const ulonglong2 w = __ldg(tw + (1 << (C::SL + J)) + (g << J) + i);
+#pragma unroll
+      for (int r = 0; r < half; ++r) {
+        u64& x = u[i * 2 * half + r];
+        gs_fold(x, u[i * 2 * half + r + half], w, c60, c64, odd ? q4 : q2);
+        if (odd) x = fold60(x, c60);
+      }
+    }
+  }
 }
 
 template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+__device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typename Mode::Params& P, int poly,
+                                                 int limb, u64* sm) {
+  using C = FCfg<LOGN, LOGE>;
+  const int tau = threadIdx.x;
+  const LimbConst& lc = ctx.limb[limb];
+  const u64 q = lc.q, q2 = 2 * q;
+  const u32 c60 = (u32)lc.c60, c64 = (u32)lc.c64;
+  const ulonglong2* tw = ctx.tw_fwd_f + (size_t)limb * C::N;
+  u64 v[C::E];
+  if constexpr (Mode::kHeavyLoad) {
+#pragma unroll(Mode::kLoadUnroll)
+    for (int l = 0; l < C::E; ++l) {
+      const int e = tau + l * C::T;
+      sm[ph(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+    }
+#pragma unroll
+    for (int l = 0; l < C::E; ++l) v[l] = sm[ph(tau + l * C::T)];
+  } else {
+#pragma unroll
+    for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
+  }
+  // (round 0 stores each thread's words at the slots it read them from: no barrier needed here)
+  FFwdRounds<LOGN, LOGE, 0>::run(v, sm, tw, tau, c60, c64, q2);
+  if constexpr (C::FUSE) {
+    constexpr int W = 1 << C::KL;
+#pragma unroll(Mode::kEpilogueUnroll)
+    for (int j = 0; j < (C::E >> C::KL); ++j) {
+      const int g = j * C::T + tau;
+      u64 u[W];
+      const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(g * W));
+#pragma unroll
+      for (int i = 0; i < W / 2; ++i) {
+        const ulonglong2 x = b[i];
+        u[2 * i] = x.x;
+        u[2 * i + 1] = x.y;
+      }
+      fold_last_fwd<LOGN, LOGE>(u, tw, g, c60, c64, q, q2);
+#pragma unroll
+      for (int i = 0; i < W / 2; ++i) Mode::template store2<C::N>(ctx, P, lc, poly, limb, g * W + 2 * i, u[2 * i],
+                                                                 u[2 * i + 1]);
+    }
+  } else {
+    using Rd = FRound<LOGN, LOGE, C::SL>;
+    Rd::load(v, sm, tau);
+    Rd::fwd(v, tw, tau, c60, c64, q2);
+#pragma unroll
+    for (int l = 0; l < C::E; ++l) v[l] = csub(fold60(v[l], c60), q);
+    __syncthreads();
+    Rd::store(v, sm, tau);
+    __syncthreads();
+#pragma unroll(Mode::kEpilogueUnroll)
+    for (int l = 0; l < C::E / 2; ++l) {
+      const int e = 2 * (tau + l * C::T);
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sm + ph(e));
+      Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x.x, x.y);
+    }
+  }
+}
+
+template <int LOGN, int LOGE, class Mode>
+__device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typename Mode::Params& P, int poly,
+                                                 int limb, u64* sm) {
+  using C = FCfg<LOGN, LOGE>;
+  const int tau = threadIdx.x;
+  const LimbConst& lc = ctx.limb[limb];
+  const u64 q = lc.q, q2 = 2 * q, q4 = 4 * q;
+  const u32 c60 = (u32)lc.c60, c64 = (u32)lc.c64;
+  const ulonglong2* tw = ctx.tw_inv_f + (size_t)limb * C::N;
+  u64 v[C::E];
+  if constexpr (C::FUSE) {
+    constexpr int W = 1 << C::KL;
+#pragma unroll(Mode::kLoadUnroll)
+    for (int j = 0; j < (C::E >> C::KL); ++j) {
+      const int g = j * C::T + tau;
+      u64 u[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) u[i] = Mode::template load<C::N>(ctx, P, lc, poly, limb, g * W + i);
+      fold_first_inv<LOGN, LOGE>(u, tw, g, c60, c64, q2, q4);
+      ulonglong2* b = reinterpret_cast<ulonglong2*>(sm + ph(g * W));
+#pragma unroll
+      for (int i = 0; i < W / 2; ++i) b[i] = make_ulonglong2(u[2 * i], u[2 * i + 1]);
+    }
+    __syncthreads();
+    if constexpr (C::SL > 0) FInvRounds<LOGN, LOGE, C::SL - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+  } else {
+#pragma unroll(Mode::kLoadUnroll)
+    for (int l = 0; l < C::E; ++l) {
+      const int e = tau + l * C::T;
+      sm[ph(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+    }
+    __syncthreads();
+    FInvRounds<LOGN, LOGE, C::SL>::run(v, sm, tw, tau, c60, c64, q2, q4);
+  }
+  // v < 2.26 q; the mode's store multiplies by N^{-1} (Shoup: any 64-bit input)
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
+}
+
+// Launch shape of either engine.
+template <int LOGN, int LOGE, bool FOLD>
+struct KCfg {
+  static constexpr int T = (1 << LOGN) >> LOGE;
+  static constexpr size_t SMEM = FOLD ? FCfg<LOGN, LOGE>::SMEM : NttCfg<LOGN, LOGE>::SMEM;
+  static constexpr int MIN_BLOCKS = FOLD ? FCfg<LOGN, LOGE>::MIN_BLOCKS : NttCfg<LOGN, LOGE>::MIN_BLOCKS;
+};
+
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__device__ __forceinline__ void fwd_any(const DevCtx& ctx, const typename Mode::Params& P, int poly, int limb,
+                                        u64* sm) {
+  if constexpr (FOLD)
+    ntt_fwd_run_fold<LOGN, LOGE, Mode>(ctx, P, poly, limb, sm);
+  else
+    ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, poly, limb, sm);
+}
+
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__device__ __forceinline__ void inv_any(const DevCtx& ctx, const typename Mode::Params& P, int poly, int limb,
+                                        u64* sm) {
+  if constexpr (FOLD)
+    ntt_inv_run_fold<LOGN, LOGE, Mode>(ctx, P, poly, limb, sm);
+  else
+    ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, poly, limb, sm);
+}
+
+// CTA (x, limb) transforms polynomial first + x.
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
+    k_ntt_fwd(DevCtx ctx, typename Mode::Params P, int first) {
+  extern __shared__ __align__(16) u64 sm[];
+  fwd_any<LOGN, LOGE, Mode, FOLD>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
+}
+
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
     k_ntt_inv(DevCtx ctx, typename Mode::Params P, int first) {
-  extern __shared__ u64 sm[];
-  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
+  extern __shared__ __align__(16) u64 sm[];
+  inv_any<LOGN, LOGE, Mode, FOLD>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
 }
 
 // Multi-plan variants: CTA (blockIdx.x, limb) transforms polynomial items[x].y
 // of the plan items[x].x with that plan's parameters; `step` (device word,
 // nullable) re-keys the randomness of each replay (Mode::rebase).
-template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
     k_ntt_fwd_multi(DevCtx ctx, const typename Mode::Params* __restrict__ Ps, const int2* __restrict__ items,
                     const u64* step) {
-  extern __shared__ u64 sm[];
+  extern __shared__ __align__(16) u64 sm[];
   const int2 it = items[blockIdx.x];
   typename Mode::Params P = Ps[it.x];
   Mode::rebase(P, step ? *step : 0ull);
-  ntt_fwd_run<LOGN, LOGE, Mode>(ctx, P, it.y, blockIdx.y, sm);
+  fwd_any<LOGN, LOGE, Mode, FOLD>(ctx, P, it.y, blockIdx.y, sm);
 }
 
-template <int LOGN, int LOGE, class Mode>
-__global__ void __launch_bounds__(NttCfg<LOGN, LOGE>::T, NttCfg<LOGN, LOGE>::MIN_BLOCKS)
+template <int LOGN, int LOGE, class Mode, bool FOLD>
+__global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
     k_ntt_inv_multi(DevCtx ctx, const typename Mode::Params* __restrict__ Ps, const int2* __restrict__ items,
                     const u64* step) {
-  extern __shared__ u64 sm[];
+  extern __shared__ __align__(16) u64 sm[];
   const int2 it = items[blockIdx.x];
   typename Mode::Params P = Ps[it.x];
   Mode::rebase(P, step ? *step : 0ull);
-  ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, it.y, blockIdx.y, sm);
+  inv_any<LOGN, LOGE, Mode, FOLD>(ctx, P, it.y, blockIdx.y, sm);
 }
 
 // ------------------------------------------------------------------ fused modes
@@ -572,69 +904,71 @@ struct ModeCompact {
   }
 };
 
-// Host-side launcher; explicitly instantiated per LOGN in ntt12.cu / ntt13.cu / ntt14.cu.
-template <int LOGN, int LOGE, class Mode, bool INV>
+// Host-side launcher; explicitly instantiated per LOGN and engine in ntt12.cu /
+// ntt13.cu / ntt14.cu (Shoup) and ntt12f.cu / ntt13f.cu / ntt14f.cu (folds).
+template <int LOGN, int LOGE, class Mode, bool INV, bool FOLD>
 cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int first, int count, cudaStream_t s) {
-  using C = NttCfg<LOGN, LOGE>;
+  using C = KCfg<LOGN, LOGE, FOLD>;
   if (count <= 0) return cudaSuccess;
   cudaError_t err;
   dim3 grid((unsigned)count, (unsigned)ctx.L);
   if constexpr (INV) {
-    err = cudaFuncSetAttribute(k_ntt_inv<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_ntt_inv<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_inv<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
+    k_ntt_inv<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
   } else {
-    err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_fwd<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
+    k_ntt_fwd<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
   }
   return cudaGetLastError();
 }
 
-template <int LOGN, int LOGE, class Mode, bool INV>
+template <int LOGN, int LOGE, class Mode, bool INV, bool FOLD>
 cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const int2* items, long long count,
                              const u64* step, cudaStream_t s) {
-  using C = NttCfg<LOGN, LOGE>;
+  using C = KCfg<LOGN, LOGE, FOLD>;
   if (count <= 0) return cudaSuccess;
   if (count > 2147483647ll) return cudaErrorInvalidValue;
   cudaError_t err;
   dim3 grid((unsigned)count, (unsigned)ctx.L);
   if constexpr (INV) {
-    err = cudaFuncSetAttribute(k_ntt_inv_multi<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_ntt_inv_multi<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_inv_multi<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
+    k_ntt_inv_multi<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
   } else {
-    err = cudaFuncSetAttribute(k_ntt_fwd_multi<LOGN, LOGE, Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    err = cudaFuncSetAttribute(k_ntt_fwd_multi<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_fwd_multi<LOGN, LOGE, Mode><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
+    k_ntt_fwd_multi<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, Ps, items, step);
   }
   return cudaGetLastError();
 }
 
-#define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV)                                                          \
-  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params&, int, int,      \
-                                                              cudaStream_t);                                   \
-  SPEC template cudaError_t launch_ntt_multi<LOGN, LOGE, MODE, INV>(const DevCtx&, const MODE::Params*, const int2*, \
-                                                                    long long, const u64*, cudaStream_t);
-#define PENCIL_NTT_INST_E(SPEC, LOGN, LOGE)                \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, false)       \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, true)        \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncrypt, false)   \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false)    \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMoPrep, false)    \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false)    \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkKeygen, false)  \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkU, false)       \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncryptPk, false) \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeCompact, true)      \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true)
-// Radix 2^4 and 2^5 register blocks for one N.
-#define PENCIL_NTT_INSTANTIATE(SPEC, LOGN) \
-  PENCIL_NTT_INST_E(SPEC, LOGN, 4)         \
-  PENCIL_NTT_INST_E(SPEC, LOGN, 5)
+#define PENCIL_NTT_INST1(SPEC, LOGN, LOGE, MODE, INV, FOLD)                                                    \
+  SPEC template cudaError_t launch_ntt<LOGN, LOGE, MODE, INV, FOLD>(const DevCtx&, const MODE::Params&, int, int, \
+                                                                    cudaStream_t);                             \
+  SPEC template cudaError_t launch_ntt_multi<LOGN, LOGE, MODE, INV, FOLD>(const DevCtx&, const MODE::Params*,     \
+                                                                          const int2*, long long, const u64*,   \
+                                                                          cudaStream_t);
+#define PENCIL_NTT_INST_E(SPEC, LOGN, LOGE, FOLD)                \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, false, FOLD)       \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeRaw, true, FOLD)        \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncrypt, false, FOLD)   \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncode, false, FOLD)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeMoPrep, false, FOLD)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeKeygen, false, FOLD)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkKeygen, false, FOLD)  \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkU, false, FOLD)       \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncryptPk, false, FOLD) \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeCompact, true, FOLD)    \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true, FOLD)
+// Radix 2^4 and 2^5 register blocks for one N and one engine.
+#define PENCIL_NTT_INSTANTIATE(SPEC, LOGN, FOLD) \
+  PENCIL_NTT_INST_E(SPEC, LOGN, 4, FOLD)         \
+  PENCIL_NTT_INST_E(SPEC, LOGN, 5, FOLD)
 
 }  // namespace pencil

@@ -42,6 +42,7 @@ BATCH_PT, BATCH_CT_IN, BATCH_CT_OUT, BATCH_CT_KERNEL = 0, 1, 2, 3
 TUNE_NTT_LOG_RADIX = 0
 TUNE_MAC_COLUMNS = 1
 TUNE_MAC_STAGING = 2
+TUNE_NTT_ARITH = 3
 KERNEL_NAMES = ("ntt_raw", "intt_raw", "ntt_encrypt", "ntt_addplain", "ntt_encode", "ntt_mask", "intt_decrypt",
                 "ntt_keygen", "mac", "mac_dual", "sample_err", "mask_poly", "mo_share", "decrypt_combine",
                 "ring", "bias_grad", "ntt_mo_prep", "lincomb", "sample_pk", "ntt_pk_u", "ntt_encrypt_pk",

@@ -111,3 +111,42 @@ def test_large_batch_roundtrip(he):
         assert (got[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all()
     he.pencil_ntt_batch(ctx, d, inverse=True)
     assert torch.equal(d, to_dev(a))
+
+
+@pytest.mark.parametrize("log_n,L,radix", [(13, 3, 4), (13, 3, 5), (14, 4, 4), (14, 4, 5), (12, 4, 4), (12, 2, 5)])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_butterfly_arithmetic_knob_matches_oracle(he, log_n, L, radix, arith):
+    """Both butterfly arithmetics (Shoup / Harvey and the pseudo-Mersenne folds
+    with lazily growing values) give the oracle's transforms for every radix,
+    including the all-(q - 1) and single-spike rows."""
+    ctx = he.Context(log_n, L, 60)
+    ctx.tune(he.TUNE_NTT_ARITH, arith)
+    ctx.tune(he.TUNE_NTT_LOG_RADIX, radix)
+    assert ctx.get_tune(he.TUNE_NTT_ARITH) == arith
+    p = BfvParams(log_n=log_n, num_primes=L, prime_bits=60)
+    a = _random_polys(p, 4, 500 + log_n + radix + 7 * arith)
+    d = to_dev(a)
+    he.pencil_ntt_batch(ctx, d, inverse=False)
+    fwd = to_np(d)
+    d2 = to_dev(a)
+    he.pencil_ntt_batch(ctx, d2, inverse=True)
+    inv = to_np(d2)
+    for i in (1, 2, 3):
+        j = i % L
+        q, psi = p.primes[j], p.psis[j]
+        want = ntt_radix2([int(x) for x in a[i, j]], q, psi)
+        assert (fwd[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all(), (i, j)
+        want = intt_radix2([int(x) for x in a[i, j]], q, psi)
+        assert (inv[i, j] == np.array(list(want), dtype=object).astype(np.uint64)).all(), (i, j)
+    he.pencil_ntt_batch(ctx, d, inverse=True)
+    assert (to_np(d) == a).all()
+
+
+def test_fold_arithmetic_needs_pseudo_mersenne_primes(he):
+    """54-bit primes are not 2^60 - c: the fold butterflies are refused there and
+    the context keeps the Shoup arithmetic."""
+    ctx = he.Context(12, 2, 54)
+    assert ctx.get_tune(he.TUNE_NTT_ARITH) == 0
+    with pytest.raises(he.PencilError):
+        ctx.tune(he.TUNE_NTT_ARITH, 1)
+    assert he.Context(13, 3, 60).get_tune(he.TUNE_NTT_ARITH) == 1
