@@ -332,3 +332,89 @@ def test_autotuner_over_forward_and_backward_roles(he):
     local = add(protocol.ring_op(ol, "wgrad", to_np(g1).reshape(ol.y_shape()), to_np(x1).reshape(ol.x_shape()), 41),
                 protocol.ring_op(ol, "wgrad", to_np(g0).reshape(ol.y_shape()), to_np(x0).reshape(ol.x_shape()), 41))
     assert (add(to_np(y0), to_np(y1), local.reshape(-1)) == protocol.ring_op(ol, "wgrad", gy, x, 41).reshape(-1)).all()
+
+
+def test_batch_entries_match_oracle(he):
+    """Forward, input-gradient and weight-gradient entries of a conv and an FC
+    layer in one batch, compared with the oracle directly (not through the
+    per-layer calls): the last output ciphertext of every entry is bit-exact
+    with Alg. 1 / Alg. 2, the MO's shares and the DO's decrypted shares equal
+    the oracle's, and the shares reconstruct the ring operators."""
+    from oracle import bfv, protocol
+    from oracle.packing import Partition, counts
+    from oracle.params import BfvParams
+    from oracle.protocol import DGRAD, FWD, WGRAD
+    from oracle.protocol import Layer as OLayer
+    from tests.gpu_util import as_u64, to_np
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(12)
+    p = BfvParams(log_n=13, num_primes=3, prime_bits=60)
+    osk = bfv.keygen(p, 12)
+    layers = [(he.Layer(he.CONV, 4, 16, 8, 8, 8, 3, 1), OLayer("conv", B=4, Ci=16, Co=8, h=8, w=8, s=3, pad=1)),
+              (he.Layer(he.FC, 16, 512, 10), OLayer("fc", B=16, Ci=512, Co=10))]
+    roles = ((he.ROLE_FWD, FWD), (he.ROLE_DGRAD, DGRAD), (he.ROLE_WGRAD, WGRAD))
+    entries = [(hr, orole, hl, ol) for hl, ol in layers for hr, orole in roles]
+    plans = [he.Plan(ctx, hl, hr, None) for hr, _, hl, _ in entries]
+    batch = he.Batch(ctx, plans)
+    g = inputs.rng(13)
+    data = []
+    for i, ((hr, orole, hl, ol), pl) in enumerate(zip(entries, plans)):
+        y0 = torch.full((pl.sizes.out_elems,), -1, dtype=torch.int64, device="cuda")
+        y1 = torch.full_like(y0, -1)
+        if hr == he.ROLE_WGRAD:
+            x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, ol.x_shape()))
+            g0, g1 = inputs.split_shares(g, inputs.gaussian_fixed(g, ol.y_shape()))
+            batch.bind_wgrad(i, to_dev(g0), to_dev(g1), to_dev(x0), to_dev(x1), y0, y1)
+            data.append({"x0": x0, "x1": x1, "g0": g0, "g1": g1, "y0": y0, "y1": y1})
+        else:
+            W = inputs.gaussian_fixed(g, ol.w_shape())
+            v0, v1 = inputs.split_shares(g, inputs.gaussian_fixed(g, ol.x_shape() if hr == he.ROLE_FWD
+                                                                  else ol.y_shape()))
+            bias = inputs.uniform_zt(g, (ol.Co,)) if hr == he.ROLE_FWD else None
+            batch.bind(i, to_dev(W), to_dev(v1), to_dev(v0), None if bias is None else to_dev(bias), y0, y1)
+            data.append({"W": W, "v0": v0, "v1": v1, "bias": bias, "y0": y0, "y1": y1})
+    ws = torch.empty((batch.workspace_bytes + 7) // 8, dtype=torch.int64, device="cuda")
+    batch.commit(sk, ws, ENC, MASK)
+    batch.forward()
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == 0
+    tm = np.uint64((1 << 41) - 1)
+    for i, ((hr, orole, hl, ol), pl, d) in enumerate(zip(entries, plans, data)):
+        enc, mask = ENC + i, MASK + i           # step 0 seeds of entry i
+        part = Partition(*pl.part)
+        c = counts(protocol.geometry(ol, orole), part)
+        o = c.ct_out - 1
+        m, nn = divmod(o, c.NC)
+        ins = [m * c.K + k for k in range(c.K)]
+        kers = [k * c.NC + nn for k in range(c.K)]
+        got_t = pl.new_ct(pl.sizes.ct_out)
+        batch.read(i, he.BATCH_CT_OUT, got_t)
+        torch.cuda.synchronize()
+        got = to_np(got_t)
+        y0, y1 = to_np(d["y0"]), to_np(d["y1"])
+        if hr == he.ROLE_WGRAD:
+            want = protocol.mo_wgrad_ct(
+                p, ol, part, protocol.encrypt_inputs(p, osk, ol, WGRAD, part, d["x1"], enc, indices=ins),
+                protocol.encode_kernel(p, ol, WGRAD, part, d["g0"], indices=kers),
+                protocol.encrypt_kernel_operand(p, osk, ol, WGRAD, part, d["g1"], enc + (1 << 31), indices=kers),
+                protocol.encode_input(p, ol, WGRAD, part, d["x0"], indices=ins), mask, o)
+            assert (y0 == protocol.mo_share(p, ol, WGRAD, mask).reshape(-1)).all(), i
+            gy, x = (d["g0"] + d["g1"]) & tm, (d["x0"] + d["x1"]) & tm
+            local = (protocol.ring_op(ol, WGRAD, d["g0"], d["x0"], 41) + protocol.ring_op(ol, WGRAD, d["g1"], d["x1"], 41))
+            assert (((y0 + y1 + local.reshape(-1)) & tm) == protocol.ring_op(ol, WGRAD, gy, x, 41).reshape(-1)).all(), i
+        else:
+            cts = protocol.encrypt_inputs(p, osk, ol, orole, part, d["v1"], enc, indices=ins)
+            pts = protocol.encode_kernel(p, ol, orole, part, d["W"], indices=kers)
+            want = protocol.mo_forward_ct(p, ol, orole, part, cts, pts, d["v0"], mask, o)
+            assert (y0 == protocol.mo_share(p, ol, orole, mask, d["bias"]).reshape(-1)).all(), i
+            v = (d["v0"] + d["v1"]) & tm
+            ref = protocol.ring_op(ol, orole, d["W"], v, 41)
+            if d["bias"] is not None:
+                ref = (ref + d["bias"].reshape((1, -1) + (1,) * (ref.ndim - 2))) & tm
+            assert (((y0 + y1) & tm) == ref.reshape(-1)).all(), i
+        # the DO's share at the last ciphertext's outputs = the oracle's decryption of it
+        dec = protocol.decrypt_outputs(p, osk, ol, orole, part, {o: want})
+        from oracle.packing import decode_positions
+        flats = [protocol.output_flat(ol, orole, *pos) for _, pos in decode_positions(protocol.geometry(ol, orole), part, m, nn)]
+        assert (y1[flats] == dec[flats]).all(), i
+        assert (got[o].reshape(-1) == as_u64(want).reshape(-1)).all(), i

@@ -137,6 +137,21 @@ def test_conv_16_16_32x32_b64_n8192(he):
                   sample_in=[9], sample_pt=[5], sample_out=[7], with_bias=False)
 
 
+def test_conv_16_16_benched_partition(he):
+    """The headline layer at the partition bench.py times (the planner's choice
+    with default knobs: 7 samples per batch block, so the last block holds one
+    sample): raw ciphertexts of the first and last blocks, output ciphertexts
+    of the first, a middle and the ragged last batch block, every decoded
+    element, the MO share and the reconstruction, all against the oracle."""
+    import bench
+    Lb = bench.LAYER
+    L = Layer("conv", B=Lb["batch"], Ci=Lb["c_in"], Co=Lb["c_out"], h=Lb["h"], w=Lb["w"], s=Lb["s"], pad=Lb["pad"])
+    plan = check_forward(he, (bench.LOG_N, bench.L, bench.PRIME_BITS), L, FWD, None, 4,
+                         sample_in=[17, 144, 150], sample_pt=[255], sample_out=[0, 77, 144, 150], with_bias=True)
+    assert plan.part == (7, 1, 1, 32, 32, 3, 3)
+    assert (plan.sizes.ct_in, plan.sizes.pt, plan.sizes.ct_out, plan.sizes.products) == (160, 256, 160, 2560)
+
+
 @pytest.mark.parametrize("L,part,cfg", [
     (Layer("conv", B=2, Ci=3, Co=4, h=6, w=5, s=3, pad=1), (1, 2, 2, 4, 3, 3, 3), (12, 2, 54)),
     (Layer("conv", B=3, Ci=2, Co=3, h=5, w=5, s=3, pad=0), (2, 1, 2, 2, 3, 3, 3), (13, 3, 60)),
