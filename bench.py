@@ -37,9 +37,9 @@ UNIT = "products/s"
 LOG_N, L, PRIME_BITS, T_BITS = 13, 3, 60, 41
 LAYER = dict(batch=64, c_in=16, c_out=16, h=32, w=32, s=3, pad=1)
 WORKLOAD = "conv3x3_16to16_32x32_b64_fwd_N8192_L3x60_t41"
-SMS = 152                    # GB300 SM count (two dies x 76)
-IMAD_PER_CLK_SM = 64         # 32-bit integer multiply-add results per clock per SM
-MAX_SM_MHZ = 2070.0
+IMAD_PER_CLK_SM = 64         # 32-bit integer multiply-add results per clock per SM (16 per sub-partition)
+MAX_SM_MHZ = 2070.0          # GB300 maximum SM clock (MEASURED_PEAKS.json sm_max_mhz overrides it)
+HEADLINE_PARTITION = (7, 1, 1, 32, 32, 3, 3)   # the planner's choice for the workload (default knobs)
 
 
 def parse():
@@ -171,11 +171,15 @@ def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: di
         mults, byts = kernel_work(name, S, n, L_)
         per = ms / max(1, launches) * 1e-3
         sl, sms = serial.get(name, (0, 0.0))
+        alone = sms / max(1, sl) * 1e-3 if sl else None
         table[name] = {"launches": launches, "ms_per_launch": per * 1e3,
-                       "ms_per_launch_alone": sms / max(1, sl) if sl else None,
+                       "ms_per_launch_alone": alone * 1e3 if alone else None,
                        "share_alone": sms / total,
                        "tmul_per_s": mults / per / 1e12 if mults else None,
-                       "gb_per_s": byts / per / 1e9 if byts else None}
+                       "gb_per_s": byts / per / 1e9 if byts else None,
+                       # accounting fraction of the integer peak, in the step and alone
+                       "frac_alu": round(mults / per / 1e12 / peaks["alu_tmul"], 4) if mults else None,
+                       "frac_alu_alone": round(mults / alone / 1e12 / peaks["alu_tmul"], 4) if mults and alone else None}
     dom = max((k for k in table if kernel_work(k, S, n, L_)[0] > 0), key=lambda k: table[k]["share_alone"])
     mults, byts = kernel_work(dom, S, n, L_)
     per = table[dom]["ms_per_launch"] * 1e-3
@@ -219,17 +223,39 @@ def ncu_traffic(kernel: str):
     return None
 
 
-def load_peaks():
+def sm_count(device: int = 0) -> int:
+    """Streaming multiprocessors of the device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def load_peaks(sms: int = 152):
+    """HBM peak from MEASURED_PEAKS.json (else the fallback) and the integer
+    multiply peak derived from the SM count, 64 IMAD results per clock per SM and
+    the maximum SM clock."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm, src = 6800.0, "fallback"
+    hbm, src, mhz = 6800.0, "fallback", MAX_SM_MHZ
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
         hbm = float(d.get("hbm_gbs", hbm))
+        mhz = float(d.get("sm_max_mhz", mhz))
         src = "measured"
-    alu = SMS * IMAD_PER_CLK_SM * MAX_SM_MHZ * 1e6 / 1e12
-    return {"hbm_gbs": hbm, "hbm_source": src, "alu_tmul": alu,
-            "alu_source": f"derived: {SMS} SMs x {IMAD_PER_CLK_SM} IMAD/clk x {MAX_SM_MHZ:.0f} MHz"}
+    alu = sms * IMAD_PER_CLK_SM * mhz * 1e6 / 1e12
+    return {"hbm_gbs": hbm, "hbm_source": src, "alu_tmul": alu, "sms": sms,
+            "alu_source": f"derived: {sms} SMs (device properties) x {IMAD_PER_CLK_SM} IMAD/clk x {mhz:.0f} MHz"}
+
+
+def check_peak(peaks: dict, imad32_probe: float) -> str:
+    """The derived integer peak against the register-only 32-bit multiply-add
+    probe: more than 5 % apart means a wrong SM count, clock or pipe width."""
+    gap = abs(imad32_probe - peaks["alu_tmul"]) / peaks["alu_tmul"]
+    if gap > 0.05:
+        msg = (f"PEAK MISMATCH: derived {peaks['alu_tmul']:.2f} T/s vs probe {imad32_probe:.2f} T/s "
+               f"({100 * gap:.1f} % apart)")
+        print(msg, file=sys.stderr, flush=True)
+        return msg
+    return f"ok: probe {imad32_probe:.2f} T/s within {100 * gap:.1f} % of the derived peak"
 
 
 # ---------------------------------------------------------------- batched NTT sweep (row a10)
@@ -237,7 +263,7 @@ def ntt_sweep(he, device: int, polys: int, points: str, reps: int, log_radix: in
     """Sustained batched forward NTT and inverse NTT over `polys` uniform random
     polynomials per (N, L) point (60-bit primes), CUDA events on the launch stream."""
     import torch
-    peaks = load_peaks()
+    peaks = load_peaks(sm_count(device))
     out = []
     stream = torch.cuda.current_stream()
     for pt in points.split(","):
@@ -607,6 +633,30 @@ TABLE5 = [("fc", 256, 100, 1, 1, 6.8), ("fc", 512, 10, 1, 1, 2.6), ("fc", 2048, 
           ("conv", 64, 64, 16, 5, 165.0), ("conv", 3, 64, 56, 3, 244.0), ("conv", 64, 3, 56, 3, 237.0)]
 
 
+def _reconstruction_check(kind, Ly, W, x0, x1, g0, g1, Y, GX, GW) -> dict:
+    """Every element of the reconstructed Y, grad_X and grad_W against float64
+    PyTorch operators on the plaintext fixed-point values (exact: every partial
+    sum is an integer below 2^53), compared mod t."""
+    import torch
+    import torch.nn.functional as F
+    t_mask = (1 << T_BITS) - 1
+
+    def centred(v):
+        v = v & t_mask
+        return torch.where(v >= (1 << (T_BITS - 1)), v - (1 << T_BITS), v).double()
+    x, gy, w = centred(x0 + x1), centred(g0 + g1), centred(W)
+    if kind == "fc":
+        ry, rgx, rgw = x @ w.T, gy @ w, gy.T @ x
+    else:
+        ry = F.conv2d(x, w, padding=Ly.pad)
+        rgx = torch.nn.grad.conv2d_input(x.shape, w, gy, padding=Ly.pad)
+        rgw = torch.nn.grad.conv2d_weight(x, w.shape, gy, padding=Ly.pad)
+
+    def same(got, ref):
+        return bool(torch.equal(got.reshape(-1) & t_mask, ref.reshape(-1).round().to(torch.int64) & t_mask))
+    return {"y": same(Y, ry), "grad_x": same(GX, rgx), "grad_w": same(GW, rgw)}
+
+
 def table5_layers(he, device: int, reps: int = 2):
     """Forward + grad_X + grad_W of each layer through the HE path (Alg. 1, Alg. 2),
     N = 8192, batch 64: ms per layer step and per sample, ciphertext bytes per sample."""
@@ -631,10 +681,12 @@ def table5_layers(he, device: int, reps: int = 2):
                   inputs.split_shares(g, inputs.gaussian_fixed(g, ys)))
 
         def step():
-            sess.forward(Ly, W, None, x0, x1)
-            sess.backward(Ly, W, x0, x1, g0, g1, True)
-        step()
+            y = sess.forward(Ly, W, None, x0, x1)
+            return y, sess.backward(Ly, W, x0, x1, g0, g1, True)
+        (y0, y1), (gx0, gx1, gw, _) = step()
         torch.cuda.synchronize()
+        checked = _reconstruction_check(kind, Ly, W, x0, x1, g0, g1, sess.reconstruct(y0, y1),
+                                        sess.reconstruct(gx0, gx1), gw)
         sess.bytes_do_to_mo = sess.bytes_mo_to_do = 0
         t = []
         for _ in range(reps):
@@ -648,6 +700,7 @@ def table5_layers(he, device: int, reps: int = 2):
         ms = statistics.median(t)
         comm = (sess.bytes_do_to_mo + sess.bytes_mo_to_do) / reps
         out.append({"layer": f"{kind} {ci}->{co}" + (f" {hw}x{hw} k{ks}" if kind == "conv" else ""),
+                    "reconstruction_ok": checked,
                     "ms_fwd_bwd": round(ms, 3), "ms_per_sample": round(ms / B, 4),
                     "ciphertext_MB_per_sample": round(comm / B / 1e6, 3),
                     "paper_a6000_ms_per_sample_context": paper_ms})
@@ -759,7 +812,107 @@ def compact_send(he, device: int, reps: int = 10):
     return out
 
 
-EXTRAS = {"batched_uneven": batched_uneven, "batched_fwd_bwd": batched_fwd_bwd, "training_step_cnn": training_step,
+def _layer_fwd_bwd(he, device: int, cfg, Ly, xs, ys, ws, reps: int, seed: int):
+    """Alg. 1 forward + input gradient + Alg. 2 weight gradient of one layer through
+    the HE session (the calls HeLinearFn makes), median ms over `reps` steps."""
+    import torch
+    from paper_2403_11166_gb300 import autograd, inputs
+    sess = autograd.HeSession(*cfg, T_BITS, seed=seed, device=device)
+    g = inputs.rng(seed + 1)
+    dev = sess.device
+    W = torch.as_tensor(inputs.gaussian_fixed(g, ws), device=dev) & sess.mask
+    x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in inputs.split_shares(g, inputs.gaussian_fixed(g, xs)))
+    g0, g1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in inputs.split_shares(g, inputs.gaussian_fixed(g, ys)))
+
+    def fwd_bwd():
+        sess.forward(Ly, W, None, x0, x1)
+        return sess.backward(Ly, W, x0, x1, g0, g1, True)
+    fwd_bwd()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fwd_bwd()
+        b.record()
+        b.synchronize()
+        t.append(a.elapsed_time(b))
+    ok = sess.ctx.sync_status() == 0
+    prods = {r: sess.plan(Ly, v).sizes.products * (2 if v == he.ROLE_WGRAD else 1)
+             for r, v in (("fwd", he.ROLE_FWD), ("dgrad", he.ROLE_DGRAD), ("wgrad", he.ROLE_WGRAD))}
+    ms = statistics.median(t)
+    out = {"ms_fwd_bwd": round(ms, 4), "products": sum(prods.values()), "products_by_role": prods,
+           "products_per_s": sum(prods.values()) / (ms * 1e-3), "status_ok": ok,
+           "partitions": {r: sess.plan(Ly, v).part for r, v in (("fwd", he.ROLE_FWD), ("dgrad", he.ROLE_DGRAD),
+                                                                ("wgrad", he.ROLE_WGRAD))}}
+    del sess
+    torch.cuda.empty_cache()
+    return out
+
+
+def headline_fwd_bwd(he, device: int, reps: int = 10):
+    """The headline layer (conv3x3 16->16, 32x32, B = 64, N = 8192): forward +
+    input gradient + weight gradient, the metric's "fwd+bwd ms"."""
+    Ly = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
+                  LAYER["pad"])
+    B, ci, co, h, w = LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"]
+    return _layer_fwd_bwd(he, device, (LOG_N, L, PRIME_BITS), Ly, (B, ci, h, w), (B, co, h, w), (co, ci, 3, 3),
+                          reps, 21)
+
+
+def fc784_n4096(he, device: int, reps: int = 20):
+    """FC 784 -> 100, batch 32, N = 4096, two 54-bit primes (the small workload):
+    the forward step of the headline's form (encode, MO preparation, encryption,
+    multiply-accumulate, decryption; products/s) and forward + backward ms."""
+    import torch
+    from paper_2403_11166_gb300 import inputs
+    ctx = he.Context(12, 2, 54, T_BITS, device=device)
+    sk = ctx.keygen(31)
+    Ly = he.Layer(he.FC, 32, 784, 100)
+    plan = he.Plan(ctx, Ly, he.ROLE_FWD, None)
+    S = plan.sizes
+    g = inputs.rng(32)
+    dev = f"cuda:{device}"
+    W = torch.as_tensor(inputs.gaussian_fixed(g, (100, 784)), device=dev)
+    x0, x1 = (torch.as_tensor(a.view(np.int64), device=dev) for a in
+              inputs.split_shares(g, inputs.gaussian_fixed(g, (32, 784))))
+    pt, ct_in, ct_out = plan.new_pt(S.pt), plan.new_ct(S.ct_in), plan.new_ct(S.ct_out)
+    ws = plan.new_ws(max(S.ws_encrypt, S.ws_forward, S.ws_decrypt))
+    y0 = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
+    y1 = torch.empty_like(y0)
+
+    def step(i):
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, W, pt)
+        he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, x1, 100 + i, ct_in, ws)
+        he.he_linear_forward(ctx, plan, ct_in, pt, x0, None, 200 + i, ct_out, y0, ws)
+        he.decrypt_to_share(ctx, sk, plan, ct_out, y1, False, ws)
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(reps):
+        step(10 + i)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    def centred(v):
+        v = v & ((1 << T_BITS) - 1)
+        return torch.where(v >= (1 << (T_BITS - 1)), v - (1 << T_BITS), v).double()
+    # self-check: the reconstruction is the plaintext product (exact in float64)
+    ok = bool(torch.equal(centred(y0 + y1).view(32, 100), centred(x0 + x1) @ W.double().T))
+    out = {"forward": {"ms_per_step": round(ms, 4), "products_per_step": S.products,
+                       "products_per_s": S.products / (ms * 1e-3), "partition": plan.part,
+                       "ct_in": S.ct_in, "pt": S.pt, "ct_out": S.ct_out, "reconstruction_ok": ok,
+                       "status_ok": ctx.sync_status() == 0}}
+    del ctx
+    torch.cuda.empty_cache()
+    out["fwd_bwd"] = _layer_fwd_bwd(he, device, (12, 2, 54), Ly, (32, 784), (32, 100), (100, 784), reps, 33)
+    return out
+
+
+EXTRAS = {"headline_fwd_bwd": headline_fwd_bwd, "fc784_b32_n4096": fc784_n4096,
+          "batched_uneven": batched_uneven, "batched_fwd_bwd": batched_fwd_bwd, "training_step_cnn": training_step,
           "large_conv_128_fwd_bwd": large_conv, "pencil_plus_fwd_m8": pencil_plus,
           "paper_table5_layers_b64": table5_layers, "public_key_and_flooding": pk_and_flooding,
           "compact_send_form": compact_send}
@@ -850,14 +1003,119 @@ def cpu_ntt_baseline(seconds: float = 6.0):
     return out
 
 
+def cpu_pipeline(he, device: int):
+    """The plain C/OpenMP build of the HE pipeline (oracle/cpu_he.c: encode,
+    encrypt, Alg. 1 / Alg. 2 evaluation, decrypt; bit-exact with the oracle) on
+    the host cores, on the partitions the GPU planner picks for each (layer, role).
+    ms per step at one thread (the small workloads) and at every thread.  The
+    96-layer batch is timed on one layer of each shape and role (the other 31
+    copies are identical: x 32) and the conv 128->128 layer at batch 16 with the
+    batch-128 partitions (scaled by the product count); both are marked."""
+    from oracle.cpu_he import CpuHe, max_threads
+    from oracle.packing import Partition, counts
+    from oracle.params import BfvParams
+    from oracle.protocol import DGRAD, FWD, WGRAD
+    from oracle.protocol import Layer as OL
+    from oracle.protocol import geometry
+    from paper_2403_11166_gb300 import inputs
+    cores = max_threads()
+    roles = {he.ROLE_FWD: FWD, he.ROLE_DGRAD: DGRAD, he.ROLE_WGRAD: WGRAD}
+    engines, gctx = {}, {}
+
+    def engine(cfg):
+        if cfg not in engines:
+            engines[cfg] = CpuHe(BfvParams(log_n=cfg[0], num_primes=cfg[1], prime_bits=cfg[2]), 5)
+            gctx[cfg] = he.Context(*cfg, T_BITS, device=device)
+        return engines[cfg], gctx[cfg]
+
+    def olayer(Ly):
+        if Ly.kind == he.FC:
+            return OL("fc", B=Ly.batch, Ci=Ly.c_in, Co=Ly.c_out)
+        return OL("conv", B=Ly.batch, Ci=Ly.c_in, Co=Ly.c_out, h=Ly.height, w=Ly.width, s=Ly.kernel, pad=Ly.pad)
+
+    def run(cfg, entries, threads, part_from=None):
+        """entries: (he.Layer, he role); returns (seconds, products)."""
+        che, ctx = engine(cfg)
+        g = inputs.rng(3)
+        total, prods = 0.0, 0
+        for Ly, r in entries:
+            L_ = olayer(Ly)
+            src = part_from(Ly, r) if part_from else Ly
+            part = Partition(*he.Plan(ctx, src, r, None).part)
+            c = counts(geometry(L_, roles[r]), part)
+            if r == he.ROLE_WGRAD:
+                x0, x1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L_.x_shape()))
+                g0, g1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L_.y_shape()))
+                t0 = time.perf_counter()
+                che.layer_alg2(L_, part, g0, g1, x0, x1, 1, 2, 3, threads=threads)
+                total += time.perf_counter() - t0
+                prods += 2 * c.products
+            else:
+                W = inputs.gaussian_fixed(g, L_.w_shape())
+                v0, v1 = inputs.split_shares(g, inputs.gaussian_fixed(g, L_.x_shape() if r == he.ROLE_FWD
+                                                                      else L_.y_shape()))
+                t0 = time.perf_counter()
+                che.layer_alg1(L_, roles[r], part, W, v1, v0, 1, 2, threads=threads)
+                total += time.perf_counter() - t0
+                prods += c.products
+        return total, prods
+
+    def line(sec, prods, threads, note=None):
+        d = {"ms": round(sec * 1e3, 2), "products": prods, "products_per_s": prods / sec, "threads": threads}
+        if note:
+            d["note"] = note
+        return d
+    cfg60, cfg54 = (LOG_N, L, PRIME_BITS), (12, 2, 54)
+    fb = (he.ROLE_FWD, he.ROLE_DGRAD, he.ROLE_WGRAD)
+    head = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
+                    LAYER["pad"])
+    fc1 = he.Layer(he.FC, 32, 784, 100)
+    out = {"cores": cores, "kind": "plain C + OpenMP build of the pipeline (oracle/cpu_he.c, oracle/cpu_ntt.c)"}
+    t0 = time.perf_counter()
+    out["conv16_b64_fwd"] = {"threads_1": line(*run(cfg60, [(head, he.ROLE_FWD)], 1), 1),
+                             "threads_all": line(*run(cfg60, [(head, he.ROLE_FWD)], cores), cores)}
+    out["conv16_b64_fwd_bwd"] = {"threads_all": line(*run(cfg60, [(head, r) for r in fb], cores), cores)}
+    out["fc784_b32_n4096_fwd"] = {"threads_1": line(*run(cfg54, [(fc1, he.ROLE_FWD)], 1), 1),
+                                  "threads_all": line(*run(cfg54, [(fc1, he.ROLE_FWD)], cores), cores)}
+    out["fc784_b32_n4096_fwd_bwd"] = {"threads_all": line(*run(cfg54, [(fc1, r) for r in fb], cores), cores)}
+    cnn = [(he.Layer(he.CONV, 64, 3, 16, 32, 32, 3, 1), he.ROLE_FWD), (he.Layer(he.CONV, 64, 3, 16, 32, 32, 3, 1),
+                                                                      he.ROLE_WGRAD)]
+    cnn += [(he.Layer(he.CONV, 64, 16, 32, 32, 32, 3, 1), r) for r in fb]
+    cnn += [(he.Layer(he.FC, 64, 8192, 10), r) for r in fb]
+    out["cnn3_b64_fwd_bwd"] = {"threads_all": line(*run(cfg60, cnn, cores), cores)}
+    shapes = [he.Layer(he.FC, 16, 512, 10), he.Layer(he.CONV, 32, 64, 64, 8, 8, 3, 1),
+              he.Layer(he.CONV, 8, 128, 256, 4, 4, 1, 0)]
+    sec, prods = run(cfg60, [(Ly, r) for Ly in shapes for r in fb], cores)
+    out["batched_96_layers_fwd_bwd"] = {"threads_all": line(sec * 32, prods * 32, cores,
+                                                            "one layer of each shape and role timed, x 32")}
+    big = he.Layer(he.CONV, 128, 128, 128, 16, 16, 3, 1)
+    small = he.Layer(he.CONV, 16, 128, 128, 16, 16, 3, 1)
+    sec, prods = run(cfg60, [(small, r) for r in fb], cores, part_from=lambda Ly, r: big)
+    full = 0
+    for r in fb:
+        part = Partition(*he.Plan(gctx[cfg60], big, r, None).part)
+        full += counts(geometry(olayer(big), roles[r]), part).products * (2 if r == he.ROLE_WGRAD else 1)
+    out["conv128_b128_fwd_bwd"] = {"threads_all": line(sec * full / prods, full, cores,
+                                                       f"timed at batch 16 with the batch-128 partitions "
+                                                       f"({prods} products), scaled to {full}")}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    for c in gctx.values():
+        c.close()
+    return out
+
+
 def run_reference(args):
+    """The oracle (the only reference implementation of the paper there is) on the
+    host cores, on the partition the GPU arm times: every step times one round of
+    each stage (one encryption, add_plain, encoding, product, re-mask and
+    decryption) and scales the stage times by the partition's counts."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     vals, steps_s = [], []
     desc, spent = "", 0.0
     for i in range(args.warmup + args.steps):
-        v, st, desc, sp = oracle_sample(seed=i)
+        v, st, desc, sp = oracle_sample(seed=i, part_tuple=HEADLINE_PARTITION)
         if i >= args.warmup:
             vals.append(v)
             steps_s.append(st)
@@ -866,8 +1124,13 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(steps_s) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (RNS mod q_i), u64 mod 2^41",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "inputs": "larger than L2 (201 MB of ct_in)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "partition": dict(zip(("bb", "cib", "cob", "th", "tw", "kth", "ktw"),
+                                                                HEADLINE_PARTITION)),
+                       "inputs": "larger than L2 (ct_in 63 MB per step)"},
+            "extrapolated_from_stage_medians": True,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                             "seconds": round(spent, 1)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -912,6 +1175,8 @@ def run_ours(args):
     layer = he.Layer(he.CONV, LAYER["batch"], LAYER["c_in"], LAYER["c_out"], LAYER["h"], LAYER["w"], LAYER["s"],
                      LAYER["pad"])
     plan = he.Plan(ctx, layer, he.ROLE_FWD, None)
+    if plan.part != HEADLINE_PARTITION and args.mac_columns < 0 and args.mac_staging < 0:
+        print(f"note: the planner chose {plan.part}, not {HEADLINE_PARTITION} (the reference arm's)", file=sys.stderr)
     S = plan.sizes
     g = inputs.rng(100 + rank)
     W = inputs.gaussian_fixed(g, (LAYER["c_out"], LAYER["c_in"], 3, 3))
@@ -998,10 +1263,11 @@ def run_ours(args):
     parity_ok = bool(torch.equal(rec, ref))
 
     # multiply-pipe probe: measured 32-bit IMAD and 64-bit Shoup rates (register-only)
+    sms = sm_count(local)
     probe = {}
     for which, key in ((0, "imad32"), (1, "shoup64"), (2, "madwide32"), (3, "mac128")):
-        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
-        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, SMS * 8, 256)
+        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, sms * 8, 256)
+        ms_p, steps_p = ctx.mul_probe(which, 1 << 14, sms * 8, 256)
         probe[key] = steps_p / (ms_p * 1e-3) / 1e12
     uuid = None
     try:
@@ -1055,10 +1321,19 @@ def run_ours(args):
     f0.record(stream)
     copy.wait_event(f0)
 
+    # events around every copy on the copy stream: the copies' own time per step
+    cp_ev = []
+
+    def timed_copy(fn):
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(copy)
+        fn()
+        b_.record(copy)
+        cp_ev.append((a, b_))
+
     def h2d_into(b):
         with torch.cuda.stream(copy):
-            for k in host:
-                sets[b][k].copy_(host[k], non_blocking=True)
+            timed_copy(lambda: [sets[b][k].copy_(host[k], non_blocking=True) for k in host])
         ev_in[b].record(copy)
 
     h2d_into(0)
@@ -1073,20 +1348,23 @@ def run_ours(args):
         ev_done[b].record(stream)
         copy.wait_event(ev_done[b])
         with torch.cuda.stream(copy):
-            hy0.copy_(sets[b]["y0"], non_blocking=True)
-            hy1.copy_(sets[b]["y1"], non_blocking=True)
+            timed_copy(lambda: (hy0.copy_(sets[b]["y0"], non_blocking=True),
+                                hy1.copy_(sets[b]["y1"], non_blocking=True)))
     ev_copied.record(copy)
     stream.wait_event(ev_copied)
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
+    copy_ms = sum(a.elapsed_time(b_) for a, b_ in cp_ev) / args.steps
+    copy_gbs = (h2d + d2h) / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], world, dev)
     value = job_throughput(S.products, args.steps, world, ms)
-    peaks = load_peaks()
+    peaks = load_peaks(sms)
     dom, table, roof = roofline(prof, serial, S, ctx.n, ctx.L, args.steps, peaks, ck)
     roof["probe"] = {"imad32_T_per_s": round(probe["imad32"], 3), "shoup64_T_per_s": round(probe["shoup64"], 3),
                      "madwide32_T_per_s": round(probe["madwide32"], 3), "mac128_T_per_s": round(probe["mac128"], 3),
-                     "note": "register-only chains, 8 per thread, 1216 x 256 threads, measured before the timed region"}
+                     "note": f"register-only chains, 8 per thread, {sms * 8} x 256 threads, measured before the timed region"}
+    roof["peak_check"] = check_peak(peaks, probe["imad32"])
     launches = sum(v[0] for v in prof.values())
     if rank != 0:
         if world > 1:
@@ -1109,7 +1387,12 @@ def run_ours(args):
         "clocks": ck,
         "gpu_launches": launches,
         "e2e": {"value": job_throughput(S.products, args.steps, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 4),
+                # the copies' own time per step (events on the copy stream) and the host link rate they reached;
+                # overlap = the part of the copy time hidden behind the step
+                "copy_ms_per_step": round(copy_ms, 4), "copy_gb_per_s": round(copy_gbs, 1) if copy_gbs else None,
+                "overlap": round(max(0.0, min(1.0, (ms / args.steps + copy_ms - ms_e2e / args.steps) / copy_ms)), 3)
+                if copy_ms > 0 else None},
     }
     if not args.no_extras and world == 1:
         line["workloads"] = extras(he, local)
@@ -1120,7 +1403,8 @@ def run_ours(args):
         v, st, desc, spent = oracle_sample(part_tuple=plan.part, min_seconds=12.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                 "seconds": round(spent, 1), "host_cores_available": len(os.sched_getaffinity(0)),
-                                "plain_cpu_ntt_limb_ntts_per_s": cpu_ntt_baseline()}
+                                "plain_cpu_ntt_limb_ntts_per_s": cpu_ntt_baseline(),
+                                "plain_cpu_pipeline": cpu_pipeline(he, local)}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

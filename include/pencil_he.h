@@ -275,9 +275,10 @@ int encrypt_share_pk(PencilCtx* ctx, const PencilPublicKey* pk, const PencilPlan
  * library holds until the process exits.  Larger calls (e.g. more than 1024
  * ciphertexts at N = 8192) return PENCIL_E_CAPACITY, print the reason on
  * stderr and launch nothing.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array,
+ * The first call with each context looks up the array's device address
+ * (cudaGetSymbolAddress, with the context's device current) and keeps it with
+ * the context; make that first call before any stream capture.  Every call on
+ * a device shares the one array,
  * which keeps the previous call's contents: each call writes every byte it
  * then reads, so nothing needs clearing, but calls that overlap on the GPU
  * (different streams, or threads) race on it -- the caller must serialise
@@ -489,7 +490,10 @@ int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t max_entrie
  * multiply-accumulate, 4: split-quotient Shoup multiply (mul_shoup3), 5: forward
  * butterfly on [0, 8q), 6: forward butterfly on [0, 4q) (Harvey), 7: inverse
  * butterfly on [0, 4q), 8: inverse butterfly on [0, 2q) (Harvey), 9: 32x32
- * high half (mul.hi.u32); for 5-8 a step is one butterfly.  Times the launch with CUDA events on `stream` and returns
+ * high half (mul.hi.u32), 10: pseudo-Mersenne product (mul_fold, PTX), 11: the
+ * same product written in C (mul_fold_c), 12: forward fold butterfly, 13: inverse
+ * fold butterfly, 14: fold60 alone, 15: forward butterfly with mul_fold_c; for
+ * 5-8 and 12, 13, 15 a step is one butterfly.  Times the launch with CUDA events on `stream` and returns
  * the elapsed milliseconds and the number of chain steps (threads * 8 * iters).
  * Synchronises `stream`. */
 int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads, double* ms,

@@ -14,7 +14,7 @@ prints; gradients are encoded / truncated with round-to-nearest
 floor(x 2^f + 1/2), because at f = 12 the floor's systematic half-unit bias,
 summed over a convolution's batch and positions, exceeds the gradient itself
 (measured: relative error above 1 for the conv weight gradients); the loss is
-scaled by the caller (2^10 in the tests) before its gradient is encoded.
+scaled by the caller (2^12 in the tests) before its gradient is encoded.
 """
 from __future__ import annotations
 

@@ -160,6 +160,7 @@ struct PencilCtx {
   ulonglong2* tw_fwd_f = nullptr;   // fold tables (w, w 2^32 mod q), when every prime allows them
   ulonglong2* tw_inv_f = nullptr;
   int* status = nullptr;
+  void* noalloc_addr = nullptr;     // device address of encrypt_share_noalloc's static scratch (this context's)
 };
 
 struct PencilSecretKey {
@@ -1445,7 +1446,7 @@ extern "C" int pencil_profile_read(PencilCtx* ctx, PencilProfEntry* out, int32_t
 
 extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, int32_t blocks, int32_t threads,
                                 double* ms, double* steps, void* stream) {
-  if (!ctx || !ms || !steps || which < 0 || which > 9 || iters < 1 || blocks < 1 || threads < 32 ||
+  if (!ctx || !ms || !steps || which < 0 || which > 15 || iters < 1 || blocks < 1 || threads < 32 ||
       threads > 1024)
     return PENCIL_E_ARG;
   DeviceGuard guard(ctx->device);
@@ -1476,28 +1477,26 @@ extern "C" int pencil_mul_probe(PencilCtx* ctx, int32_t which, int64_t iters, in
 // the call needs no workspace and allocates nothing; each GPU that loads the
 // library holds these 8 MiB until the process exits.
 #define PENCIL_NOALLOC_SCRATCH_BYTES (8ull << 20)
-#define PENCIL_NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) int8_t g_noalloc_scratch[PENCIL_NOALLOC_SCRATCH_BYTES];
 static std::mutex g_noalloc_mutex;
-static void* g_noalloc_addr[PENCIL_NOALLOC_MAX_DEVICES];
 
-// Device address of the scratch array on `device` (which must be current).
+// Device address of the scratch array for `ctx` (whose device must be current).
 // Host code cannot use the symbol itself: its name stands for a host-side
-// shadow, not for device memory.  Looked up once per device.
-static int noalloc_scratch(int device, int8_t** out) {
-  if (device < 0 || device >= PENCIL_NOALLOC_MAX_DEVICES) return PENCIL_E_ARG;
+// shadow, not for device memory.  Looked up on the context's first call and kept
+// with the context (a context created after a device reset looks it up again).
+static int noalloc_scratch(PencilCtx* ctx, int8_t** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[device]) {
+  if (!ctx->noalloc_addr) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
-      fprintf(stderr, "pencil: encrypt_share_noalloc: cudaGetSymbolAddress failed on device %d: %s\n", device,
+      fprintf(stderr, "pencil: encrypt_share_noalloc: cudaGetSymbolAddress failed on device %d: %s\n", ctx->device,
               cudaGetErrorString(e));
       return PENCIL_E_CUDA;
     }
-    g_noalloc_addr[device] = p;
+    ctx->noalloc_addr = p;
   }
-  *out = reinterpret_cast<int8_t*>(g_noalloc_addr[device]);
+  *out = reinterpret_cast<int8_t*>(ctx->noalloc_addr);
   return PENCIL_OK;
 }
 
@@ -1517,10 +1516,13 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
   }
   DeviceGuard guard(ctx->device);
   int8_t* err = nullptr;
-  const int rc = noalloc_scratch(ctx->device, &err);
+  const int rc = noalloc_scratch(ctx, &err);
   if (rc != PENCIL_OK) return rc;
   const cudaStream_t s = (cudaStream_t)stream;
-  CUDA_TRY(launch_sample_err(seed, 0, (int)count, ctx->n, err, s));
+  {
+    PROF(ctx, PENCIL_K_SAMPLE_ERR, s);
+    CUDA_TRY(launch_sample_err(seed, 0, (int)count, ctx->n, err, s));
+  }
   ModeEncrypt::Params M;
   M.pk = operand == PENCIL_OPERAND_KERNEL ? P->pk_w : P->pk_v;
   M.ac = operand == PENCIL_OPERAND_KERNEL ? P->acc_w : P->acc_v;
@@ -1529,7 +1531,10 @@ extern "C" int encrypt_share_noalloc(PencilCtx* ctx, const PencilSecretKey* sk, 
   M.sk = sk->sk;
   M.ct = ct;
   M.seed = seed;
-  CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+  {
+    PROF(ctx, PENCIL_K_NTT_ENCRYPT, s);
+    CUDA_TRY((ntt<ModeEncrypt, false>(ctx->dev, M, (int)count, s)));
+  }
   return PENCIL_OK;
 }
 

@@ -194,10 +194,51 @@ __device__ __forceinline__ void gs_butterfly(u64& x, u64& y, u64 w, u64 ws, u64 
 // a sum S < 2^93 of four 32x32->64 partial products (no quotient estimate).  With
 // S = sh 2^64 + sm 2^60 + sl (sh <= 2^29 + 1, sm < 16, sl < 2^60) the folds
 //   S = sl + sm c60 + sh c64 (mod q) < 2^60 + 2^57 + 2^30 < 1.13 q
-// leave a lazy residue; the products are six 32x32->64 multiply-adds and a few
-// 32-bit ALU operations, against eight such products and four 32-bit
-// multiply-adds for a Shoup product.
+// leave a lazy residue; the product is six 32x32->64 multiply-adds and seven
+// 32-bit ALU operations, against six such products, four 32-bit multiply-adds
+// and the correction of a Shoup product (measured with pencil_mul_probe's
+// counters: a Shoup product occupies the multiply pipe 34 cycles per warp).
+// Written as one PTX block so that every 64-bit addend of a 32x32->64
+// multiply-add is a register pair that a previous multiply produced (addends
+// assembled from 32-bit halves cost register moves: measured 30.6 -> 25.0
+// instructions per warp of butterflies in the N = 8192 forward transform).
+//   h = y1 w32h + y0 wh (< 2^61),  l = y0 wl,  m = y1 w32l,
+//   S = l + m + 2^32 h = u 2^64 + t 2^32 + s0   (one 32-bit carry chain),
+//   sm = t >> 28, sl = (t mod 2^28) 2^32 + s0, sh = u.
 __device__ __forceinline__ u64 mul_fold(u64 y, u64 w, u64 w32, u32 c60, u32 c64) {
+  u64 r;
+  asm("{\n\t"
+      ".reg .u64 h, l, m, p;\n\t"
+      ".reg .u32 y0, y1, w0, w1, v0, v1, l0, l1, m0, m1, h0, h1, s0, t, u, sm, tl;\n\t"
+      "mov.b64 {y0, y1}, %1;\n\t"
+      "mov.b64 {w0, w1}, %2;\n\t"
+      "mov.b64 {v0, v1}, %3;\n\t"
+      "mul.wide.u32 h, y1, v1;\n\t"
+      "mad.wide.u32 h, y0, w1, h;\n\t"
+      "mul.wide.u32 l, y0, w0;\n\t"
+      "mul.wide.u32 m, y1, v0;\n\t"
+      "mov.b64 {l0, l1}, l;\n\t"
+      "mov.b64 {m0, m1}, m;\n\t"
+      "mov.b64 {h0, h1}, h;\n\t"
+      "add.cc.u32 s0, l0, m0;\n\t"
+      "addc.cc.u32 t, l1, m1;\n\t"
+      "addc.u32 u, h1, 0;\n\t"
+      "add.cc.u32 t, t, h0;\n\t"
+      "addc.u32 u, u, 0;\n\t"
+      "shr.u32 sm, t, 28;\n\t"
+      "and.b32 tl, t, 0x0FFFFFFF;\n\t"
+      "mov.b64 p, {s0, tl};\n\t"
+      "mad.wide.u32 p, sm, %4, p;\n\t"
+      "mad.wide.u32 %0, u, %5, p;\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(y), "l"(w), "l"(w32), "r"(c60), "r"(c64));
+  return r;
+}
+
+// The same product in plain C (the reference form of the PTX above; the
+// multiply probe times both).
+__device__ __forceinline__ u64 mul_fold_c(u64 y, u64 w, u64 w32, u32 c60, u32 c64) {
   const u32 y0 = (u32)y, y1 = (u32)(y >> 32);
   // S = y0 wl + y1 w32l + 2^32 (y0 wh + y1 w32h)   (l, h: low and high 32-bit halves)
   const u64 p1 = (u64)y1 * (u32)w32;                           // y1 w32l

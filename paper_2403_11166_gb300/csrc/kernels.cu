@@ -1492,6 +1492,52 @@ __global__ void k_mul_probe(int which, long long iters, u64 seed, u64* sink) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc ^= x[i];
     if (acc == 0xFFFFFFFFu && seed == 0) sink[0] = acc;
+  } else if (which >= 10) {
+    // pseudo-Mersenne products and butterflies (q = 2^60 - 16383), 8 independent values:
+    // 10 mul_fold (PTX), 11 mul_fold_c (C), 12 ct_fold, 13 gs_fold, 14 fold60, 15 ct butterfly with mul_fold_c
+    const u64 q = 0xfffffffffffc001ull, q2 = 2 * q, q4 = 4 * q;
+    const u32 c60 = 16383u, c64 = 16u * 16383u;
+    const u64 w = (seed | 1ull) % q, w32 = (u64)((((unsigned __int128)w) << 32) % q);
+    const ulonglong2 ww = make_ulonglong2(w, w32);
+    u64 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (seed + t * 0x9E3779B97F4A7C15ull + i) % q;
+    for (long long it = 0; it < iters; ++it) {
+      if (which == 10) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = mul_fold(x[i], w, w32, c60, c64);
+      } else if (which == 11) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = mul_fold_c(x[i], w, w32, c60, c64);
+      } else if (which == 12) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ct_fold(x[i], x[i + 1], ww, c60, c64, q2);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fold60(x[i], c60);   // keep the chain bounded
+      } else if (which == 13) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) gs_fold(x[i], x[i + 1], ww, c60, c64, q4);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) x[i] = fold60(x[i], c60);
+      } else if (which == 14) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fold60(x[i] * 3 + 1, c60);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+          const u64 tt = mul_fold_c(x[i + 1], ww.x, ww.y, c60, c64);
+          x[i + 1] = x[i] + q2 - tt;
+          x[i] = x[i] + tt;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fold60(x[i], c60);
+      }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= x[i];
+    // (the lazy results are below 2^61, so the test must not be provably false)
+    if (acc == (seed ^ 0x5DEECE66Dull) * 3u) sink[0] = acc;
   } else if (which >= 4) {
     // butterfly / modmul formulations of the NTT kernels, 8 independent values
     const u64 q = 0xfffffffffffc001ull, q2 = 2 * q, q3 = 3 * q, q4 = 4 * q, nq = 0ull - q;

@@ -43,6 +43,22 @@ def test_noalloc_equals_encrypt_share_twice(he):
         assert torch.equal(got, want)
 
 
+def test_noalloc_at_exact_capacity(he):
+    """1024 ciphertexts x 8192 coefficients fill the 8 MiB scratch exactly: the
+    call is accepted and equals encrypt_share."""
+    ctx = he.Context(13, 3, 60)
+    sk = ctx.keygen(10)
+    plan = he.Plan(ctx, he.Layer(he.FC, 1024, 16, 16), he.ROLE_FWD, (1, 16, 16, 1, 1, 1, 1))
+    assert plan.sizes.ct_in * 8192 == 8 << 20
+    share = _share((1024, 16), 4)
+    got = plan.new_ct(plan.sizes.ct_in)
+    he.encrypt_share_noalloc(ctx, sk, plan, he.OPERAND_INPUT, share, 21, got)
+    want = plan.new_ct(plan.sizes.ct_in)
+    he.encrypt_share(ctx, sk, plan, he.OPERAND_INPUT, share, 21, want, plan.new_ws(plan.sizes.ws_encrypt))
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)
+
+
 def test_noalloc_rejects_oversized_call(he):
     ctx = he.Context(13, 3, 60)
     sk = ctx.keygen(9)
