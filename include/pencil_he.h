@@ -129,8 +129,9 @@ int pencil_sk_destroy(PencilSecretKey* sk);
 /* DO side: BFV public key (the scheme of Sec. 2.2 [Fan-Vercauteren]; the
  * paper's security simulators hand pk between the parties), for
  * encrypt_share_pk:
- *   p1 = a,  a[i] = (w0 * 2^64 + w1) mod q_j, Philox key (seed, 7), counter
- *            (i/2, 0, j, 0), words 2(i%2), 2(i%2)+1 -- NTT form;
+ *   p1 = a,  a[i] uniform mod q_j as encrypt_share's a, on Philox key (seed, 7)
+ *            with ciphertext index 0: counter (i/4, 0, j, 0), word i%4 (rejected
+ *            words replaced from counter (i, 0, j, r)) -- NTT form;
  *   p0 = -(a * NTT(s)) - NTT(e),  e[i] from the CDT (as encrypt_share's errors)
  *            on Philox key (seed, 8), counter (i/4, 0, 0, 0), word i%4.
  * Device memory owned by the handle ([2][L][N] values with Shoup companions,
@@ -237,8 +238,10 @@ int encode_weights(PencilCtx* ctx, const PencilPlan* plan, int32_t operand,
 
 /* DO: symmetric BFV encryption of a packed share (Sec. 2.2, Alg. 1 step 1,
  * Alg. 2 step 1).  For ciphertext index c (0-based within this call):
- *   c1 = a,  a[i] = (w0 * 2^64 + w1) mod q_j from Philox (key (seed, 2),
- *             counter (i/2, c, j, 0), words 2(i%2), 2(i%2)+1) -- NTT form;
+ *   c1 = a,  a[i] = w mod q_j, w = word i%4 of Philox (key (seed, 2), counter
+ *             (i/4, c, j, 0)) if w < floor(2^64 / q_j) q_j, else word 0 of the first
+ *             accepted block at counter (i, c, j, r), r = 1, 2, ... -- exactly
+ *             uniform, NTT form;
  *   c0 = NTT(Delta m + e) - a * NTT(s)  (Delta m = round(q m / t), above),
  *   e[i] from the CDT on Philox (key (seed, 3), counter (i/4, c, 0, 0), word i%4).
  * operand INPUT packs `share` with pi_v into ct[M*K]; operand KERNEL packs it

@@ -5,7 +5,8 @@
  * What it computes is oracle/protocol.py's, step by step, in C with 64-bit
  * limbs, OpenMP over ciphertexts and the NTT of oracle/cpu_ntt.c:
  *   encode   (App. A pi_W / pi_v packing, centred lift, NTT)           Sec. 5, App. A
- *   encrypt  (pi_v or pi_W packing, c1 = a, c0 = NTT(round(q m / t) + e) - a s)   Sec. 2.2
+ *   encrypt  (pi_v or pi_W packing, c1 = a, c0 = NTT(round(q m / t) + e) - a s;
+ *             a uniform mod q_j from one 64-bit word per coefficient, rejection)   Sec. 2.2
  *   Alg. 1   (c0 + NTT(round(q pi_v(x0) / t)), sum over input blocks of the
  *             ct x pt products, minus NTT(round(q s / t)); MO share s + b)
  *   Alg. 2   (sum Enc(x1) pt(gy0) + Enc(gy1) pt(x0), minus NTT(round(q s / t)))
@@ -306,12 +307,19 @@ static void encrypt_one(const HeCtx* c, const u64* m, u64 seed, long idx, u64* c
   ntt_limbs(c, c0, 0);
   for (int j = 0; j < L; ++j) {
     const u64 q = c->q[j];
-    for (int blk = 0; blk < n / 2; ++blk) {
+    const u64 bound = (u64)((((u128)1) << 64) / q * q - 1);   /* largest accepted word */
+    for (int blk = 0; blk < n / 4; ++blk) {
       u64 w[4];
       philox((u64)blk, (u64)idx, (u64)j, 0, seed, DOM_A, w);
-      for (int r = 0; r < 2; ++r) {
-        const int e = 2 * blk + r;
-        const u64 a = (u64)((((u128)w[2 * r]) << 64 | w[2 * r + 1]) % q);
+      for (int r = 0; r < 4; ++r) {
+        const int e = 4 * blk + r;
+        u64 x = w[r];
+        for (u64 attempt = 1; x > bound; ++attempt) {   /* rejected: fallback counter (e, idx, j, attempt) */
+          u64 f[4];
+          philox((u64)e, (u64)idx, (u64)j, attempt, seed, DOM_A, f);
+          x = f[0];
+        }
+        const u64 a = x % q;
         c1[(size_t)j * n + e] = a;
         c0[(size_t)j * n + e] = submod(c0[(size_t)j * n + e], mulmod(a, c->s_hat[(size_t)j * n + e], q), q);
       }

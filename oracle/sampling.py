@@ -7,7 +7,9 @@ step 3): the model owner draws a uniform mask s in Z_t.
 Readings (the paper fixes none of these): the secret key is ternary; e is a
 discrete Gaussian with sigma = 3.2, tail-cut at |e| <= 19 (~6 sigma), sampled
 by inversion of its cumulative table (CDT) at 63-bit resolution; a is drawn
-directly as an NTT-domain value, (hi*2^64 + lo) mod q_i from two 64-bit words.
+directly as an NTT-domain value, exactly uniform mod q_i: one 64-bit word per
+coefficient, kept when it lies below the largest multiple of q_i under 2^64
+(then reduced mod q_i), else replaced by a word from a fallback counter.
 """
 from __future__ import annotations
 
@@ -67,12 +69,22 @@ def ternary_secret(seed: int, n: int) -> List[int]:
 
 def uniform_a(seed: int, ct: int, limb: int, n: int, q: int, domain: int = DOMAIN_A) -> List[int]:
     """Encryption mask a for (ciphertext ct, limb), already in NTT form (the
-    public key's a with domain DOMAIN_PK_A, ct = 0)."""
+    public key's a with domain DOMAIN_PK_A, ct = 0).  Coefficient i takes word
+    i % 4 of the block at counter (i / 4, ct, limb, 0); a word w is accepted when
+    w < floor(2^64 / q) q, and then a_i = w mod q (every residue equally likely);
+    a rejected word is replaced by word 0 of the block at counter (i, ct, limb, r)
+    for r = 1, 2, ... until one is accepted (the fourth counter word is never 0
+    there, so these blocks are disjoint from the main ones)."""
+    bound = ((1 << 64) // q) * q
     out = []
-    for blk in range(n // 2):
+    for blk in range(n // 4):
         w = philox4x64((blk, ct, limb, 0), (seed, domain))
-        out.append(((w[0] << 64) | w[1]) % q)
-        out.append(((w[2] << 64) | w[3]) % q)
+        for r in range(4):
+            i, x, attempt = 4 * blk + r, w[r], 0
+            while x >= bound:
+                attempt += 1
+                x = philox4x64((i, ct, limb, attempt), (seed, domain))[0]
+            out.append(x % q)
     return out
 
 

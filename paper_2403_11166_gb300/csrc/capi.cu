@@ -341,6 +341,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     lc.c64 = (u64)((((u128)1) << 64) % q);
     lc.nqtil = mulmod(lc.ninv, lc.qtil, q);
     lc.nqtils = shoup(lc.nqtil, q);
+    lc.a_max = (u64)((((u128)1) << 64) / q * q - 1);
   }
   {   // q_total mod t (t = 2^t_bits divides 2^64: the product of the primes mod 2^64, masked)
     u64 qt = 1;

@@ -23,6 +23,7 @@ struct LimbConst {
   u64 th_hi, th_lo;  // floor(2^(128 + t_bits) / q_j), 128 bits   (t / q_j in 0.128 fixed point)
   u64 c60, c64;      // 2^60 mod q and 2^64 mod q                 (split multiply-accumulate folds)
   u64 nqtil, nqtils; // N^{-1} qtil mod q_j                       (INTT scaling folded into the CRT factor)
+  u64 a_max;         // floor(2^64 / q) q - 1: the largest 64-bit word accepted for a uniform residue
 };
 
 struct DevCtx {
@@ -329,6 +330,18 @@ __device__ __forceinline__ Philox4 philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u6
 
 __device__ __forceinline__ u64 philox_word(const Philox4& w, int i) {
   return i == 0 ? w.v[0] : i == 1 ? w.v[1] : i == 2 ? w.v[2] : w.v[3];
+}
+
+// Uniform residue mod q_j of coefficient `coef` from its 64-bit Philox word w
+// (the encryption mask a, the public key's a): w is accepted when w <= a_max
+// (below the largest multiple of q_j under 2^64) and reduced; a rejected word is
+// replaced by word 0 of the block at counter (coef, ct, limb, r), r = 1, 2, ...
+// (probability below 2^-32 per word for the primes used; the loop stops after 64
+// replacements, which for primes above 2^40 never happens in practice).
+__device__ __forceinline__ u64 uniform_mod_q(u64 w, int coef, int ct, int limb, u64 seed, u64 dom,
+                                             const LimbConst& lc) {
+  for (u64 r = 1; w > lc.a_max && r <= 64; ++r) w = philox4x64((u64)coef, (u64)ct, (u64)limb, r, seed, dom).v[0];
+  return reduce64(w, lc);
 }
 
 // ------------------------------------------------------------------ packing gathers

@@ -172,12 +172,23 @@ __device__ __forceinline__ void ntt_fwd_run(const DevCtx& ctx, const typename Mo
     for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
   }
   FwdRounds<LOGN, C::LOGE, 0>::run(v, sm, tw, tau, q, q2);
+  if constexpr (Mode::kQuad) {
 #pragma unroll(Mode::kEpilogueUnroll)
-  for (int l = 0; l < C::E / 2; ++l) {
-    const int e = 2 * (tau + l * C::T);
-    const u64 x0 = canon4(sm[sidx<LOGN>(e)], q, q2);
-    const u64 x1 = canon4(sm[sidx<LOGN>(e + 1)], q, q2);
-    Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x0, x1);
+    for (int l = 0; l < C::E / 4; ++l) {
+      const int e = 4 * (tau + l * C::T);
+      u64 x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = canon4(sm[sidx<LOGN>(e + i)], q, q2);
+      Mode::template store4<C::N>(ctx, P, lc, poly, limb, e, x);
+    }
+  } else {
+#pragma unroll(Mode::kEpilogueUnroll)
+    for (int l = 0; l < C::E / 2; ++l) {
+      const int e = 2 * (tau + l * C::T);
+      const u64 x0 = canon4(sm[sidx<LOGN>(e)], q, q2);
+      const u64 x1 = canon4(sm[sidx<LOGN>(e + 1)], q, q2);
+      Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x0, x1);
+    }
   }
 }
 
@@ -369,8 +380,8 @@ struct FInvRounds {
 // The last forward round's KL stages on one group of W = 2^KL consecutive slots
 // (group index g: positions g W .. g W + W - 1), then canonical values.
 template <int LOGN, int LOGE>
-__device__ __forceinline__ void fold_last_fwd(u64 (&u)[1 << FCfg<LOGN, LOGE>::KL], const ulonglong2* __restrict__ tw,
-                                              int g, u32 c60, u32 c64, u64 q, u64 q2) {
+__device__ __forceinline__ void fold_last_fwd(u64* u, const ulonglong2* __restrict__ tw, int g, u32 c60, u32 c64,
+                                              u64 q, u64 q2) {
   using C = FCfg<LOGN, LOGE>;
   constexpr int W = 1 << C::KL;
 #pragma unroll
@@ -436,22 +447,31 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
   // (round 0 stores each thread's words at the slots it read them from: no barrier needed here)
   FFwdRounds<LOGN, LOGE, 0>::run(v, sm, tw, tau, c60, c64, q2);
   if constexpr (C::FUSE) {
+    // groups of GW consecutive slots per iteration: the last round's groups of
+    // W = 2^KL, gathered in fours for modes that store four coefficients at a time
     constexpr int W = 1 << C::KL;
+    constexpr int GW = (Mode::kQuad && W < 4) ? 4 : W;
 #pragma unroll(Mode::kEpilogueUnroll)
-    for (int j = 0; j < (C::E >> C::KL); ++j) {
-      const int g = j * C::T + tau;
-      u64 u[W];
-      const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(g * W));
+    for (int j = 0; j < C::E / GW; ++j) {
+      const int k = j * C::T + tau;
+      u64 u[GW];
+      const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(k * GW));
 #pragma unroll
-      for (int i = 0; i < W / 2; ++i) {
+      for (int i = 0; i < GW / 2; ++i) {
         const ulonglong2 x = b[i];
         u[2 * i] = x.x;
         u[2 * i + 1] = x.y;
       }
-      fold_last_fwd<LOGN, LOGE>(u, tw, g, c60, c64, q, q2);
 #pragma unroll
-      for (int i = 0; i < W / 2; ++i) Mode::template store2<C::N>(ctx, P, lc, poly, limb, g * W + 2 * i, u[2 * i],
-                                                                 u[2 * i + 1]);
+      for (int s = 0; s < GW / W; ++s) fold_last_fwd<LOGN, LOGE>(u + s * W, tw, k * (GW / W) + s, c60, c64, q, q2);
+      if constexpr (Mode::kQuad) {
+#pragma unroll
+        for (int i = 0; i < GW / 4; ++i) Mode::template store4<C::N>(ctx, P, lc, poly, limb, k * GW + 4 * i, u + 4 * i);
+      } else {
+#pragma unroll
+        for (int i = 0; i < GW / 2; ++i)
+          Mode::template store2<C::N>(ctx, P, lc, poly, limb, k * GW + 2 * i, u[2 * i], u[2 * i + 1]);
+      }
     }
   } else {
     using Rd = FRound<LOGN, LOGE, C::SL>;
@@ -462,11 +482,22 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
     __syncthreads();
     Rd::store(v, sm, tau);
     __syncthreads();
+    if constexpr (Mode::kQuad) {
 #pragma unroll(Mode::kEpilogueUnroll)
-    for (int l = 0; l < C::E / 2; ++l) {
-      const int e = 2 * (tau + l * C::T);
-      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sm + ph(e));
-      Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x.x, x.y);
+      for (int l = 0; l < C::E / 4; ++l) {
+        const int e = 4 * (tau + l * C::T);
+        const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(e));
+        const ulonglong2 x01 = b[0], x23 = b[1];
+        u64 x[4] = {x01.x, x01.y, x23.x, x23.y};
+        Mode::template store4<C::N>(ctx, P, lc, poly, limb, e, x);
+      }
+    } else {
+#pragma unroll(Mode::kEpilogueUnroll)
+      for (int l = 0; l < C::E / 2; ++l) {
+        const int e = 2 * (tau + l * C::T);
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sm + ph(e));
+        Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x.x, x.y);
+      }
     }
   }
 }
@@ -587,6 +618,7 @@ __device__ __forceinline__ size_t ct_off(int poly, int comp, int limb, int L, in
 // In-place transform of [count][L][N] polynomials.
 struct ModeRaw {
   static constexpr bool kHeavyLoad = false;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 32;
   static constexpr int kEpilogueUnroll = 16;
   struct Params {
@@ -611,11 +643,13 @@ struct ModeRaw {
 };
 
 // DO encryption: prologue round(q m / t) + e (m gathered by the packing), epilogue
-// c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain.
+// c0 = slot - a*s_hat, c1 = a with a sampled in the NTT domain, four coefficients
+// per Philox block (one 64-bit word each, uniform_mod_q).
 struct ModeEncrypt {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = true;
   static constexpr int kLoadUnroll = 8;
-  static constexpr int kEpilogueUnroll = 1;   // Philox + two reductions per pair
+  static constexpr int kEpilogueUnroll = 1;   // Philox + four products per quad
   struct Params {
     Packing pk;
     Accessor ac;
@@ -635,23 +669,29 @@ struct ModeEncrypt {
     return ee >= 0 ? add_mod(r, (u64)ee, lc.q) : sub_mod(r, (u64)(-ee), lc.q);
   }
   template <int N>
-  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
-                                                int limb, int e, u64 x0, u64 x1) {
-    const Philox4 w = philox4x64((u64)(e >> 1), (u64)poly, (u64)limb, 0ull, P.seed, PENCIL_DOM_A);
-    const u64 a0 = reduce128(w.v[0], w.v[1], lc);
-    const u64 a1 = reduce128(w.v[2], w.v[3], lc);
-    const ulonglong2 s0 = __ldg(P.sk + (size_t)limb * N + e);
-    const ulonglong2 s1 = __ldg(P.sk + (size_t)limb * N + e + 1);
-    const u64 c00 = sub_mod(x0, mul_shoup(a0, s0.x, s0.y, lc.q), lc.q);
-    const u64 c01 = sub_mod(x1, mul_shoup(a1, s1.x, s1.y, lc.q), lc.q);
-    *reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 0, limb, c.L, N) + e) = make_ulonglong2(c00, c01);
-    *reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 1, limb, c.L, N) + e) = make_ulonglong2(a0, a1);
+  static __device__ __forceinline__ void store4(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                                int limb, int e, const u64* x) {
+    const Philox4 w = philox4x64((u64)(e >> 2), (u64)poly, (u64)limb, 0ull, P.seed, PENCIL_DOM_A);
+    u64 a[4], c0[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = uniform_mod_q(w.v[i], e + i, poly, limb, P.seed, PENCIL_DOM_A, lc);
+      const ulonglong2 s = __ldg(P.sk + (size_t)limb * N + e + i);
+      c0[i] = sub_mod(x[i], mul_shoup(a[i], s.x, s.y, lc.q), lc.q);
+    }
+    ulonglong2* d0 = reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 0, limb, c.L, N) + e);
+    ulonglong2* d1 = reinterpret_cast<ulonglong2*>(P.ct + ct_off(poly, 1, limb, c.L, N) + e);
+    d0[0] = make_ulonglong2(c0[0], c0[1]);
+    d0[1] = make_ulonglong2(c0[2], c0[3]);
+    d1[0] = make_ulonglong2(a[0], a[1]);
+    d1[1] = make_ulonglong2(a[2], a[3]);
   }
 };
 
 // MO plaintext encoding: centred lift of Z_t values, NTT.
 struct ModeEncode {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
@@ -680,6 +720,7 @@ struct ModeEncode {
 // polynomials (subtracted by the multiply-accumulate's store).
 struct ModeMoPrep {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 8;
   struct Params {
@@ -721,6 +762,7 @@ __device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
 // DO key generation: ternary s, NTT, stored with Shoup companions.
 struct ModeKeygen {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 4;
   static constexpr int kEpilogueUnroll = 1;
   struct Params {
@@ -747,10 +789,11 @@ __device__ __forceinline__ u64 neg_mod(u64 v, u64 q) { return v ? q - v : 0; }
 
 // DO public key (BFV as in Fan-Vercauteren): x = NTT(e) of the sampled error;
 // p1 = a, uniform in the NTT domain from Philox (key (seed, 7), counter
-// (i/2, 0, limb, 0), words 2(i%2), 2(i%2)+1); p0 = -(a s) - x.  Both stored
+// (i/4, 0, limb, 0), word i%4; uniform_mod_q); p0 = -(a s) - x.  Both stored
 // with Shoup companions: key[comp][L][N].
 struct ModePkKeygen {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = true;
   static constexpr int kLoadUnroll = 8;
   static constexpr int kEpilogueUnroll = 1;
   struct Params {
@@ -765,27 +808,24 @@ struct ModePkKeygen {
     return lift_small(P.err[e], lc.q);
   }
   template <int N>
-  static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst& lc, int, int limb,
-                                                int e, u64 x0, u64 x1) {
-    const Philox4 w = philox4x64((u64)(e >> 1), 0ull, (u64)limb, 0ull, P.seed, PENCIL_DOM_PK_A);
-    const u64 a0 = reduce128(w.v[0], w.v[1], lc);
-    const u64 a1 = reduce128(w.v[2], w.v[3], lc);
-    const ulonglong2 s0 = __ldg(P.sk + (size_t)limb * N + e);
-    const ulonglong2 s1 = __ldg(P.sk + (size_t)limb * N + e + 1);
-    const u64 p00 = neg_mod(add_mod(mul_shoup(a0, s0.x, s0.y, lc.q), x0, lc.q), lc.q);
-    const u64 p01 = neg_mod(add_mod(mul_shoup(a1, s1.x, s1.y, lc.q), x1, lc.q), lc.q);
-    ulonglong2* k0 = P.key + (size_t)limb * N + e;
-    ulonglong2* k1 = P.key + (size_t)(c.L + limb) * N + e;
-    k0[0] = make_ulonglong2(p00, shoup_companion(p00, lc.q));
-    k0[1] = make_ulonglong2(p01, shoup_companion(p01, lc.q));
-    k1[0] = make_ulonglong2(a0, shoup_companion(a0, lc.q));
-    k1[1] = make_ulonglong2(a1, shoup_companion(a1, lc.q));
+  static __device__ __forceinline__ void store4(const DevCtx& c, const Params& P, const LimbConst& lc, int, int limb,
+                                                int e, const u64* x) {
+    const Philox4 w = philox4x64((u64)(e >> 2), 0ull, (u64)limb, 0ull, P.seed, PENCIL_DOM_PK_A);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const u64 a = uniform_mod_q(w.v[i], e + i, 0, limb, P.seed, PENCIL_DOM_PK_A, lc);
+      const ulonglong2 s = __ldg(P.sk + (size_t)limb * N + e + i);
+      const u64 p0 = neg_mod(add_mod(mul_shoup(a, s.x, s.y, lc.q), x[i], lc.q), lc.q);
+      P.key[(size_t)limb * N + e + i] = make_ulonglong2(p0, shoup_companion(p0, lc.q));
+      P.key[(size_t)(c.L + limb) * N + e + i] = make_ulonglong2(a, shoup_companion(a, lc.q));
+    }
   }
 };
 
 // Public-key encryption, first pass: NTT(u) of each ciphertext's ternary u.
 struct ModePkU {
   static constexpr bool kHeavyLoad = false;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 8;
   struct Params {
@@ -811,6 +851,7 @@ struct ModePkU {
 // polynomial 2 ct + comp the component's slot).
 struct ModeEncryptPk {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 8;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
@@ -851,6 +892,7 @@ struct ModeEncryptPk {
 // the output coefficients' c0 is added by the combine kernel.
 struct ModeDecrypt {
   static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 8;
   static constexpr int kEpilogueUnroll = 16;
   struct Params {
@@ -881,6 +923,7 @@ struct ModeDecrypt {
 // (the rest is dropped).
 struct ModeCompact {
   static constexpr bool kHeavyLoad = false;
+  static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 16;
   struct Params {
