@@ -817,9 +817,17 @@ extern "C" int pencil_plan_linear(PencilCtx* ctx, const PencilLayerDesc* layer, 
     pencil_plan_destroy(P);
     return PENCIL_E_CUDA;
   }
-  P->pk_v = Packing{P->d_tab, P->d_org, make_int4(g.B, g.Ci, g.H, g.W)};
-  P->pk_w = Packing{P->d_tab + n, P->d_org + P->ct_in, make_int4(g.Co, g.Ci, g.KH, g.KW)};
-  P->pk_y = Packing{P->d_tab + 2 * (size_t)n, P->d_org + P->ct_in + P->pt, make_int4(g.B, g.Co, g.Ho(), g.Wo())};
+  int support[3] = {0, 0, 0};
+  for (int sgm = 0; sgm < 3; ++sgm)
+    for (int e = n - 1; e >= 0; --e)
+      if (tab[(size_t)sgm * n + e] != PENCIL_TAB_NONE) {
+        support[sgm] = e + 1;
+        break;
+      }
+  P->pk_v = Packing{P->d_tab, P->d_org, make_int4(g.B, g.Ci, g.H, g.W), support[0]};
+  P->pk_w = Packing{P->d_tab + n, P->d_org + P->ct_in, make_int4(g.Co, g.Ci, g.KH, g.KW), support[1]};
+  P->pk_y = Packing{P->d_tab + 2 * (size_t)n, P->d_org + P->ct_in + P->pt, make_int4(g.B, g.Co, g.Ho(), g.Wo()),
+                    support[2]};
 
   // --- workspace sizes (bytes, each region 256-byte aligned)
   auto al = [](long long b) { return (b + 255) / 256 * 256; };

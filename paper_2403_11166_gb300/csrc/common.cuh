@@ -60,11 +60,13 @@ struct Accessor {
 // Packing of one operand position class (inputs, kernels or outputs):
 // tab[e] = local (a, b, r, s) of coefficient e packed as 4 x 16 bits, or
 // all-ones when coefficient e carries nothing; org[idx] = the block origin of
-// polynomial idx; bound = the geometry extent of (a, b, r, s).
+// polynomial idx; bound = the geometry extent of (a, b, r, s); support = 1 +
+// the highest e with an entry (coefficients from support on are always zero).
 struct Packing {
   const u64* tab;
   const int4* org;
   int4 bound;
+  int support;
 };
 
 #define PENCIL_TAB_NONE 0xFFFFFFFFFFFFFFFFull

@@ -15,6 +15,7 @@
 // result goes through shared memory once more so the fused epilogue sees pairs
 // of consecutive slots (16-byte coalesced stores, one Philox block per pair).
 #pragma once
+#include <type_traits>
 #include <utility>
 
 #include "common.cuh"
@@ -334,6 +335,16 @@ struct FRound {
   static __device__ __forceinline__ void fwd(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
     fwd_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, c60, c64, q2);
   }
+  // Stages j0 .. K - 1 only (j0 uniform across the CTA).
+  template <int... J>
+  static __device__ __forceinline__ void fwd_from_seq(std::integer_sequence<int, J...>, int j0, u64 (&v)[E],
+                                                      const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
+    ((J >= j0 ? fwd_stage<J>(v, tw, tau, c60, c64, q2) : void()), ...);
+  }
+  static __device__ __forceinline__ void fwd_from(int j0, u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60,
+                                                  u32 c64, u64 q2) {
+    fwd_from_seq(std::make_integer_sequence<int, K>{}, j0, v, tw, tau, c60, c64, q2);
+  }
   static __device__ __forceinline__ void inv(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2,
                                              u64 q4) {
     inv_seq(std::make_integer_sequence<int, K>{}, v, tw, tau, c60, c64, q2, q4);
@@ -422,6 +433,47 @@ __device__ __forceinline__ void fold_first_inv(u64 (&u)[1 << FCfg<LOGN, LOGE>::K
   }
 }
 
+// Modes whose input polynomials may have a short support (Mode::support(P):
+// coefficients from there on are zero).
+template <class M, class = void>
+struct SparseInput : std::false_type {};
+template <class M>
+struct SparseInput<M, std::void_t<decltype(M::kSparse)>> : std::bool_constant<M::kSparse> {};
+
+// Forward rounds 0 and 1 of a polynomial of degree < sup <= T.  After s
+// Cooley-Tukey stages, block b of N / 2^s words holds p mod (X^{N/2^s} - zeta_b),
+// which is p itself while deg p < N / 2^s: the first LOGN - ceil(log2 sup)
+// stages only copy.  Round 0 (LOGE stages) is therefore skipped whole, and so
+// are the first j stages of round 1 where sup <= T / 2^j; round 1 then starts
+// from word x = p[x mod (N / 2^(LOGE + j))], read from the T prologue values in
+// shared memory (one gather per thread instead of E).  The values and their
+// bounds are those the skipped butterflies leave (ct_fold(a, 0) = (a, a + 2q)
+// only widens the bound).  Leaves round 1's words, folded, in shared memory.
+template <int LOGN, int LOGE, class Mode>
+__device__ __forceinline__ void fold_sparse_head(const DevCtx& ctx, const typename Mode::Params& P,
+                                                 const LimbConst& lc, int poly, int limb, int sup, u64 (&v)[1 << LOGE],
+                                                 u64* sm, const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
+  using C = FCfg<LOGN, LOGE>;
+  using R1 = FRound<LOGN, LOGE, LOGE>;
+  static_assert(R1::K == LOGE && R1::G == 1, "round 1 must be a full round");
+  sm[ph(tau)] = tau < sup ? Mode::template load<C::N>(ctx, P, lc, poly, limb, tau) : 0ull;
+  int j = 0;
+  while (j < LOGE && sup <= (C::T >> (j + 1))) ++j;
+  __syncthreads();
+  constexpr int D1 = 1 << R1::LOGD;   // round 1: thread tau holds words base + l D1
+  const int m = (C::E >> j) - 1;
+  const u64* b = sm + ph(tau & (D1 - 1));
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) v[l] = b[ph(D1 * (l & m))];
+  R1::fwd_from(j, v, tw, tau, c60, c64, q2);
+#pragma unroll
+  for (int l = 0; l < C::E; ++l) v[l] = fold60(v[l], c60);
+  __syncthreads();   // every thread has read the prologue values
+  R1::store(v, sm, tau);
+  __syncthreads();
+  if constexpr (2 * LOGE < C::SL) FFwdRounds<LOGN, LOGE, 2 * LOGE>::run(v, sm, tw, tau, c60, c64, q2);
+}
+
 template <int LOGN, int LOGE, class Mode>
 __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typename Mode::Params& P, int poly,
                                                  int limb, u64* sm) {
@@ -432,20 +484,30 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
   const u32 c60 = (u32)lc.c60, c64 = (u32)lc.c64;
   const ulonglong2* tw = ctx.tw_fwd_f + (size_t)limb * C::N;
   u64 v[C::E];
-  if constexpr (Mode::kHeavyLoad) {
-#pragma unroll(Mode::kLoadUnroll)
-    for (int l = 0; l < C::E; ++l) {
-      const int e = tau + l * C::T;
-      sm[ph(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+  bool dense = true;
+  if constexpr (SparseInput<Mode>::value && C::R >= 3) {
+    const int sup = Mode::support(P);
+    if (sup <= C::T) {
+      dense = false;
+      fold_sparse_head<LOGN, LOGE, Mode>(ctx, P, lc, poly, limb, sup, v, sm, tw, tau, c60, c64, q2);
     }
-#pragma unroll
-    for (int l = 0; l < C::E; ++l) v[l] = sm[ph(tau + l * C::T)];
-  } else {
-#pragma unroll
-    for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
   }
-  // (round 0 stores each thread's words at the slots it read them from: no barrier needed here)
-  FFwdRounds<LOGN, LOGE, 0>::run(v, sm, tw, tau, c60, c64, q2);
+  if (dense) {
+    if constexpr (Mode::kHeavyLoad) {
+#pragma unroll(Mode::kLoadUnroll)
+      for (int l = 0; l < C::E; ++l) {
+        const int e = tau + l * C::T;
+        sm[ph(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
+      }
+#pragma unroll
+      for (int l = 0; l < C::E; ++l) v[l] = sm[ph(tau + l * C::T)];
+    } else {
+#pragma unroll
+      for (int l = 0; l < C::E; ++l) v[l] = Mode::template load<C::N>(ctx, P, lc, poly, limb, tau + l * C::T);
+    }
+    // (round 0 stores each thread's words at the slots it read them from: no barrier needed here)
+    FFwdRounds<LOGN, LOGE, 0>::run(v, sm, tw, tau, c60, c64, q2);
+  }
   if constexpr (C::FUSE) {
     // groups of GW consecutive slots per iteration: the last round's groups of
     // W = 2^KL, gathered in fours for modes that store four coefficients at a time
@@ -688,10 +750,12 @@ struct ModeEncrypt {
   }
 };
 
-// MO plaintext encoding: centred lift of Z_t values, NTT.
+// MO plaintext encoding: centred lift of Z_t values, NTT (short supports,
+// e.g. one small kernel block per plaintext, skip the copy-only stages).
 struct ModeEncode {
   static constexpr bool kHeavyLoad = true;
   static constexpr bool kQuad = false;
+  static constexpr bool kSparse = true;
   static constexpr int kLoadUnroll = 16;
   static constexpr int kEpilogueUnroll = 4;
   struct Params {
@@ -699,6 +763,7 @@ struct ModeEncode {
     Accessor ac;
     u64* pt;   // [count][L][N]
   };
+  static __device__ __forceinline__ int support(const Params& P) { return P.pk.support; }
   static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly, int,
