@@ -42,6 +42,13 @@ MAX_SM_MHZ = 2070.0          # GB300 maximum SM clock (MEASURED_PEAKS.json sm_ma
 HEADLINE_PARTITION = (7, 1, 1, 32, 32, 3, 3)   # the planner's choice for the workload (default knobs)
 
 
+def _record(st):
+    import torch
+    ev = torch.cuda.Event()
+    ev.record(st)
+    return ev
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1307,51 +1314,78 @@ def run_ours(args):
     ctx.profile(False)
     serial = ctx.profile_read()
     # ---- end to end: host buffers; every step's inputs are copied in from pinned
-    # host memory and both shares copied back inside the region, on a copy stream
-    # (double-buffered: step i + 1's inputs go in and step i - 1's shares come out
-    # while step i computes)
+    # host memory and both shares copied back inside the region, inputs on one
+    # copy stream and shares on another (the two directions of the host link run
+    # at once); double-buffered: step i + 1's inputs go in and step i - 1's shares
+    # come out while step i computes
     h2d = sum(v.numel() * 8 for v in host.values())
     d2h = 2 * S.out_elems * 8
-    copy = torch.cuda.Stream(device=dev)
+    copy_in, copy_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
     ev_copied = torch.cuda.Event()
+    # the same copies with the GPU otherwise idle: the host link's own rate (the
+    # first pass, untimed, also warms the copy path: the first copies from these
+    # pinned buffers ran at a third of the later rate)
+    def idle_copies(reps):
+        for _ in range(reps):
+            with torch.cuda.stream(copy_in):
+                for k in host:
+                    sets[0][k].copy_(host[k], non_blocking=True)
+            with torch.cuda.stream(copy_out):
+                hy0.copy_(sets[1]["y0"], non_blocking=True)
+                hy1.copy_(sets[1]["y1"], non_blocking=True)
+
     torch.cuda.synchronize()
+    idle_reps = 10
+    idle_copies(idle_reps)
+    torch.cuda.synchronize()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    copy_in.wait_event(i0)
+    copy_out.wait_event(i0)
+    idle_copies(idle_reps)
+    stream.wait_event(_record(copy_in))
+    stream.wait_event(_record(copy_out))
+    i1.record(stream)
+    torch.cuda.synchronize()
+    copy_idle_ms = i0.elapsed_time(i1) / idle_reps
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    copy.wait_event(f0)
+    copy_in.wait_event(f0)
+    copy_out.wait_event(f0)
 
-    # events around every copy on the copy stream: the copies' own time per step
+    # events around every copy on its copy stream: the copies' own time per step
     cp_ev = []
 
-    def timed_copy(fn):
+    def timed_copy(st, fn):
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(copy)
-        fn()
-        b_.record(copy)
+        a.record(st)
+        with torch.cuda.stream(st):
+            fn()
+        b_.record(st)
         cp_ev.append((a, b_))
 
     def h2d_into(b):
-        with torch.cuda.stream(copy):
-            timed_copy(lambda: [sets[b][k].copy_(host[k], non_blocking=True) for k in host])
-        ev_in[b].record(copy)
+        timed_copy(copy_in, lambda: [sets[b][k].copy_(host[k], non_blocking=True) for k in host])
+        ev_in[b].record(copy_in)
 
     h2d_into(0)
     for i in range(args.steps):
         b = i % 2
         if i + 1 < args.steps:
             if i >= 1:
-                copy.wait_event(ev_done[1 - b])   # step i - 1 has finished with that set
+                copy_in.wait_event(ev_done[1 - b])   # step i - 1 (and its copy out) has finished with that set
             h2d_into(1 - b)
         stream.wait_event(ev_in[b])
         step(10_000 + i, sets[b])
-        ev_done[b].record(stream)
-        copy.wait_event(ev_done[b])
-        with torch.cuda.stream(copy):
-            timed_copy(lambda: (hy0.copy_(sets[b]["y0"], non_blocking=True),
-                                hy1.copy_(sets[b]["y1"], non_blocking=True)))
-    ev_copied.record(copy)
+        copy_out.wait_event(_record(stream))
+        timed_copy(copy_out, lambda: (hy0.copy_(sets[b]["y0"], non_blocking=True),
+                                      hy1.copy_(sets[b]["y1"], non_blocking=True)))
+        ev_done[b].record(copy_out)
+    ev_copied.record(copy_out)
     stream.wait_event(ev_copied)
+    stream.wait_event(_record(copy_in))
     f1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = f0.elapsed_time(f1)
@@ -1391,6 +1425,9 @@ def run_ours(args):
                 # the copies' own time per step (events on the copy stream) and the host link rate they reached;
                 # overlap = the part of the copy time hidden behind the step
                 "copy_ms_per_step": round(copy_ms, 4), "copy_gb_per_s": round(copy_gbs, 1) if copy_gbs else None,
+                # both directions at once with the GPU idle (the link's rate): bound = max(step, this)
+                "copy_idle_ms_per_step": round(copy_idle_ms, 4),
+                "copy_idle_gb_per_s": round((h2d + d2h) / (copy_idle_ms * 1e-3) / 1e9, 1) if copy_idle_ms > 0 else None,
                 "overlap": round(max(0.0, min(1.0, (ms / args.steps + copy_ms - ms_e2e / args.steps) / copy_ms)), 3)
                 if copy_ms > 0 else None},
     }

@@ -1261,6 +1261,17 @@ extern "C" int decrypt_to_share(PencilCtx* ctx, const PencilSecretKey* sk, const
   D.sk = sk->sk;
   D.out = reinterpret_cast<u64*>(ws);
   D.skip_c0 = 0;
+  if (ctx->dev.L <= 8) {   // INTT and CRT step in one launch, one cluster of L CTAs per ciphertext
+    ModeDecryptFused::Params F;
+    F.d = D;
+    F.pk = P->pk_y;
+    F.ac = P->acc_y;
+    F.y1 = y1;
+    F.check = check_noise ? 1 : 0;
+    PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
+    CUDA_TRY((ntt<ModeDecryptFused, true>(ctx->dev, F, (int)P->out_count(), s, (int)P->out_first())));
+    return PENCIL_OK;
+  }
   {
     PROF(ctx, PENCIL_K_INTT_DECRYPT, s);
     CUDA_TRY((ntt<ModeDecrypt, true>(ctx->dev, D, (int)P->out_count(), s, (int)P->out_first())));

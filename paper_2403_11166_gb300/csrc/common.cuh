@@ -362,6 +362,36 @@ __device__ __forceinline__ u64 gather(const Packing& pk, const Accessor& ac, int
   return __ldg(ac.ptr + ac.base + a * ac.s0 + b * ac.s1 + r * ac.s2 + s * ac.s3);
 }
 
+// Decryption's CRT step: with y_j = x_j (q/q_j)^{-1} mod q_j,
+//   t x / q = sum_j y_j t / q_j - v t  (v integer),
+// so round(t x / q) mod t = round(sum_j y_j th_j / 2^128) mod t with
+// th_j = floor(2^(128 + t_bits) / q_j).  The sum is kept as a 128-bit window
+// (64 integer bits, 64 fraction bits); truncation error < L * 2^-63.
+struct CrtSum {
+  u64 lo, hi;
+};
+__device__ __forceinline__ void crt_add(CrtSum& s, u64 y, const LimbConst& lc) {
+  const u64 a_hi = __umul64hi(y, lc.th_lo);
+  const u64 b_lo = y * lc.th_hi;
+  const u64 b_hi = __umul64hi(y, lc.th_hi);
+  const u64 w_lo = b_lo + a_hi;
+  const u64 w_hi = b_hi + (w_lo < b_lo ? 1ull : 0ull);
+  s.lo += w_lo;
+  s.hi += w_hi + (s.lo < w_lo ? 1ull : 0ull);
+}
+// The rounded value mod t; with `check`, flags (status bit 0) a fraction within
+// 1/4 of one half (noise too close to the decryption bound).
+__device__ __forceinline__ u64 crt_round(const CrtSum& s, u64 t_mask, int check, int* status) {
+  if (check) {
+    const i64 frac = (i64)s.lo;   // signed distance to the nearest integer, units of 2^-64
+    const u64 mag = frac < 0 ? (u64)(-frac) : (u64)frac;
+    if (mag >= (1ull << 62)) atomicOr(status, 1);
+  }
+  const u64 r_lo = s.lo + (1ull << 63);
+  const u64 r_hi = s.hi + (r_lo < s.lo ? 1ull : 0ull);
+  return r_hi & t_mask;
+}
+
 // Output flat index of coefficient e of output polynomial idx, or -1.
 __device__ __forceinline__ i64 out_index(const Packing& pk, const Accessor& ac, int idx, int e) {
   u64 ent = __ldg(pk.tab + e);

@@ -333,13 +333,24 @@ __device__ __forceinline__ void mbar_arrive(u32 bar) {
 // Warp-specialised: warps 0 .. MAC_BT/32 - 1 multiply (thread = slot), the last
 // warp's lane 0 produces.  full[s] completes when stage s holds its block (byte
 // count), empty[s] when the MAC_BT/32 consumer warps have finished reading it.
+// A stage holds KB consecutive input blocks (two where a block's rows are few,
+// halving the waits, votes and arrivals per block); NS stages.
+template <int NT, bool DUAL>
+struct BulkCfg {
+  static constexpr int W = MacRing<NT, DUAL>::W;   // rows per block
+  static constexpr int KB = W <= 8 ? 2 : 1;
+  static constexpr int NS = KB == 2 ? 3 : MAC_BSTAGES;
+  static constexpr size_t SMEM = (size_t)NS * KB * W * MAC_BT * sizeof(u64);
+};
+
 template <int NT, bool DUAL>
 __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams P) {
-  constexpr int W = MacRing<NT, DUAL>::W;   // rows per stage
+  using BC = BulkCfg<NT, DUAL>;
+  constexpr int W = BC::W, KB = BC::KB, NS = BC::NS;
   constexpr u32 ROW = MAC_BT * sizeof(u64);
   constexpr int CONSUMER_WARPS = MAC_BT / 32;
-  extern __shared__ __align__(128) u64 ring[];   // [MAC_BSTAGES][W][MAC_BT]
-  __shared__ __align__(8) u64 full[MAC_BSTAGES], empty[MAC_BSTAGES];
+  extern __shared__ __align__(128) u64 ring[];   // [NS][KB][W][MAC_BT]
+  __shared__ __align__(8) u64 full[NS], empty[NS];
   const int ntiles = (P.NC + NT - 1) / NT;
   const int m = blockIdx.x / ntiles + P.m_base;
   const int n0 = (blockIdx.x % ntiles) * NT;
@@ -349,7 +360,7 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   const int nn = min(NT, P.NC - n0);
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < MAC_BSTAGES; ++st) {
+    for (int st = 0; st < NS; ++st) {
       mbar_init(smem_u32(&full[st]), 1);
       mbar_init(smem_u32(&empty[st]), CONSUMER_WARPS);
     }
@@ -359,14 +370,18 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   if (tid >= MAC_BT) {   // producer warp
     if (tid != MAC_BT) return;
     const bool has_p = DUAL || P.p0 != nullptr;
-    const u32 stage_bytes = (u32)(has_p ? W : W - 1) * ROW;
-    int k = 0;
-    for (; k < P.K; ++k) {
-      const int st = k % MAC_BSTAGES;
-      if (k >= MAC_BSTAGES && !mbar_wait_bounded(smem_u32(&empty[st]), (u32)(k / MAC_BSTAGES - 1) & 1u)) break;
+    const u32 block_bytes = (u32)(has_p ? W : W - 1) * ROW;
+    const int ng = (P.K + KB - 1) / KB;
+    int g = 0;
+    for (; g < ng; ++g) {
+      const int st = g % NS;
+      if (g >= NS && !mbar_wait_bounded(smem_u32(&empty[st]), (u32)(g / NS - 1) & 1u)) break;
       const u32 bar = smem_u32(&full[st]);
-      const u32 dst = smem_u32(ring + (size_t)st * W * MAC_BT);
-      mbar_expect_tx(bar, stage_bytes);
+      const int nb = min(KB, P.K - g * KB);
+      mbar_expect_tx(bar, (u32)nb * block_bytes);
+      for (int kk = 0; kk < nb; ++kk) {
+      const int k = g * KB + kk;
+      const u32 dst = smem_u32(ring + ((size_t)st * KB + kk) * W * MAC_BT);
       const size_t mk = (size_t)m * P.K + k;
       bulk_g2s(dst, P.a0 + mk * P.a0_stride + lane0, ROW, bar);
       bulk_g2s(dst + ROW, P.a1 + mk * P.a1_stride + lane0, ROW, bar);
@@ -383,11 +398,11 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
           bulk_g2s(dst + (3 + 2 * NT + j) * ROW, P.cb1 + kn * P.cb_stride + lane0, ROW, bar);
         }
       }
+      }
     }
-    if (k < P.K) {   // consumers stopped releasing stages: record it, let the issued copies land
+    if (g < ng) {   // consumers stopped releasing stages: record it, let the issued copies land
       atomicOr(ctx.status, 2);
-      for (int kk = max(0, k - MAC_BSTAGES); kk < k; ++kk)
-        mbar_wait_bounded(smem_u32(&full[kk % MAC_BSTAGES]), (u32)(kk / MAC_BSTAGES) & 1u);
+      for (int gg = max(0, g - NS); gg < g; ++gg) mbar_wait_bounded(smem_u32(&full[gg % NS]), (u32)(gg / NS) & 1u);
     }
     return;
   }
@@ -399,14 +414,20 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   Acc3 acc[NT][2];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = Acc3{0, 0, 0, 0, 0, 0};
-  for (int k = 0; k < P.K; ++k) {
-    const int st = k % MAC_BSTAGES;
-    const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u32)(k / MAC_BSTAGES) & 1u);
+  const int ng = (P.K + KB - 1) / KB;
+  for (int g = 0; g < ng; ++g) {
+    const int st = g % NS;
+    const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u32)(g / NS) & 1u);
     if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform give-up
       if ((tid & 31) == 0) atomicOr(ctx.status, 2);   // the producer then times out on this warp's stages
       return;
     }
-    const u64* cur = ring + (size_t)st * W * MAC_BT + tid;
+    const int nb = min(KB, P.K - g * KB);
+#pragma unroll
+    for (int kk = 0; kk < KB; ++kk) {
+    if (kk >= nb) break;
+    const int k = g * KB + kk;
+    const u64* cur = ring + ((size_t)st * KB + kk) * W * MAC_BT + tid;
     u64 a0 = cur[0];
     if (!DUAL && P.p0) a0 = add_mod(a0, cur[2 * MAC_BT], lc.q);   // Alg. 1 step 2: + NTT(Delta x0)
     const u64 a1 = cur[MAC_BT];
@@ -420,8 +441,10 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
         c1w[j] = cur[(3 + 2 * NT + j) * MAC_BT];
       }
     }
-    __syncwarp();
-    if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
+    if (kk == nb - 1) {
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
+    }
     const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
     const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
     const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
@@ -460,6 +483,7 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
         fold3(acc[j][0], c60, c64);
         fold3(acc[j][1], c60, c64);
       }
+    }
     }
   }
   const size_t ln = (size_t)P.lanes;
@@ -685,8 +709,7 @@ static cudaError_t launch_mac_bulk(const DevCtx& ctx, const MacParams& P0, bool 
   const int ntiles = (P.NC + NT - 1) / NT;
   const unsigned gy = (unsigned)(P.lanes / MAC_BT);
   const int mchunk = max(1, 2147483647 / max(1, ntiles));
-  const size_t smem = (size_t)MAC_BSTAGES * (dual ? MacRing<NT, true>::W : MacRing<NT, false>::W) * MAC_BT *
-                      sizeof(u64);
+  const size_t smem = dual ? BulkCfg<NT, true>::SMEM : BulkCfg<NT, false>::SMEM;
   const void* fn = dual ? (const void*)k_mac_bulk<NT, true> : (const void*)k_mac_bulk<NT, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -892,11 +915,7 @@ cudaError_t launch_mo_share(u64 seed, long long count, u64 t_mask, const u64* bi
 }
 
 // ------------------------------------------------------------------ decryption, second half
-// y_j = x_j * (q/q_j)^{-1} mod q_j (first half); then
-//   t x / q = sum_j y_j t / q_j - v t  (v integer),
-// so round(t x / q) mod t = round(sum_j y_j th_j / 2^128) mod t with
-// th_j = floor(2^(128 + t_bits) / q_j).  The sum is kept as a 128-bit window
-// (64 integer bits, 64 fraction bits); truncation error < L * 2^-63.
+// y_j = x_j * (q/q_j)^{-1} mod q_j (first half), then crt_add / crt_round.
 // c0c (compact send form, else null): c0 at the output coefficients in
 // coefficient form, [L][out_elems]; added as c0c * qtil to the INTT(c1 s) residues.
 __device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Packing& pk, const Accessor& ac,
@@ -905,27 +924,14 @@ __device__ __forceinline__ void decrypt_combine_one(const DevCtx& ctx, const Pac
   const int n = ctx.n;
   const i64 flat = out_index(pk, ac, ct, e);
   if (flat < 0) return;
-  u64 s_lo = 0, s_hi = 0;
+  CrtSum sum{0, 0};
   for (int j = 0; j < ctx.L; ++j) {
     const LimbConst& lc = ctx.limb[j];
     u64 y = __ldg(yres + ((size_t)ct * ctx.L + j) * n + e);
     if (c0c) y = add_mod(y, mul_shoup(__ldg(c0c + (size_t)j * out_elems + flat), lc.qtil, lc.qtils, lc.q), lc.q);
-    const u64 a_hi = __umul64hi(y, lc.th_lo);
-    const u64 b_lo = y * lc.th_hi;
-    const u64 b_hi = __umul64hi(y, lc.th_hi);
-    const u64 w_lo = b_lo + a_hi;
-    const u64 w_hi = b_hi + (w_lo < b_lo ? 1ull : 0ull);
-    s_lo += w_lo;
-    s_hi += w_hi + (s_lo < w_lo ? 1ull : 0ull);
+    crt_add(sum, y, lc);
   }
-  if (check) {
-    const i64 frac = (i64)s_lo;   // signed distance to the nearest integer, units of 2^-64
-    const u64 mag = frac < 0 ? (u64)(-frac) : (u64)frac;
-    if (mag >= (1ull << 62)) atomicOr(ctx.status, 1);
-  }
-  const u64 r_lo = s_lo + (1ull << 63);
-  const u64 r_hi = s_hi + (r_lo < s_lo ? 1ull : 0ull);
-  y1[flat] = r_hi & ctx.t_mask;
+  y1[flat] = crt_round(sum, ctx.t_mask, check, ctx.status);
 }
 
 __global__ void k_decrypt_combine(DevCtx ctx, Packing pk, Accessor ac, const u64* yres, int first, int count,

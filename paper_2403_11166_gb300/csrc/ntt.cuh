@@ -18,9 +18,19 @@
 #include <type_traits>
 #include <utility>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace pencil {
+
+// Inverse modes whose store writes shared memory (the run then synchronises the
+// CTA before its stores) and that finish with a step across the L limb CTAs of
+// one polynomial, launched as a thread-block cluster (1, L, 1).
+template <class M, class = void>
+struct ClusterLimbs : std::false_type {};
+template <class M>
+struct ClusterLimbs<M, std::void_t<decltype(M::kClusterLimbs)>> : std::bool_constant<M::kClusterLimbs> {};
 
 // Shared-memory slot of coefficient x: the low four index bits are XOR-ed with
 // (bits 4..7) ^ (bits 5..8).  8-byte accesses are served per half-warp (16
@@ -212,6 +222,7 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   __syncthreads();
   InvRounds<LOGN, C::LOGE, C::LAST_S0>::run(v, sm, tw, tau, q, q2);
   // v in [0, 2q); the mode applies N^{-1} (possibly folded into its own constant)
+  if constexpr (ClusterLimbs<Mode>::value) __syncthreads();   // the last round's reads are done
 #pragma unroll
   for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
 }
@@ -599,6 +610,7 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
     FInvRounds<LOGN, LOGE, C::SL>::run(v, sm, tw, tau, c60, c64, q2, q4);
   }
   // v < 2.26 q; the mode's store multiplies by N^{-1} (Shoup: any 64-bit input)
+  if constexpr (ClusterLimbs<Mode>::value) __syncthreads();   // the last round's reads are done
 #pragma unroll
   for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
 }
@@ -642,6 +654,7 @@ __global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FO
     k_ntt_inv(DevCtx ctx, typename Mode::Params P, int first) {
   extern __shared__ __align__(16) u64 sm[];
   inv_any<LOGN, LOGE, Mode, FOLD>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
+  if constexpr (ClusterLimbs<Mode>::value) Mode::template finish<1 << LOGN>(ctx, P, first + (int)blockIdx.x, sm);
 }
 
 // Multi-plan variants: CTA (blockIdx.x, limb) transforms polynomial items[x].y
@@ -983,6 +996,70 @@ struct ModeDecrypt {
   }
 };
 
+// DO decryption with the CRT step fused (launched as one cluster of the L limb
+// CTAs per ciphertext): each CTA leaves its residues y_j = N^{-1} qtil INTT(c0 +
+// c1 s) in its own shared memory (word e at slot e); after a cluster barrier CTA j
+// takes coefficient pairs j T + tau + i L T, reads the L residues of each through
+// distributed shared memory and writes round(t x / q) mod t to the output
+// element the coefficient carries; a second barrier keeps every CTA's shared
+// memory alive until the others have read it.  Saves the [count][L][N] residue
+// array's write and read and a launch.
+struct ModeDecryptFused {
+  static constexpr bool kHeavyLoad = true;
+  static constexpr bool kQuad = false;
+  static constexpr bool kClusterLimbs = true;
+  static constexpr int kLoadUnroll = 8;
+  static constexpr int kEpilogueUnroll = 16;
+  struct Params {
+    ModeDecrypt::Params d;   // d.out unused
+    Packing pk;              // output packing
+    Accessor ac;             // output layout
+    u64* y1;
+    int check;
+  };
+  static __device__ __forceinline__ void rebase(Params&, u64) {}
+  template <int N>
+  static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
+                                             int limb, int e) {
+    return ModeDecrypt::template load<N>(c, P.d, lc, poly, limb, e);
+  }
+  template <int N>
+  static __device__ __forceinline__ void store(const DevCtx&, const Params&, const LimbConst& lc, int, int, int e,
+                                               u64 x) {
+    extern __shared__ __align__(16) u64 sm_res[];
+    sm_res[e] = mul_shoup(x, lc.nqtil, lc.nqtils, lc.q);   // N^{-1} qtil
+  }
+  template <int N>
+  static __device__ __forceinline__ void finish(const DevCtx& c, const Params& P, int poly, u64* sm) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();   // every limb's residues are in its CTA's shared memory
+    const int T = (int)blockDim.x;
+    const int L = c.L;
+    const ulonglong2* res[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      res[j] = reinterpret_cast<const ulonglong2*>(j < L ? cl.map_shared_rank(sm, j) : sm);
+    // coefficient pairs (2 p, 2 p + 1): 16-byte remote loads
+#pragma unroll 2
+    for (int p = (int)blockIdx.y * T + (int)threadIdx.x; p < N / 2; p += L * T) {
+      const i64 f0 = out_index(P.pk, P.ac, poly, 2 * p), f1 = out_index(P.pk, P.ac, poly, 2 * p + 1);
+      if (f0 < 0 && f1 < 0) continue;
+      CrtSum s0{0, 0}, s1{0, 0};
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < L) {
+          const ulonglong2 y = res[j][p];
+          crt_add(s0, y.x, c.limb[j]);
+          crt_add(s1, y.y, c.limb[j]);
+        }
+      if (f0 >= 0) P.y1[f0] = crt_round(s0, c.t_mask, P.check, c.status);
+      if (f1 >= 0) P.y1[f1] = crt_round(s1, c.t_mask, P.check, c.status);
+    }
+    cl.sync();   // the other CTAs have finished reading this one's shared memory
+  }
+};
+
 // MO, compact send form of returned ciphertexts: INTT(c0) and, at the
 // coefficients carrying output element flat, c0c[limb][flat] = that coefficient
 // (the rest is dropped).
@@ -1024,7 +1101,25 @@ cudaError_t launch_ntt(const DevCtx& ctx, const typename Mode::Params& P, int fi
     err = cudaFuncSetAttribute(k_ntt_inv<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
     if (err != cudaSuccess) return err;
-    k_ntt_inv<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
+    if constexpr (ClusterLimbs<Mode>::value) {
+      // the L limb CTAs of a polynomial form one cluster (portable size <= 8)
+      if (ctx.L > 8) return cudaErrorInvalidValue;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3((unsigned)C::T);
+      cfg.dynamicSmemBytes = C::SMEM;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = (unsigned)ctx.L;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_ntt_inv<LOGN, LOGE, Mode, FOLD>, ctx, P, first);
+    } else {
+      k_ntt_inv<LOGN, LOGE, Mode, FOLD><<<grid, C::T, C::SMEM, s>>>(ctx, P, first);
+    }
   } else {
     err = cudaFuncSetAttribute(k_ntt_fwd<LOGN, LOGE, Mode, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM);
@@ -1038,6 +1133,7 @@ template <int LOGN, int LOGE, class Mode, bool INV, bool FOLD>
 cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps, const int2* items, long long count,
                              const u64* step, cudaStream_t s) {
   using C = KCfg<LOGN, LOGE, FOLD>;
+  if constexpr (ClusterLimbs<Mode>::value) return cudaErrorNotSupported;   // single-plan launches only
   if (count <= 0) return cudaSuccess;
   if (count > 2147483647ll) return cudaErrorInvalidValue;
   cudaError_t err;
@@ -1073,7 +1169,8 @@ cudaError_t launch_ntt_multi(const DevCtx& ctx, const typename Mode::Params* Ps,
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModePkU, false, FOLD)       \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeEncryptPk, false, FOLD) \
   PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeCompact, true, FOLD)    \
-  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true, FOLD)
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecrypt, true, FOLD)     \
+  PENCIL_NTT_INST1(SPEC, LOGN, LOGE, ModeDecryptFused, true, FOLD)
 // Radix 2^4 and 2^5 register blocks for one N and one engine.
 #define PENCIL_NTT_INSTANTIATE(SPEC, LOGN, FOLD) \
   PENCIL_NTT_INST_E(SPEC, LOGN, 4, FOLD)         \
