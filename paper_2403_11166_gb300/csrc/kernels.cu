@@ -333,24 +333,13 @@ __device__ __forceinline__ void mbar_arrive(u32 bar) {
 // Warp-specialised: warps 0 .. MAC_BT/32 - 1 multiply (thread = slot), the last
 // warp's lane 0 produces.  full[s] completes when stage s holds its block (byte
 // count), empty[s] when the MAC_BT/32 consumer warps have finished reading it.
-// A stage holds KB consecutive input blocks (two where a block's rows are few,
-// halving the waits, votes and arrivals per block); NS stages.
-template <int NT, bool DUAL>
-struct BulkCfg {
-  static constexpr int W = MacRing<NT, DUAL>::W;   // rows per block
-  static constexpr int KB = W <= 8 ? 2 : 1;
-  static constexpr int NS = KB == 2 ? 3 : MAC_BSTAGES;
-  static constexpr size_t SMEM = (size_t)NS * KB * W * MAC_BT * sizeof(u64);
-};
-
 template <int NT, bool DUAL>
 __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams P) {
-  using BC = BulkCfg<NT, DUAL>;
-  constexpr int W = BC::W, KB = BC::KB, NS = BC::NS;
+  constexpr int W = MacRing<NT, DUAL>::W;   // rows per stage
   constexpr u32 ROW = MAC_BT * sizeof(u64);
   constexpr int CONSUMER_WARPS = MAC_BT / 32;
-  extern __shared__ __align__(128) u64 ring[];   // [NS][KB][W][MAC_BT]
-  __shared__ __align__(8) u64 full[NS], empty[NS];
+  extern __shared__ __align__(128) u64 ring[];   // [MAC_BSTAGES][W][MAC_BT]
+  __shared__ __align__(8) u64 full[MAC_BSTAGES], empty[MAC_BSTAGES];
   const int ntiles = (P.NC + NT - 1) / NT;
   const int m = blockIdx.x / ntiles + P.m_base;
   const int n0 = (blockIdx.x % ntiles) * NT;
@@ -360,7 +349,7 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   const int nn = min(NT, P.NC - n0);
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < NS; ++st) {
+    for (int st = 0; st < MAC_BSTAGES; ++st) {
       mbar_init(smem_u32(&full[st]), 1);
       mbar_init(smem_u32(&empty[st]), CONSUMER_WARPS);
     }
@@ -370,18 +359,14 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   if (tid >= MAC_BT) {   // producer warp
     if (tid != MAC_BT) return;
     const bool has_p = DUAL || P.p0 != nullptr;
-    const u32 block_bytes = (u32)(has_p ? W : W - 1) * ROW;
-    const int ng = (P.K + KB - 1) / KB;
-    int g = 0;
-    for (; g < ng; ++g) {
-      const int st = g % NS;
-      if (g >= NS && !mbar_wait_bounded(smem_u32(&empty[st]), (u32)(g / NS - 1) & 1u)) break;
+    const u32 stage_bytes = (u32)(has_p ? W : W - 1) * ROW;
+    int k = 0;
+    for (; k < P.K; ++k) {
+      const int st = k % MAC_BSTAGES;
+      if (k >= MAC_BSTAGES && !mbar_wait_bounded(smem_u32(&empty[st]), (u32)(k / MAC_BSTAGES - 1) & 1u)) break;
       const u32 bar = smem_u32(&full[st]);
-      const int nb = min(KB, P.K - g * KB);
-      mbar_expect_tx(bar, (u32)nb * block_bytes);
-      for (int kk = 0; kk < nb; ++kk) {
-      const int k = g * KB + kk;
-      const u32 dst = smem_u32(ring + ((size_t)st * KB + kk) * W * MAC_BT);
+      const u32 dst = smem_u32(ring + (size_t)st * W * MAC_BT);
+      mbar_expect_tx(bar, stage_bytes);
       const size_t mk = (size_t)m * P.K + k;
       bulk_g2s(dst, P.a0 + mk * P.a0_stride + lane0, ROW, bar);
       bulk_g2s(dst + ROW, P.a1 + mk * P.a1_stride + lane0, ROW, bar);
@@ -398,11 +383,11 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
           bulk_g2s(dst + (3 + 2 * NT + j) * ROW, P.cb1 + kn * P.cb_stride + lane0, ROW, bar);
         }
       }
-      }
     }
-    if (g < ng) {   // consumers stopped releasing stages: record it, let the issued copies land
+    if (k < P.K) {   // consumers stopped releasing stages: record it, let the issued copies land
       atomicOr(ctx.status, 2);
-      for (int gg = max(0, g - NS); gg < g; ++gg) mbar_wait_bounded(smem_u32(&full[gg % NS]), (u32)(gg / NS) & 1u);
+      for (int kk = max(0, k - MAC_BSTAGES); kk < k; ++kk)
+        mbar_wait_bounded(smem_u32(&full[kk % MAC_BSTAGES]), (u32)(kk / MAC_BSTAGES) & 1u);
     }
     return;
   }
@@ -414,20 +399,14 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   Acc3 acc[NT][2];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = Acc3{0, 0, 0, 0, 0, 0};
-  const int ng = (P.K + KB - 1) / KB;
-  for (int g = 0; g < ng; ++g) {
-    const int st = g % NS;
-    const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u32)(g / NS) & 1u);
+  for (int k = 0; k < P.K; ++k) {
+    const int st = k % MAC_BSTAGES;
+    const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u32)(k / MAC_BSTAGES) & 1u);
     if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform give-up
       if ((tid & 31) == 0) atomicOr(ctx.status, 2);   // the producer then times out on this warp's stages
       return;
     }
-    const int nb = min(KB, P.K - g * KB);
-#pragma unroll
-    for (int kk = 0; kk < KB; ++kk) {
-    if (kk >= nb) break;
-    const int k = g * KB + kk;
-    const u64* cur = ring + ((size_t)st * KB + kk) * W * MAC_BT + tid;
+    const u64* cur = ring + (size_t)st * W * MAC_BT + tid;
     u64 a0 = cur[0];
     if (!DUAL && P.p0) a0 = add_mod(a0, cur[2 * MAC_BT], lc.q);   // Alg. 1 step 2: + NTT(Delta x0)
     const u64 a1 = cur[MAC_BT];
@@ -441,10 +420,8 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
         c1w[j] = cur[(3 + 2 * NT + j) * MAC_BT];
       }
     }
-    if (kk == nb - 1) {
-      __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
-    }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
     const u32 a0L = (u32)a0 & M30, a0H = (u32)(a0 >> 30);
     const u32 a1L = (u32)a1 & M30, a1H = (u32)(a1 >> 30);
     const u32 pL = (u32)pa & M30, pH = (u32)(pa >> 30);
@@ -483,7 +460,6 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
         fold3(acc[j][0], c60, c64);
         fold3(acc[j][1], c60, c64);
       }
-    }
     }
   }
   const size_t ln = (size_t)P.lanes;
@@ -709,7 +685,8 @@ static cudaError_t launch_mac_bulk(const DevCtx& ctx, const MacParams& P0, bool 
   const int ntiles = (P.NC + NT - 1) / NT;
   const unsigned gy = (unsigned)(P.lanes / MAC_BT);
   const int mchunk = max(1, 2147483647 / max(1, ntiles));
-  const size_t smem = dual ? BulkCfg<NT, true>::SMEM : BulkCfg<NT, false>::SMEM;
+  const size_t smem = (size_t)MAC_BSTAGES * (dual ? MacRing<NT, true>::W : MacRing<NT, false>::W) * MAC_BT *
+                      sizeof(u64);
   const void* fn = dual ? (const void*)k_mac_bulk<NT, true> : (const void*)k_mac_bulk<NT, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
