@@ -260,8 +260,23 @@ struct FCfg {
   static constexpr int MIN_BLOCKS = (T <= 512 && 2 * SMEM <= 227 * 1024) ? 2 : 1;
 };
 
+// Barrier between two shared-memory phases: the warp's own when every slot the
+// following phase touches was last touched by the same warp, the CTA's otherwise.
+template <bool WARP_LOCAL>
+__device__ __forceinline__ void phase_sync() {
+  if constexpr (WARP_LOCAL)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
 // Round S0 of the fold engine: K stages on G groups of 2^K words per thread;
 // group gg of thread tau is at positions base + l 2^LOGD, slot ph(base) + ph(l 2^LOGD).
+// A round is warp-local (kLocal) when warp w reads and writes only the 32 E
+// consecutive positions [32 E w, 32 E (w + 1)): full rounds with LOGD <= 5, and
+// the last (partial) round, whose G groups per thread are numbered warp by warp
+// (group 32 G w + 32 gg + lane) for that purpose.  Between two warp-local phases
+// the exchange through shared memory needs only __syncwarp.
 template <int LOGN, int LOGE, int S0>
 struct FRound {
   static constexpr int K = (LOGN - S0) < LOGE ? (LOGN - S0) : LOGE;
@@ -269,8 +284,16 @@ struct FRound {
   static constexpr int LOGD = LOGN - S0 - K;
   static constexpr int T = (1 << LOGN) >> LOGE;
   static constexpr int E = 1 << LOGE;
+  static constexpr bool kLocal = (K < LOGE) || (LOGD <= 5);
+  static_assert(T % 32 == 0, "whole warps");
+  static_assert(K == LOGE || LOGD == 0, "only the last round is partial");
 
-  static __device__ __forceinline__ int grp(int tau, int gg) { return gg * T + tau; }
+  static __device__ __forceinline__ int grp(int tau, int gg) {
+    if constexpr (G == 1)
+      return tau;
+    else
+      return ((tau >> 5) << (5 + LOGE - K)) + (gg << 5) + (tau & 31);
+  }
   static __device__ __forceinline__ int base(int tau, int gg) {
     const int g = grp(tau, gg);
     return ph(((g >> LOGD) << (LOGD + K)) + (g & ((1 << LOGD) - 1)));
@@ -374,9 +397,9 @@ struct FFwdRounds {
     Rd::fwd(v, tw, tau, c60, c64, q2);
 #pragma unroll
     for (int l = 0; l < (1 << LOGE); ++l) v[l] = fold60(v[l], c60);
-    if constexpr (S0 > 0) __syncthreads();   // every thread has read the previous layout
+    if constexpr (S0 > 0) phase_sync<Rd::kLocal>();   // every reader of these slots is done
     Rd::store(v, sm, tau);
-    __syncthreads();
+    phase_sync<Rd::kLocal>();   // the following rounds are warp-local once this one is
     if constexpr (S0 + LOGE < FCfg<LOGN, LOGE>::SL) FFwdRounds<LOGN, LOGE, S0 + LOGE>::run(v, sm, tw, tau, c60, c64, q2);
   }
 };
@@ -391,9 +414,9 @@ struct FInvRounds {
     Rd::load(v, sm, tau);
     Rd::inv(v, tw, tau, c60, c64, q2, q4);
     if constexpr (S0 > 0) {
-      __syncthreads();
+      phase_sync<Rd::kLocal>();
       Rd::store(v, sm, tau);
-      __syncthreads();
+      phase_sync<Rd::kLocal && FRound<LOGN, LOGE, S0 - LOGE>::kLocal>();
       FInvRounds<LOGN, LOGE, S0 - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
     }
   }
@@ -481,7 +504,7 @@ __device__ __forceinline__ void fold_sparse_head(const DevCtx& ctx, const typena
   for (int l = 0; l < C::E; ++l) v[l] = fold60(v[l], c60);
   __syncthreads();   // every thread has read the prologue values
   R1::store(v, sm, tau);
-  __syncthreads();
+  phase_sync<R1::kLocal>();
   if constexpr (2 * LOGE < C::SL) FFwdRounds<LOGN, LOGE, 2 * LOGE>::run(v, sm, tw, tau, c60, c64, q2);
 }
 
@@ -524,9 +547,11 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
     // W = 2^KL, gathered in fours for modes that store four coefficients at a time
     constexpr int W = 1 << C::KL;
     constexpr int GW = (Mode::kQuad && W < 4) ? 4 : W;
+    // group k = 32 (E / GW) w + 32 j + lane: warp w's own positions [32 E w, 32 E (w + 1))
+    const int kbase = (tau >> 5) * (32 * C::E / GW) + (tau & 31);
 #pragma unroll(Mode::kEpilogueUnroll)
     for (int j = 0; j < C::E / GW; ++j) {
-      const int k = j * C::T + tau;
+      const int k = kbase + 32 * j;
       u64 u[GW];
       const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(k * GW));
 #pragma unroll
@@ -552,13 +577,16 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
     Rd::fwd(v, tw, tau, c60, c64, q2);
 #pragma unroll
     for (int l = 0; l < C::E; ++l) v[l] = csub(fold60(v[l], c60), q);
-    __syncthreads();
+    static_assert(Rd::kLocal, "the last round is warp-local");
+    __syncwarp();
     Rd::store(v, sm, tau);
-    __syncthreads();
+    __syncwarp();
+    // the epilogue's groups are warp w's own positions [32 E w, 32 E (w + 1))
+    const int wbase = (tau >> 5) * 32 * C::E, lane = tau & 31;
     if constexpr (Mode::kQuad) {
 #pragma unroll(Mode::kEpilogueUnroll)
       for (int l = 0; l < C::E / 4; ++l) {
-        const int e = 4 * (tau + l * C::T);
+        const int e = wbase + 4 * (lane + 32 * l);
         const ulonglong2* b = reinterpret_cast<const ulonglong2*>(sm + ph(e));
         const ulonglong2 x01 = b[0], x23 = b[1];
         u64 x[4] = {x01.x, x01.y, x23.x, x23.y};
@@ -567,7 +595,7 @@ __device__ __forceinline__ void ntt_fwd_run_fold(const DevCtx& ctx, const typena
     } else {
 #pragma unroll(Mode::kEpilogueUnroll)
       for (int l = 0; l < C::E / 2; ++l) {
-        const int e = 2 * (tau + l * C::T);
+        const int e = wbase + 2 * (lane + 32 * l);
         const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(sm + ph(e));
         Mode::template store2<C::N>(ctx, P, lc, poly, limb, e, x.x, x.y);
       }
@@ -587,9 +615,11 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
   u64 v[C::E];
   if constexpr (C::FUSE) {
     constexpr int W = 1 << C::KL;
+    // group g = 32 (E / W) w + 32 j + lane: warp w's own positions [32 E w, 32 E (w + 1))
+    const int gbase = (tau >> 5) * (32 * C::E / W) + (tau & 31);
 #pragma unroll(Mode::kLoadUnroll)
     for (int j = 0; j < (C::E >> C::KL); ++j) {
-      const int g = j * C::T + tau;
+      const int g = gbase + 32 * j;
       u64 u[W];
 #pragma unroll
       for (int i = 0; i < W; ++i) u[i] = Mode::template load<C::N>(ctx, P, lc, poly, limb, g * W + i);
@@ -598,15 +628,23 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
 #pragma unroll
       for (int i = 0; i < W / 2; ++i) b[i] = make_ulonglong2(u[2 * i], u[2 * i + 1]);
     }
-    __syncthreads();
-    if constexpr (C::SL > 0) FInvRounds<LOGN, LOGE, C::SL - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+    if constexpr (C::SL > 0) {
+      phase_sync<FRound<LOGN, LOGE, C::SL - LOGE>::kLocal>();
+      FInvRounds<LOGN, LOGE, C::SL - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+    } else {
+      __syncthreads();
+    }
   } else {
+    // warp w loads its own positions [32 E w, 32 E (w + 1)), which the first
+    // (warp-local) inverse round reads
+    const int wbase = (tau >> 5) * 32 * C::E + (tau & 31);
 #pragma unroll(Mode::kLoadUnroll)
     for (int l = 0; l < C::E; ++l) {
-      const int e = tau + l * C::T;
+      const int e = wbase + 32 * l;
       sm[ph(e)] = Mode::template load<C::N>(ctx, P, lc, poly, limb, e);
     }
-    __syncthreads();
+    static_assert(FRound<LOGN, LOGE, C::SL>::kLocal, "the last round is warp-local");
+    __syncwarp();
     FInvRounds<LOGN, LOGE, C::SL>::run(v, sm, tw, tau, c60, c64, q2, q4);
   }
   // v < 2.26 q; the mode's store multiplies by N^{-1} (Shoup: any 64-bit input)
