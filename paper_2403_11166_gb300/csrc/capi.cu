@@ -342,6 +342,18 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
     lc.nqtil = mulmod(lc.ninv, lc.qtil, q);
     lc.nqtils = shoup(lc.nqtil, q);
     lc.a_max = (u64)((((u128)1) << 64) / q * q - 1);
+    {
+      const u64 w1 = powmod(psi_inv, brv(1u, p.log_n), q);   // the last inverse stage's twiddle
+      const u64 ks[2] = {lc.ninv, lc.nqtil};
+      u64* dst[2] = {lc.sc_ninv, lc.sc_nqtil};
+      for (int i = 0; i < 2; ++i) {
+        const u64 wk = mulmod(w1, ks[i], q);
+        dst[i][0] = ks[i];
+        dst[i][1] = (u64)((((u128)ks[i]) << 32) % q);
+        dst[i][2] = wk;
+        dst[i][3] = (u64)((((u128)wk) << 32) % q);
+      }
+    }
   }
   {   // q_total mod t (t = 2^t_bits divides 2^64: the product of the primes mod 2^64, masked)
     u64 qt = 1;

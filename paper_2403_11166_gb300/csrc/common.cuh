@@ -24,6 +24,11 @@ struct LimbConst {
   u64 c60, c64;      // 2^60 mod q and 2^64 mod q                 (split multiply-accumulate folds)
   u64 nqtil, nqtils; // N^{-1} qtil mod q_j                       (INTT scaling folded into the CRT factor)
   u64 a_max;         // floor(2^64 / q) q - 1: the largest 64-bit word accepted for a uniform residue
+  // Final scaling kappa of an inverse transform merged into its last stage (fold
+  // engine): {kappa, kappa 2^32, w1 kappa, w1 kappa 2^32} mod q, w1 = psi^-brv(1)
+  // the one twiddle of that stage; kappa = N^{-1} (sc_ninv) or N^{-1} qtil (sc_nqtil).
+  u64 sc_ninv[4];
+  u64 sc_nqtil[4];
 };
 
 struct DevCtx {

@@ -24,6 +24,11 @@
 
 namespace pencil {
 
+// Final scaling of an inverse transform, applied by the engine (the mode's store
+// receives the canonical scaled coefficient): N^{-1}, or N^{-1} qtil for
+// decryption (the CRT factor folded in).
+enum class InvScale { kNinv, kNqtil };
+
 // Inverse modes whose store writes shared memory (the run then synchronises the
 // CTA before its stores) and that finish with a step across the L limb CTAs of
 // one polynomial, launched as a thread-block cluster (1, L, 1).
@@ -221,10 +226,13 @@ __device__ __forceinline__ void ntt_inv_run(const DevCtx& ctx, const typename Mo
   }
   __syncthreads();
   InvRounds<LOGN, C::LOGE, C::LAST_S0>::run(v, sm, tw, tau, q, q2);
-  // v in [0, 2q); the mode applies N^{-1} (possibly folded into its own constant)
+  // v in [0, 2q); scaled here by the mode's kappa (N^{-1}, possibly with its own constant folded in)
   if constexpr (ClusterLimbs<Mode>::value) __syncthreads();   // the last round's reads are done
+  const bool ninv = Mode::kInvScale == InvScale::kNinv;
+  const u64 kap = ninv ? lc.ninv : lc.nqtil, kaps = ninv ? lc.ninvs : lc.nqtils;
 #pragma unroll
-  for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
+  for (int l = 0; l < C::E; ++l)
+    Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, mul_shoup(v[l], kap, kaps, q));
 }
 
 // ------------------------------------------------------------------ pseudo-Mersenne engine
@@ -361,9 +369,30 @@ struct FRound {
                                                  const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
     (fwd_stage<J>(v, tw, tau, c60, c64, q2), ...);
   }
+  // Round 0 of the inverse with the transform's final scaling kappa merged into
+  // its last stage (global stage 0, whose butterflies all use w1 = tw[1]):
+  //   x' = (x + y) kappa,  y' = (x - y + cq) (w1 kappa),  both < 1.13 q,
+  // N / 2 products instead of the stage's N / 2 and the N of a separate scaling.
+  // sc = {kappa, kappa 2^32, w1 kappa, w1 kappa 2^32} mod q.
+  static __device__ __forceinline__ void inv_scaled(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64,
+                                                    u64 q2, u64 q4, const u64* sc) {
+    static_assert(S0 == 0 && G == 1 && K == LOGE, "the first round, full");
+    inv_seq(std::make_integer_sequence<int, K - 1>{}, v, tw, tau, c60, c64, q2, q4, 1);
+    constexpr bool odd = ((LOGN - 1) & 1) != 0;   // the subtraction constant of inverse step LOGN - 1
+    const u64 cq = odd ? q4 : q2;
+    const u64 k = sc[0], k32 = sc[1], wk = sc[2], wk32 = sc[3];
+#pragma unroll
+    for (int r = 0; r < E / 2; ++r) {
+      const u64 x = v[r], y = v[r + E / 2];
+      v[r] = mul_fold(x + y, k, k32, c60, c64);
+      v[r + E / 2] = mul_fold(x + cq - y, wk, wk32, c60, c64);
+    }
+  }
+  // Stages K - 1 .. 0 (inverse order), or K - 1 .. 1 with sizeof...(J) = K - 1.
   template <int... J>
   static __device__ __forceinline__ void inv_seq(std::integer_sequence<int, J...>, u64 (&v)[E],
-                                                 const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2, u64 q4) {
+                                                 const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2, u64 q4,
+                                                 int = 0) {
     (inv_stage<K - 1 - J>(v, tw, tau, c60, c64, q2, q4), ...);
   }
   static __device__ __forceinline__ void fwd(u64 (&v)[E], const ulonglong2* tw, int tau, u32 c60, u32 c64, u64 q2) {
@@ -409,15 +438,18 @@ struct FFwdRounds {
 template <int LOGN, int LOGE, int S0>
 struct FInvRounds {
   static __device__ __forceinline__ void run(u64 (&v)[1 << LOGE], u64* sm, const ulonglong2* tw, int tau, u32 c60,
-                                             u32 c64, u64 q2, u64 q4) {
+                                             u32 c64, u64 q2, u64 q4, const u64* sc) {
     using Rd = FRound<LOGN, LOGE, S0>;
     Rd::load(v, sm, tau);
-    Rd::inv(v, tw, tau, c60, c64, q2, q4);
+    if constexpr (S0 == 0)
+      Rd::inv_scaled(v, tw, tau, c60, c64, q2, q4, sc);
+    else
+      Rd::inv(v, tw, tau, c60, c64, q2, q4);
     if constexpr (S0 > 0) {
       phase_sync<Rd::kLocal>();
       Rd::store(v, sm, tau);
       phase_sync<Rd::kLocal && FRound<LOGN, LOGE, S0 - LOGE>::kLocal>();
-      FInvRounds<LOGN, LOGE, S0 - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+      FInvRounds<LOGN, LOGE, S0 - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4, sc);
     }
   }
 };
@@ -612,6 +644,7 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
   const u64 q = lc.q, q2 = 2 * q, q4 = 4 * q;
   const u32 c60 = (u32)lc.c60, c64 = (u32)lc.c64;
   const ulonglong2* tw = ctx.tw_inv_f + (size_t)limb * C::N;
+  const u64* sc = Mode::kInvScale == InvScale::kNinv ? lc.sc_ninv : lc.sc_nqtil;
   u64 v[C::E];
   if constexpr (C::FUSE) {
     constexpr int W = 1 << C::KL;
@@ -630,7 +663,7 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
     }
     if constexpr (C::SL > 0) {
       phase_sync<FRound<LOGN, LOGE, C::SL - LOGE>::kLocal>();
-      FInvRounds<LOGN, LOGE, C::SL - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4);
+      FInvRounds<LOGN, LOGE, C::SL - LOGE>::run(v, sm, tw, tau, c60, c64, q2, q4, sc);
     } else {
       __syncthreads();
     }
@@ -645,12 +678,12 @@ __device__ __forceinline__ void ntt_inv_run_fold(const DevCtx& ctx, const typena
     }
     static_assert(FRound<LOGN, LOGE, C::SL>::kLocal, "the last round is warp-local");
     __syncwarp();
-    FInvRounds<LOGN, LOGE, C::SL>::run(v, sm, tw, tau, c60, c64, q2, q4);
+    FInvRounds<LOGN, LOGE, C::SL>::run(v, sm, tw, tau, c60, c64, q2, q4, sc);
   }
-  // v < 2.26 q; the mode's store multiplies by N^{-1} (Shoup: any 64-bit input)
+  // v < 1.13 q, already scaled by the mode's kappa in the last stage
   if constexpr (ClusterLimbs<Mode>::value) __syncthreads();   // the last round's reads are done
 #pragma unroll
-  for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, v[l]);
+  for (int l = 0; l < C::E; ++l) Mode::template store<C::N>(ctx, P, lc, poly, limb, tau + l * C::T, csub(v[l], q));
 }
 
 // Launch shape of either engine.
@@ -730,6 +763,7 @@ __device__ __forceinline__ size_t ct_off(int poly, int comp, int limb, int L, in
 
 // In-place transform of [count][L][N] polynomials.
 struct ModeRaw {
+  static constexpr InvScale kInvScale = InvScale::kNinv;
   static constexpr bool kHeavyLoad = false;
   static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 32;
@@ -751,7 +785,7 @@ struct ModeRaw {
   template <int N>
   static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
-    P.polys[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.ninv, lc.ninvs, lc.q);
+    P.polys[limb_off(poly, limb, c.L, N) + e] = x;   // x = N^{-1} INTT, canonical
   }
 };
 
@@ -1007,6 +1041,7 @@ struct ModeEncryptPk {
 // With skip_c0 (decryption of the compact send form) only c1 * s is transformed;
 // the output coefficients' c0 is added by the combine kernel.
 struct ModeDecrypt {
+  static constexpr InvScale kInvScale = InvScale::kNqtil;
   static constexpr bool kHeavyLoad = true;
   static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 8;
@@ -1030,7 +1065,7 @@ struct ModeDecrypt {
   template <int N>
   static __device__ __forceinline__ void store(const DevCtx& c, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
-    P.out[limb_off(poly, limb, c.L, N) + e] = mul_shoup(x, lc.nqtil, lc.nqtils, lc.q);   // N^{-1} qtil
+    P.out[limb_off(poly, limb, c.L, N) + e] = x;   // x = N^{-1} qtil INTT, canonical
   }
 };
 
@@ -1043,6 +1078,7 @@ struct ModeDecrypt {
 // memory alive until the others have read it.  Saves the [count][L][N] residue
 // array's write and read and a launch.
 struct ModeDecryptFused {
+  static constexpr InvScale kInvScale = InvScale::kNqtil;
   static constexpr bool kHeavyLoad = true;
   static constexpr bool kQuad = false;
   static constexpr bool kClusterLimbs = true;
@@ -1065,7 +1101,7 @@ struct ModeDecryptFused {
   static __device__ __forceinline__ void store(const DevCtx&, const Params&, const LimbConst& lc, int, int, int e,
                                                u64 x) {
     extern __shared__ __align__(16) u64 sm_res[];
-    sm_res[e] = mul_shoup(x, lc.nqtil, lc.nqtils, lc.q);   // N^{-1} qtil
+    sm_res[e] = x;   // x = N^{-1} qtil INTT, canonical
   }
   template <int N>
   static __device__ __forceinline__ void finish(const DevCtx& c, const Params& P, int poly, u64* sm) {
@@ -1102,6 +1138,7 @@ struct ModeDecryptFused {
 // coefficients carrying output element flat, c0c[limb][flat] = that coefficient
 // (the rest is dropped).
 struct ModeCompact {
+  static constexpr InvScale kInvScale = InvScale::kNinv;
   static constexpr bool kHeavyLoad = false;
   static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 16;
@@ -1123,7 +1160,7 @@ struct ModeCompact {
   static __device__ __forceinline__ void store(const DevCtx&, const Params& P, const LimbConst& lc, int poly,
                                                int limb, int e, u64 x) {
     const i64 flat = out_index(P.pk, P.ac, poly, e);
-    if (flat >= 0) P.c0c[(size_t)limb * P.out_elems + flat] = mul_shoup(x, lc.ninv, lc.ninvs, lc.q);
+    if (flat >= 0) P.c0c[(size_t)limb * P.out_elems + flat] = x;   // x = N^{-1} INTT, canonical
   }
 };
 
