@@ -364,7 +364,9 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   d.mac_staging = 1;   // measured: bulk copies by a producer warp, 4 columns per thread
   d.mac_split = 1;
   for (int j = 0; j < d.L; ++j)
-    if (qs[j] >= (1ull << 60) || d.limb[j].c60 >= (1ull << 28) || d.limb[j].c64 >= (1ull << 28)) d.mac_split = 0;
+    if (qs[j] >= (1ull << 60) || qs[j] <= (1ull << 59) + (1ull << 33) || d.limb[j].c60 >= (1ull << 28) ||
+        d.limb[j].c64 >= (1ull << 28))
+      d.mac_split = 0;   // (q > 2^59 + 2^33: the accumulator's final value, below 2^60 + 2^33, is below 2 q)
   cudaError_t e1 = cudaMalloc(&ctx->tw_fwd, tf.size() * sizeof(ulonglong2));
   cudaError_t e2 = cudaMalloc(&ctx->tw_inv, ti.size() * sizeof(ulonglong2));
   cudaError_t e3 = cudaMalloc(&ctx->status, sizeof(int));

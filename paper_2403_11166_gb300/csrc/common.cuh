@@ -45,7 +45,7 @@ struct DevCtx {
   const ulonglong2* tw_fwd_f;  // [L][N] (psi^brv(k), psi^brv(k) 2^32 mod q)   (null unless every
   const ulonglong2* tw_inv_f;  // [L][N] (psi^-brv(k), psi^-brv(k) 2^32 mod q)  q_j = 2^60 - c, c < 2^24)
   int* status;               // device status word (atomicOr of error bits)
-  int mac_split;             // 1: every q_j < 2^60 with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
+  int mac_split;             // 1: every q_j in (2^59 + 2^33, 2^60) with 2^60, 2^64 mod q_j < 2^28 (30-bit split MAC)
   int mac_nt;                // output columns per thread of the split MAC: 2, 4 or 8
   int mac_staging;           // operand staging of the split MAC: 0 per-thread cp.async ring, 1 bulk copies
   u64 q_mod_t;               // (q_total mod t): messages are scaled as round(q_total m / t)

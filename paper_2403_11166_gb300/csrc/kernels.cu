@@ -125,12 +125,14 @@ __device__ __forceinline__ void fold3(Acc3& a, u64 c60, u64 c64) {
 
 // canonical value of an accumulator.  After fold3, S0 < 2^30 and S1 < 2^35, and
 // S0 + S1 2^30 = S0 + (S1 mod 2^30) 2^30 + (S1 >> 30) 2^60 with 2^60 = c60 mod q
-// (c60 < 2^28), a sum below 2^60 + 2^33: one Barrett reduction (any q < 2^60).
+// (c60 < 2^28), a sum below 2^60 + 2^33.  The split form is used only for
+// q = 2^60 - c60 with c60 < 2^28, so that sum is below 2 q: one conditional
+// subtraction.
 __device__ __forceinline__ u64 acc3_value(Acc3 a, const LimbConst& lc) {
   fold3(a, lc.c60, lc.c64);
   const u64 s1 = ((u64)a.h1 << 32) | a.l1;
   const u64 v = (u64)a.l0 + ((s1 & ((1ull << 30) - 1)) << 30) + (u64)(u32)(s1 >> 30) * (u32)lc.c60;
-  return reduce64(v, lc);
+  return csub(v, lc.q);
 }
 
 __device__ __forceinline__ void cp_async16(u64* smem, const u64* gmem, int bytes) {
