@@ -9,7 +9,11 @@ he_linear_forward_prepare (MO: NTT(Delta <X>_0), mask s, NTT(Delta s), share
 s + b) on their own streams, and the layer streamed in row slices through
 encrypt_share (DO: pi_v + BFV encryption), he_linear_forward_apply (MO: ct x pt
 multiply-accumulate with the add of <X>_0 and the re-mask fused) and
-decrypt_to_share (DO), each slice's stages overlapping the neighbours'.  Metric:
+decrypt_to_share (DO), each slice's stages overlapping the neighbours'.  Two
+steps are in flight (double-buffered device buffers): step i + 1's encoding,
+preparation and encryption run beside step i's multiply-accumulate and
+decryption; the line also gives one step's latency with no such overlap
+(ms_per_step_unpipelined).  Metric:
 ct x pt products per second (whole job), plus the per-kernel roofline of the
 dominant kernel, an end-to-end number with host buffers, and the oracle timed
 on the host cores.
@@ -165,13 +169,17 @@ def kernel_work(name: str, S, n: int, L_: int):
     return 0.0, 0.0
 
 
-def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: dict, clocks: dict):
+def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: dict, clocks: dict,
+             unpiped: dict | None = None):
     """Dominant kernel: the largest share of a step when the step's kernels run one
     at a time (`serial`, a profiling pass on one stream after the timed region);
-    its achieved rate uses its launch duration in the timed region (`prof`, CUDA
-    events on its own stream).  Kernels that overlap others in the timed step
-    (encode / preparation / encryption run on three streams) show longer event
-    durations there than alone."""
+    its achieved rate uses its launch duration in a timed run (CUDA events on its
+    own stream): the timed run of unpipelined steps (`unpiped`) when given, where
+    the multiply-accumulate and the decryption have the GPU to themselves, else the
+    main timed run (`prof`).  Kernels that overlap others (encode / preparation /
+    encryption on three streams; with two steps in flight, the next step's
+    transforms beside this step's multiply-accumulate and decryption) show longer
+    event durations in the main timed run than alone."""
     total = sum(v[1] for v in serial.values()) or 1.0
     table = {}
     for name, (launches, ms) in prof.items():
@@ -179,7 +187,9 @@ def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: di
         per = ms / max(1, launches) * 1e-3
         sl, sms = serial.get(name, (0, 0.0))
         alone = sms / max(1, sl) * 1e-3 if sl else None
+        ul, ums = (unpiped or {}).get(name, (0, 0.0))
         table[name] = {"launches": launches, "ms_per_launch": per * 1e3,
+                       "ms_per_launch_unpipelined": ums / ul if ul else None,
                        "ms_per_launch_alone": alone * 1e3 if alone else None,
                        "share_alone": sms / total,
                        "tmul_per_s": mults / per / 1e12 if mults else None,
@@ -189,11 +199,13 @@ def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: di
                        "frac_alu_alone": round(mults / alone / 1e12 / peaks["alu_tmul"], 4) if mults and alone else None}
     dom = max((k for k in table if kernel_work(k, S, n, L_)[0] > 0), key=lambda k: table[k]["share_alone"])
     mults, byts = kernel_work(dom, S, n, L_)
-    per = table[dom]["ms_per_launch"] * 1e-3
+    timed = "unpipelined timed run" if table[dom]["ms_per_launch_unpipelined"] else "timed run"
+    per = (table[dom]["ms_per_launch_unpipelined"] or table[dom]["ms_per_launch"]) * 1e-3
     alu_peak = peaks["alu_tmul"]
     achieved = mults / per / 1e12
     return dom, table, {
         "kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 3),
+        "duration_from": timed, "ms_per_launch": round(per * 1e3, 5),
         "unit": "T 32-bit mult/s", "frac": round(achieved / alu_peak, 4), "traffic": ncu_traffic(dom),
         "peak_source": peaks["alu_source"],
         "hbm": {"achieved_gbs": round(byts / per / 1e9, 1), "peak_gbs": peaks["hbm_gbs"],
@@ -1222,47 +1234,82 @@ def run_ours(args):
     # while the DO encrypts its share.  The layer then streams through the rest
     # of the protocol in `chunks` slices of its output rows (batch blocks): the
     # MO's multiply-accumulate of slice c overlaps the DO's encryption of slice
-    # c + 1 and the DO's decryption of slice c - 1.  Streams fork from and join
-    # back into the launch stream inside every step.
+    # c + 1 and the DO's decryption of slice c - 1.  A timed run of steps forks
+    # the step streams from the launch stream once and joins them at its end.
     M_rows = plan.rows
     nch = max(1, min(args.chunks, M_rows))
     bounds = [M_rows * c // nch for c in range(nch + 1)]
     slices = [plan.slice(bounds[c], bounds[c + 1] - bounds[c]) for c in range(nch)] if nch > 1 else [plan]
     mo_enc, mo_prep, mo_app = (torch.cuda.Stream(device=dev) for _ in range(3))
     do_dec = torch.cuda.Stream(device=dev)
-    fork, join_enc, join_prep = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
-    ev_ct = [torch.cuda.Event() for _ in slices]
-    ev_out = [torch.cuda.Event() for _ in slices]
-    join_app, join_dec = torch.cuda.Event(), torch.cuda.Event()
+    streams = (mo_enc, mo_prep, stream, mo_app, do_dec)
+    fork = torch.cuda.Event()
+    # Two steps in flight: step i works in device buffer set i % 2 (plaintexts,
+    # input and output ciphertexts, the MO's prepared terms) and writes the shares
+    # of input set i % 2, so step i + 1's encoding, preparation and encryption run
+    # while step i multiplies and decrypts.  Step i + 2 reuses set i % 2 only after
+    # step i's multiply-accumulate (for pt, ct_in, the prepared terms) and
+    # decryption (for ct_out) are done with it.
+    work = [{"pt": pt, "ct_in": ct_in, "ct_out": ct_out, "ws_mo": ws_mo},
+            {"pt": plan.new_pt(S.pt), "ct_in": plan.new_ct(S.ct_in), "ct_out": plan.new_ct(S.ct_out),
+             "ws_mo": plan.new_ws(S.ws_forward)}]
+    evs = [{"enc": torch.cuda.Event(), "prep": torch.cuda.Event(), "ct": [torch.cuda.Event() for _ in slices],
+            "out": [torch.cuda.Event() for _ in slices], "app": torch.cuda.Event(), "dec": torch.cuda.Event()}
+           for _ in range(2)]
+    used = [False, False]
 
-    def step(i, b=None):
-        b = d if b is None else b
+    def begin():
+        """Every step stream starts after the work already on the launch stream."""
         fork.record(stream)
-        for st in (mo_enc, mo_prep, mo_app, do_dec):
+        for st in streams:
             st.wait_event(fork)
-        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, b["W"], pt, stream=mo_enc)
-        join_enc.record(mo_enc)
-        he.he_linear_forward_prepare(ctx, plan, b["x0"], b["bias"], 5000 + i, b["y0"], ws_mo, stream=mo_prep)
-        join_prep.record(mo_prep)
-        for c, sl in enumerate(slices):            # DO: encrypt slice by slice
-            he.encrypt_share(ctx, sk, sl, he.OPERAND_INPUT, b["x1"], 1000 + i, ct_in, ws, stream=stream)
-            ev_ct[c].record(stream)
-        mo_app.wait_event(join_enc)
-        mo_app.wait_event(join_prep)
-        for c, sl in enumerate(slices):            # MO: multiply-accumulate each slice as it arrives
-            mo_app.wait_event(ev_ct[c])
-            he.he_linear_forward_apply(ctx, sl, ct_in, pt, ct_out, ws_mo, stream=mo_app)
-            ev_out[c].record(mo_app)
-        for c, sl in enumerate(slices):            # DO: decrypt each slice as it comes back
-            do_dec.wait_event(ev_out[c])
-            he.decrypt_to_share(ctx, sk, sl, ct_out, b["y1"], False, ws_dec, stream=do_dec)
-        join_dec.record(do_dec)
-        stream.wait_event(join_dec)
 
+    def end(i):
+        """The launch stream waits for step i (and so for every earlier step)."""
+        stream.wait_event(evs[i % 2]["dec"])
+
+    def step(i, b=None, serial=False, wait_in=None):
+        p = i % 2
+        b = sets[p] if b is None else b
+        w, e = work[p], evs[p]
+        if serial:
+            begin()
+        if used[p]:   # step i - 2 is done with this buffer set
+            for st in (mo_enc, mo_prep, stream):
+                st.wait_event(e["app"])
+            mo_app.wait_event(e["dec"])
+        if wait_in is not None:   # this step's inputs have been copied in
+            for st in (mo_enc, mo_prep, stream):
+                st.wait_event(wait_in)
+        he.encode_weights(ctx, plan, he.OPERAND_KERNEL, b["W"], w["pt"], stream=mo_enc)
+        e["enc"].record(mo_enc)
+        he.he_linear_forward_prepare(ctx, plan, b["x0"], b["bias"], 5000 + i, b["y0"], w["ws_mo"], stream=mo_prep)
+        e["prep"].record(mo_prep)
+        for c, sl in enumerate(slices):            # DO: encrypt slice by slice
+            he.encrypt_share(ctx, sk, sl, he.OPERAND_INPUT, b["x1"], 1000 + i, w["ct_in"], ws, stream=stream)
+            e["ct"][c].record(stream)
+        mo_app.wait_event(e["enc"])
+        mo_app.wait_event(e["prep"])
+        for c, sl in enumerate(slices):            # MO: multiply-accumulate each slice as it arrives
+            mo_app.wait_event(e["ct"][c])
+            he.he_linear_forward_apply(ctx, sl, w["ct_in"], w["pt"], w["ct_out"], w["ws_mo"], stream=mo_app)
+            e["out"][c].record(mo_app)
+        e["app"].record(mo_app)
+        for c, sl in enumerate(slices):            # DO: decrypt each slice as it comes back
+            do_dec.wait_event(e["out"][c])
+            he.decrypt_to_share(ctx, sk, sl, w["ct_out"], b["y1"], False, ws_dec, stream=do_dec)
+        e["dec"].record(do_dec)
+        used[p] = True
+        if serial:
+            end(i)
+
+    begin()
     for i in range(args.warmup):
         step(i)
+    end(args.warmup - 1)
     torch.cuda.synchronize()
     # self-check: reconstruction equals the plaintext convolution (exact in float64)
+    y0, y1 = sets[(args.warmup - 1) % 2]["y0"], sets[(args.warmup - 1) % 2]["y1"]
     rec = ((y0 + y1) & ((1 << T_BITS) - 1)).view(LAYER["batch"], LAYER["c_out"], LAYER["h"], LAYER["w"])
     rec = torch.where(rec >= (1 << (T_BITS - 1)), rec - (1 << T_BITS), rec).double()
     ref = F.conv2d(torch.from_numpy(x).double().to(dev), torch.from_numpy(W).double().to(dev),
@@ -1291,8 +1338,10 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     t_issue = time.perf_counter()
+    begin()
     for i in range(args.steps):
         step(args.warmup + i)
+    end(args.warmup + args.steps - 1)
     t_issue = time.perf_counter() - t_issue   # host time to issue the steps (the GPU runs behind it)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -1302,6 +1351,19 @@ def run_ours(args):
     ck = clocks.stop()
     ctx.profile(False)
     prof = ctx.profile_read()
+    # the same steps with no overlap between consecutive steps (each step's streams
+    # fork from and join back into the launch stream): the latency of one step
+    torch.cuda.synchronize()
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    u0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, serial=True)
+    u1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial = u0.elapsed_time(u1)
+    ctx.profile(False)
+    unpiped = ctx.profile_read()
     # serial profiling pass (not timed): the same steps with every kernel on the launch stream
     ctx.profile(True)
     for i in range(3):
@@ -1371,18 +1433,19 @@ def run_ours(args):
         ev_in[b].record(copy_in)
 
     h2d_into(0)
+    begin()
     for i in range(args.steps):
         b = i % 2
         if i + 1 < args.steps:
             if i >= 1:
                 copy_in.wait_event(ev_done[1 - b])   # step i - 1 (and its copy out) has finished with that set
             h2d_into(1 - b)
-        stream.wait_event(ev_in[b])
-        step(10_000 + i, sets[b])
-        copy_out.wait_event(_record(stream))
+        step(10_000 + i, sets[b], wait_in=ev_in[b])   # (work set and input set: both i % 2)
+        copy_out.wait_event(evs[b]["dec"])
         timed_copy(copy_out, lambda: (hy0.copy_(sets[b]["y0"], non_blocking=True),
                                       hy1.copy_(sets[b]["y1"], non_blocking=True)))
         ev_done[b].record(copy_out)
+    end(10_000 + args.steps - 1)
     ev_copied.record(copy_out)
     stream.wait_event(ev_copied)
     stream.wait_event(_record(copy_in))
@@ -1391,10 +1454,10 @@ def run_ours(args):
     ms_e2e = f0.elapsed_time(f1)
     copy_ms = sum(a.elapsed_time(b_) for a, b_ in cp_ev) / args.steps
     copy_gbs = (h2d + d2h) / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None
-    ms, ms_e2e = max_over_ranks([ms, ms_e2e], world, dev)
+    ms, ms_e2e, ms_serial = max_over_ranks([ms, ms_e2e, ms_serial], world, dev)
     value = job_throughput(S.products, args.steps, world, ms)
     peaks = load_peaks(sms)
-    dom, table, roof = roofline(prof, serial, S, ctx.n, ctx.L, args.steps, peaks, ck)
+    dom, table, roof = roofline(prof, serial, S, ctx.n, ctx.L, args.steps, peaks, ck, unpiped)
     roof["probe"] = {"imad32_T_per_s": round(probe["imad32"], 3), "shoup64_T_per_s": round(probe["shoup64"], 3),
                      "madwide32_T_per_s": round(probe["madwide32"], 3), "mac128_T_per_s": round(probe["mac128"], 3),
                      "note": f"register-only chains, 8 per thread, {sms * 8} x 256 threads, measured before the timed region"}
@@ -1407,13 +1470,16 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        # two steps in flight (step i + 1's encoding, preparation and encryption overlap step i's
+        # multiply-accumulate and decryption); one step alone, streams joined after every step:
+        "ms_per_step_unpipelined": round(ms_serial / args.steps, 4),
         "dtype": "u64 (RNS mod q_i), u64 mod 2^41", "data": "synthetic",
         "config": {"workload": WORKLOAD, "partition": dict(zip(("bb", "cib", "cob", "th", "tw", "kth", "ktw"),
                                                             plan.part)),
                    "ct_in": S.ct_in, "pt": S.pt, "ct_out": S.ct_out, "products_per_step": S.products,
                    "l2": "inputs larger than L2 (ct_in %.0f MB per step)" % (S.ct_in * S.ct_words * 8 / 1e6),
                    "parallelism": f"replicas x{world} (independent layers, no collective)",
-                   "streamed_slices": nch},
+                   "streamed_slices": nch, "steps_in_flight": 2},
         "parity_selfcheck": parity_ok,
         "host_issue_ms_per_step": round(t_issue * 1e3 / args.steps, 4),
         "roofline": roof,

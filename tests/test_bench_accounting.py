@@ -43,6 +43,27 @@ def test_roofline_picks_the_largest_serial_share_and_divides_by_its_launch_time(
     assert table["mask_poly"]["share_alone"] == pytest.approx(1.5 / total)
 
 
+def test_roofline_rate_from_the_unpipelined_run_when_given(monkeypatch):
+    """With two steps in flight a kernel's duration in the main timed run includes
+    the time it shares the GPU with the next step's kernels; the dominant kernel's
+    rate then comes from the timed run of unpipelined steps."""
+    S = SimpleNamespace(ct_in=160, pt=256, ct_out=160, products=2560)
+    prof = {"mac": (20, 20 * 0.16), "ntt_encode": (20, 20 * 0.13)}
+    serial = {"mac": (3, 3 * 0.145), "ntt_encode": (3, 3 * 0.05)}
+    unpiped = {"mac": (20, 20 * 0.144), "ntt_encode": (20, 20 * 0.051)}
+    peaks = {"alu_tmul": 20.0, "alu_source": "derived", "hbm_gbs": 6000.0}
+    monkeypatch.setattr(bench, "ncu_traffic", lambda k: None)
+    dom, table, roof = bench.roofline(prof, serial, S, 8192, 3, 20, peaks, {}, unpiped)
+    assert dom == "mac"
+    assert roof["duration_from"] == "unpipelined timed run"
+    assert roof["achieved"] == round(503316480 / 0.144e-3 / 1e12, 3)
+    assert table["mac"]["ms_per_launch"] == pytest.approx(0.16)
+    assert table["mac"]["ms_per_launch_unpipelined"] == pytest.approx(0.144)
+    dom, table, roof = bench.roofline(prof, serial, S, 8192, 3, 20, peaks, {})
+    assert roof["duration_from"] == "timed run"
+    assert roof["achieved"] == round(503316480 / 0.16e-3 / 1e12, 3)
+
+
 def test_ncu_traffic_only_for_the_recorded_sources(tmp_path, monkeypatch):
     digest = bench.csrc_digest()
     prof_dir = tmp_path / "profiles"
