@@ -295,7 +295,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   DevCtx& d = ctx->dev;
   memset(&d, 0, sizeof(d));
   d.log_n = p.log_n;
-  d.ntt_loge = p.log_n <= 13 ? 4 : 5;   // measured: radix 2^4 (two CTAs per SM) up to N = 8192
+  d.ntt_loge = p.log_n <= 13 ? 4 : 5;   // Shoup engine: radix 2^4 (two CTAs per SM) up to N = 8192
   d.n = n;
   d.L = p.num_primes;
   d.t_bits = p.t_bits;
@@ -391,6 +391,7 @@ extern "C" int pencil_ctx_create(const PencilParams* params, int device, PencilC
   d.tw_fwd_f = ctx->tw_fwd_f;
   d.tw_inv_f = ctx->tw_inv_f;
   d.ntt_arith = fold_ok ? 1 : 0;
+  if (fold_ok) d.ntt_loge = 4;   // fold engine: radix 2^4 at every N (N = 16384: 1024-thread CTAs, measured faster)
   d.status = ctx->status;
   *out = ctx;
   return PENCIL_OK;
