@@ -398,6 +398,12 @@ __global__ void __launch_bounds__(MAC_BT + 32) k_mac_bulk(DevCtx ctx, MacParams 
   const u64 c60 = lc.c60, c64 = lc.c64;
   constexpr u32 M30 = (1u << 30) - 1;
   constexpr int FOLD = DUAL ? 3 : 6;   // at most 12 products of < 2^60 per accumulator between folds
+  if (P.mask) {   // the re-mask words the store reads: into L2 now, not from DRAM at the end
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (j < nn)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P.mask + ((size_t)m * P.NC + n0 + j) * (size_t)P.lanes + lane));
+  }
   Acc3 acc[NT][2];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = Acc3{0, 0, 0, 0, 0, 0};
