@@ -235,8 +235,9 @@ __device__ __forceinline__ u64 mul_fold(u64 y, u64 w, u64 w32, u32 c60, u32 c64)
       "addc.u32 u, u, 0;\n\t"
       "shr.u32 sm, t, 28;\n\t"
       "and.b32 tl, t, 0x0FFFFFFF;\n\t"
+      "mad.lo.cc.u32 s0, sm, %4, s0;\n\t"
+      "addc.u32 tl, tl, 0;\n\t"
       "mov.b64 p, {s0, tl};\n\t"
-      "mad.wide.u32 p, sm, %4, p;\n\t"
       "mad.wide.u32 %0, u, %5, p;\n\t"
       "}"
       : "=l"(r)
@@ -259,9 +260,23 @@ __device__ __forceinline__ u64 mul_fold_c(u64 y, u64 w, u64 w32, u32 c60, u32 c6
   return (u64)(u32)(m >> 32) * c64 + t;                                                 // + sh c64
 }
 
-// v mod q, lazily: any v < 2^64 -> (v mod 2^60) + (v >> 60) c60 < 2^60 + 2^28 (< 2 q).
+// v mod q, lazily: any v < 2^64 -> (v mod 2^60) + (v >> 60) c60 < 2^60 + 2^32 (< 2 q).
+// (v >> 60) c60 < 2^32 (c60 < 2^28): a 32-bit multiply-add with carry, not a
+// 32x32->64 one (which holds the multiply pipe twice as long).
 __device__ __forceinline__ u64 fold60(u64 v, u32 c60) {
-  return (u64)(u32)(v >> 60) * c60 + (v & 0x0FFFFFFFFFFFFFFFull);
+  u64 r;
+  asm("{\n\t"
+      ".reg .u32 v0, v1, s, h;\n\t"
+      "mov.b64 {v0, v1}, %1;\n\t"
+      "shr.u32 s, v1, 28;\n\t"
+      "and.b32 h, v1, 0x0FFFFFFF;\n\t"
+      "mad.lo.cc.u32 v0, s, %2, v0;\n\t"
+      "addc.u32 h, h, 0;\n\t"
+      "mov.b64 %0, {v0, h};\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(v), "r"(c60));
+  return r;
 }
 
 // Cooley-Tukey butterfly with a lazy pseudo-Mersenne product: x, y < B q ->
