@@ -430,7 +430,11 @@ enum { PENCIL_BATCH_PT = 0, PENCIL_BATCH_CT_IN = 1, PENCIL_BATCH_CT_OUT = 2, PEN
  * launch sequence. */
 int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plans, int32_t count, PencilBatch** out);
 int pencil_batch_destroy(PencilBatch* batch);
-/* Bytes of device workspace holding every layer's plaintexts and ciphertexts. */
+/* Bytes of device workspace holding every layer's plaintexts and ciphertexts
+ * (buffers with disjoint lifetimes inside one pencil_batch_forward share
+ * memory: the mask polynomials and sampled errors sit in the output
+ * ciphertexts' region until the multiply-accumulate writes it, and the
+ * decryption residues in that of NTT(Delta x0) and NTT(Delta s)). */
 int pencil_batch_workspace(const PencilBatch* batch, int64_t* bytes);
 /* Device buffers of an Alg. 1 entry `layer` (FWD or DGRAD plan; user layouts as
  * for the per-layer calls): W, the DO's and MO's shares x1, x0 of the product's

@@ -1623,16 +1623,23 @@ extern "C" int pencil_batch_create(PencilCtx* ctx, const PencilPlan* const* plan
     o += al(P->ct_in * 2 * lnb);
     f.ct_out = o;
     o += al(P->ct_out * 2 * lnb);
-    f.err = o;
-    o += al(P->ct_in * n);
+    // Buffers whose lifetimes do not overlap share memory (the launches of a batch
+    // run in a fixed order on one stream): the mask polynomials and the sampled
+    // errors live inside the output ciphertexts' region until the
+    // multiply-accumulate writes it; the decryption residues reuse NTT(Delta x0) /
+    // <X>_0 and NTT(Delta s), which the multiply-accumulate has finished reading.
+    f.mpoly = f.ct_out;
+    if (al(P->ct_out * n * 8) + al(P->ct_in * n) <= al(P->ct_out * 2 * lnb)) {
+      f.err = f.ct_out + al(P->ct_out * n * 8);
+    } else {
+      f.err = o;
+      o += al(P->ct_in * n);
+    }
     f.p0 = o;
     o += al(P->ct_in * lnb);
     f.mnt = o;
     o += al(P->ct_out * lnb);
-    f.mpoly = o;
-    o += al(P->ct_out * n * 8);
-    f.yres = o;
-    o += al(P->ct_out * lnb);
+    f.yres = f.p0;   // ct_out lnb <= (ct_in + ct_out) lnb, the p0 and mnt regions
     f.ct_k = f.err_k = 0;
     if (P->role == PENCIL_ROLE_WGRAD) {
       f.ct_k = o;
