@@ -9,10 +9,10 @@ he_linear_forward_prepare (MO: NTT(Delta <X>_0), mask s, NTT(Delta s), share
 s + b) on their own streams, and the layer streamed in row slices through
 encrypt_share (DO: pi_v + BFV encryption), he_linear_forward_apply (MO: ct x pt
 multiply-accumulate with the add of <X>_0 and the re-mask fused) and
-decrypt_to_share (DO), each slice's stages overlapping the neighbours'.  Two
-steps are in flight (double-buffered device buffers): step i + 1's encoding,
-preparation and encryption run beside step i's multiply-accumulate and
-decryption; the line also gives one step's latency with no such overlap
+decrypt_to_share (DO), each slice's stages overlapping the neighbours'.  Three
+steps are in flight (one device buffer set each, --in-flight): step i + 1's
+encoding, preparation and encryption run beside step i's multiply-accumulate
+and decryption; the line also gives one step's latency with no such overlap
 (ms_per_step_unpipelined).  Metric:
 ct x pt products per second (whole job), plus the per-kernel roofline of the
 dominant kernel, an end-to-end number with host buffers, and the oracle timed
@@ -70,6 +70,8 @@ def parse():
                     help="force the MAC knob (0: shared-memory staged; 2, 4, 8: columns per thread)")
     ap.add_argument("--mac-staging", type=int, default=-1,
                     help="force the MAC staging knob (0: per-thread cp.async ring, 1: bulk copies by a producer warp)")
+    ap.add_argument("--in-flight", type=int, default=3,
+                    help="steps in flight in the timed runs (device buffer sets); 1: each step joins before the next")
     ap.add_argument("--chunks", type=int, default=1,
                     help="stream the layer through encrypt / multiply-accumulate / decrypt in this many row slices")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / training / large-conv workloads")
@@ -177,7 +179,7 @@ def roofline(prof: dict, serial: dict, S, n: int, L_: int, steps: int, peaks: di
     own stream): the timed run of unpipelined steps (`unpiped`) when given, where
     the multiply-accumulate and the decryption have the GPU to themselves, else the
     main timed run (`prof`).  Kernels that overlap others (encode / preparation /
-    encryption on three streams; with two steps in flight, the next step's
+    encryption on three streams; with several steps in flight, the next step's
     transforms beside this step's multiply-accumulate and decryption) show longer
     event durations in the main timed run than alone."""
     total = sum(v[1] for v in serial.values()) or 1.0
@@ -1209,10 +1211,11 @@ def run_ours(args):
 
     host = {"W": to_i64(W).pin_memory(), "x0": to_i64(x0).pin_memory(), "x1": to_i64(x1).pin_memory(),
             "bias": to_i64(bias.astype(np.uint64) & np.uint64((1 << T_BITS) - 1)).pin_memory()}
-    # two sets of per-step inputs and outputs: the end-to-end loop copies the next
-    # step's inputs in and the previous step's shares out while a step computes
+    # one set of per-step inputs and outputs per step in flight: the end-to-end loop
+    # copies the next step's inputs in and earlier steps' shares out while a step computes
+    D = args.in_flight
     sets = []
-    for _ in range(2):
+    for _ in range(D):
         b = {k: v.to(dev) for k, v in host.items()}
         b["y0"] = torch.empty(S.out_elems, dtype=torch.int64, device=dev)
         b["y1"] = torch.empty_like(b["y0"])
@@ -1244,19 +1247,19 @@ def run_ours(args):
     do_dec = torch.cuda.Stream(device=dev)
     streams = (mo_enc, mo_prep, stream, mo_app, do_dec)
     fork = torch.cuda.Event()
-    # Two steps in flight: step i works in device buffer set i % 2 (plaintexts,
+    # D steps in flight: step i works in device buffer set i % D (plaintexts,
     # input and output ciphertexts, the MO's prepared terms) and writes the shares
-    # of input set i % 2, so step i + 1's encoding, preparation and encryption run
-    # while step i multiplies and decrypts.  Step i + 2 reuses set i % 2 only after
+    # of input set i % D, so step i + 1's encoding, preparation and encryption run
+    # while step i multiplies and decrypts.  Step i + D reuses set i % D only after
     # step i's multiply-accumulate (for pt, ct_in, the prepared terms) and
     # decryption (for ct_out) are done with it.
-    work = [{"pt": pt, "ct_in": ct_in, "ct_out": ct_out, "ws_mo": ws_mo},
-            {"pt": plan.new_pt(S.pt), "ct_in": plan.new_ct(S.ct_in), "ct_out": plan.new_ct(S.ct_out),
-             "ws_mo": plan.new_ws(S.ws_forward)}]
+    work = [{"pt": pt, "ct_in": ct_in, "ct_out": ct_out, "ws_mo": ws_mo}] + [
+        {"pt": plan.new_pt(S.pt), "ct_in": plan.new_ct(S.ct_in), "ct_out": plan.new_ct(S.ct_out),
+         "ws_mo": plan.new_ws(S.ws_forward)} for _ in range(D - 1)]
     evs = [{"enc": torch.cuda.Event(), "prep": torch.cuda.Event(), "ct": [torch.cuda.Event() for _ in slices],
             "out": [torch.cuda.Event() for _ in slices], "app": torch.cuda.Event(), "dec": torch.cuda.Event()}
-           for _ in range(2)]
-    used = [False, False]
+           for _ in range(D)]
+    used = [False] * D
 
     def begin():
         """Every step stream starts after the work already on the launch stream."""
@@ -1266,15 +1269,15 @@ def run_ours(args):
 
     def end(i):
         """The launch stream waits for step i (and so for every earlier step)."""
-        stream.wait_event(evs[i % 2]["dec"])
+        stream.wait_event(evs[i % D]["dec"])
 
     def step(i, b=None, serial=False, wait_in=None):
-        p = i % 2
+        p = i % D
         b = sets[p] if b is None else b
         w, e = work[p], evs[p]
         if serial:
             begin()
-        if used[p]:   # step i - 2 is done with this buffer set
+        if used[p]:   # step i - D is done with this buffer set
             for st in (mo_enc, mo_prep, stream):
                 st.wait_event(e["app"])
             mo_app.wait_event(e["dec"])
@@ -1309,7 +1312,7 @@ def run_ours(args):
     end(args.warmup - 1)
     torch.cuda.synchronize()
     # self-check: reconstruction equals the plaintext convolution (exact in float64)
-    y0, y1 = sets[(args.warmup - 1) % 2]["y0"], sets[(args.warmup - 1) % 2]["y1"]
+    y0, y1 = sets[(args.warmup - 1) % D]["y0"], sets[(args.warmup - 1) % D]["y1"]
     rec = ((y0 + y1) & ((1 << T_BITS) - 1)).view(LAYER["batch"], LAYER["c_out"], LAYER["h"], LAYER["w"])
     rec = torch.where(rec >= (1 << (T_BITS - 1)), rec - (1 << T_BITS), rec).double()
     ref = F.conv2d(torch.from_numpy(x).double().to(dev), torch.from_numpy(W).double().to(dev),
@@ -1383,8 +1386,8 @@ def run_ours(args):
     h2d = sum(v.numel() * 8 for v in host.values())
     d2h = 2 * S.out_elems * 8
     copy_in, copy_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_in = [torch.cuda.Event() for _ in range(D)]
+    ev_done = [torch.cuda.Event() for _ in range(D)]
     ev_copied = torch.cuda.Event()
     # the same copies with the GPU otherwise idle: the host link's own rate (the
     # first pass, untimed, also warms the copy path: the first copies from these
@@ -1395,8 +1398,8 @@ def run_ours(args):
                 for k in host:
                     sets[0][k].copy_(host[k], non_blocking=True)
             with torch.cuda.stream(copy_out):
-                hy0.copy_(sets[1]["y0"], non_blocking=True)
-                hy1.copy_(sets[1]["y1"], non_blocking=True)
+                hy0.copy_(sets[-1]["y0"], non_blocking=True)
+                hy1.copy_(sets[-1]["y1"], non_blocking=True)
 
     torch.cuda.synchronize()
     idle_reps = 10
@@ -1434,18 +1437,20 @@ def run_ours(args):
 
     h2d_into(0)
     begin()
+    base = 12_000   # (a multiple of D: step base + i uses work set i % D)
     for i in range(args.steps):
-        b = i % 2
+        b = i % D
         if i + 1 < args.steps:
-            if i >= 1:
-                copy_in.wait_event(ev_done[1 - b])   # step i - 1 (and its copy out) has finished with that set
-            h2d_into(1 - b)
-        step(10_000 + i, sets[b], wait_in=ev_in[b])   # (work set and input set: both i % 2)
+            nb = (i + 1) % D
+            if i + 1 >= D:
+                copy_in.wait_event(ev_done[nb])   # step i + 1 - D (and its copy out) has finished with that set
+            h2d_into(nb)
+        step(base + i, sets[b], wait_in=ev_in[b])   # (work set and input set: both i % D)
         copy_out.wait_event(evs[b]["dec"])
         timed_copy(copy_out, lambda: (hy0.copy_(sets[b]["y0"], non_blocking=True),
                                       hy1.copy_(sets[b]["y1"], non_blocking=True)))
         ev_done[b].record(copy_out)
-    end(10_000 + args.steps - 1)
+    end(base + args.steps - 1)
     ev_copied.record(copy_out)
     stream.wait_event(ev_copied)
     stream.wait_event(_record(copy_in))
@@ -1470,7 +1475,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        # two steps in flight (step i + 1's encoding, preparation and encryption overlap step i's
+        # several steps in flight (step i + 1's encoding, preparation and encryption overlap step i's
         # multiply-accumulate and decryption); one step alone, streams joined after every step:
         "ms_per_step_unpipelined": round(ms_serial / args.steps, 4),
         "dtype": "u64 (RNS mod q_i), u64 mod 2^41", "data": "synthetic",
@@ -1479,7 +1484,7 @@ def run_ours(args):
                    "ct_in": S.ct_in, "pt": S.pt, "ct_out": S.ct_out, "products_per_step": S.products,
                    "l2": "inputs larger than L2 (ct_in %.0f MB per step)" % (S.ct_in * S.ct_words * 8 / 1e6),
                    "parallelism": f"replicas x{world} (independent layers, no collective)",
-                   "streamed_slices": nch, "steps_in_flight": 2},
+                   "streamed_slices": nch, "steps_in_flight": D},
         "parity_selfcheck": parity_ok,
         "host_issue_ms_per_step": round(t_issue * 1e3 / args.steps, 4),
         "roofline": roof,
