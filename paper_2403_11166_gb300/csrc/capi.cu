@@ -1432,6 +1432,9 @@ extern "C" int pencil_ntt_batch(PencilCtx* ctx, uint64_t* polys, int64_t count, 
   DeviceGuard guard(ctx->device);
   ModeRaw::Params R;
   R.polys = polys;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess)
+    R.ahead = 2 * sms;   // about one wave of transform CTAs (two per SM up to N = 8192)
   if (inverse) {
     PROF(ctx, PENCIL_K_INTT_RAW, (cudaStream_t)stream);
     CUDA_TRY((ntt<ModeRaw, true>(ctx->dev, R, (int)count, (cudaStream_t)stream)));

@@ -712,11 +712,31 @@ __device__ __forceinline__ void inv_any(const DevCtx& ctx, const typename Mode::
     ntt_inv_run<LOGN, LOGE, Mode>(ctx, P, poly, limb, sm);
 }
 
+// Modes whose input is one contiguous polynomial per (poly, limb): each CTA asks
+// L2 for the input of the CTA P.ahead launch positions later (about a wave on),
+// so that CTA's first loads hit L2.
+template <class M, class = void>
+struct PrefetchAhead : std::false_type {};
+template <class M>
+struct PrefetchAhead<M, std::void_t<decltype(M::kPrefetchAhead)>> : std::bool_constant<M::kPrefetchAhead> {};
+
+template <int N, class Mode>
+__device__ __forceinline__ void prefetch_ahead(const DevCtx& ctx, const typename Mode::Params& P, int first) {
+  if constexpr (PrefetchAhead<Mode>::value) {
+    if (threadIdx.x == 0 && P.ahead > 0) {
+      const long long next = (long long)blockIdx.x + (long long)blockIdx.y * gridDim.x + P.ahead;
+      const long long y = next / gridDim.x;
+      if (y < (long long)gridDim.y) Mode::template prefetch<N>(ctx, P, first + (int)(next % gridDim.x), (int)y);
+    }
+  }
+}
+
 // CTA (x, limb) transforms polynomial first + x.
 template <int LOGN, int LOGE, class Mode, bool FOLD>
 __global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
     k_ntt_fwd(DevCtx ctx, typename Mode::Params P, int first) {
   extern __shared__ __align__(16) u64 sm[];
+  prefetch_ahead<1 << LOGN, Mode>(ctx, P, first);
   fwd_any<LOGN, LOGE, Mode, FOLD>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
 }
 
@@ -724,6 +744,7 @@ template <int LOGN, int LOGE, class Mode, bool FOLD>
 __global__ void __launch_bounds__(KCfg<LOGN, LOGE, FOLD>::T, KCfg<LOGN, LOGE, FOLD>::MIN_BLOCKS)
     k_ntt_inv(DevCtx ctx, typename Mode::Params P, int first) {
   extern __shared__ __align__(16) u64 sm[];
+  prefetch_ahead<1 << LOGN, Mode>(ctx, P, first);
   inv_any<LOGN, LOGE, Mode, FOLD>(ctx, P, first + (int)blockIdx.x, blockIdx.y, sm);
   if constexpr (ClusterLimbs<Mode>::value) Mode::template finish<1 << LOGN>(ctx, P, first + (int)blockIdx.x, sm);
 }
@@ -768,14 +789,22 @@ struct ModeRaw {
   static constexpr bool kQuad = false;
   static constexpr int kLoadUnroll = 32;
   static constexpr int kEpilogueUnroll = 16;
+  static constexpr bool kPrefetchAhead = true;
   struct Params {
     u64* polys;
+    int ahead = 0;   // CTAs ahead whose input each CTA asks L2 to fetch (0: none)
   };
   static __device__ __forceinline__ void rebase(Params&, u64) {}
   template <int N>
   static __device__ __forceinline__ u64 load(const DevCtx& c, const Params& P, const LimbConst&, int poly, int limb,
                                              int e) {
     return P.polys[limb_off(poly, limb, c.L, N) + e];
+  }
+  template <int N>
+  static __device__ __forceinline__ void prefetch(const DevCtx& c, const Params& P, int poly, int limb) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.polys + limb_off(poly, limb, c.L, N)),
+                 "r"((u32)(N * sizeof(u64)))
+                 : "memory");
   }
   template <int N>
   static __device__ __forceinline__ void store2(const DevCtx& c, const Params& P, const LimbConst&, int poly,
